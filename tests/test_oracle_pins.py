@@ -1,0 +1,324 @@
+"""Pins for the CPU oracle: closed forms, invariants, library special cases
+and brute force on tiny grids.  Each test names the passage of the paper it
+checks.  None of these tests needs a GPU."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2409_16172_gb300 import synth as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rng(seed=0):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+# --------------------------------------------------------------------------
+# DFT (Eqn. FT, discrete form)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(6, 10), (4, 6, 5), (16,), (9, 12)])
+def test_exact_dft_matches_library_fft(shape):
+    v = S.random_field(rng(1), shape)
+    np.testing.assert_allclose(O.dft(v, exact=True), np.fft.fftn(v), rtol=0, atol=1e-11 * np.abs(v).sum())
+    np.testing.assert_allclose(O.dft(v, inverse=True, exact=True), np.fft.ifftn(v), rtol=0,
+                               atol=1e-12 * np.abs(v).sum())
+
+
+@pytest.mark.parametrize("exact", [True, False])
+def test_dft_delta_constant_planewave(exact):
+    Ny, Nx = 6, 10
+    j0 = (2, 7)
+    d = np.zeros((Ny, Nx), complex)
+    d[j0] = 1
+    ky = np.arange(Ny).reshape(-1, 1)
+    kx = np.arange(Nx).reshape(1, -1)
+    want = np.exp(-2j * np.pi * (j0[0] * ky / Ny + j0[1] * kx / Nx))
+    np.testing.assert_allclose(O.dft(d, exact=exact), want, atol=1e-13)
+    one = np.ones((Ny, Nx), complex)
+    ref = np.zeros((Ny, Nx), complex)
+    ref[0, 0] = Ny * Nx
+    np.testing.assert_allclose(O.dft(one, exact=exact), ref, atol=1e-12)
+    # a plane wave exp(+2 pi i k0.j/N) lands in bin k0 with weight n: pins the sign
+    k0 = (1, 3)
+    jy = np.arange(Ny).reshape(-1, 1)
+    jx = np.arange(Nx).reshape(1, -1)
+    pw = np.exp(2j * np.pi * (k0[0] * jy / Ny + k0[1] * jx / Nx))
+    ref = np.zeros((Ny, Nx), complex)
+    ref[k0] = Ny * Nx
+    np.testing.assert_allclose(O.dft(pw, exact=exact), ref, atol=1e-11)
+    np.testing.assert_allclose(O.dft(ref, inverse=True, exact=exact), pw, atol=1e-13)
+
+
+def test_parseval():
+    v = S.random_field(rng(2), (8, 12))
+    vh = O.dft(v, exact=True)
+    assert abs(np.sum(abs(vh) ** 2) / v.size - np.sum(abs(v) ** 2)) < 1e-10 * np.sum(abs(v) ** 2)
+
+
+def test_wavenumber_tables():
+    for N in (7, 8, 16):
+        # continuous table: order and values of numpy's fftfreq (a library routine)
+        np.testing.assert_allclose(O.xi2_axis(N, 1.0, 0), (2 * np.pi * np.fft.fftfreq(N, 1.0 / N)) ** 2,
+                                   rtol=1e-15)
+        # discrete table: minus the eigenvalue of the periodic second difference
+        h = 1.0 / N
+        lam = O.xi2_axis(N, 1.0, 1)
+        for k in range(N):
+            e = np.exp(2j * np.pi * k * np.arange(N) / N)
+            d2 = (np.roll(e, -1) - 2 * e + np.roll(e, 1)) / h ** 2
+            np.testing.assert_allclose(d2, -lam[k] * e, atol=1e-9 * N * N)
+
+
+# --------------------------------------------------------------------------
+# Finite-difference operator (Eqn. 001, Section 5 discretisation)
+# --------------------------------------------------------------------------
+
+def _const_medium(shape, c, zeta=0.0, a=0.0, omega=7.0, **kw):
+    return O.make_medium(np.full(shape, c), np.full(shape, zeta), np.full(shape, a), omega,
+                         c_o=c, **kw)
+
+
+@pytest.mark.parametrize("shape", [(8, 12), (6, 4, 10)])
+def test_operator_plane_wave_eigenfunction(shape):
+    """P_N e^{i xi.x} = (w^2 + i w a - gamma^2 sum_ax (2 - 2 cos(2 pi k/N))/h^2) e^{i xi.x},
+    with gamma = c (1 - i zeta) (Eqn. Complex_wave_speed)."""
+    c, zeta, a, om = 1.3, 0.2, 3.0, 9.0
+    med = _const_medium(shape, c, zeta, a, om, M=1, Mt=1)
+    k0 = [1, 2, 3][:len(shape)]
+    grids = np.meshgrid(*[np.arange(s) for s in shape], indexing="ij")
+    ph = sum(k0[ax] * grids[ax] / shape[ax] for ax in range(len(shape)))
+    u = np.exp(2j * np.pi * ph)
+    lam = sum((2 - 2 * math.cos(2 * math.pi * k0[ax] / shape[ax])) * shape[ax] ** 2
+              for ax in range(len(shape)))
+    gam = c * (1 - 1j * zeta)
+    want = (om ** 2 + 1j * om * a - gam ** 2 * lam) * u
+    np.testing.assert_allclose(O.apply_operator(med, u), want, atol=1e-10 * abs(want).max())
+
+
+def test_operator_second_order_consistency():
+    """P_N u -> c^2 Lap u + w^2 u at rate h^2 for a smooth periodic u (Section 5:
+    second-order centred differences)."""
+    errs = []
+    for N in (32, 64, 128):
+        X = S.coords((N, N))
+        y, x = X[0], X[1]
+        cc = 1.0 + 0.3 * np.cos(2 * np.pi * x) ** 2 * np.ones((N, N))
+        med = O.make_medium(cc, None, None, 5.0, M=2, c_o=1.0)
+        u = np.sin(2 * np.pi * x) * np.cos(4 * np.pi * y) + 0j
+        lap = -(4 * np.pi ** 2 + 16 * np.pi ** 2) * u
+        want = cc ** 2 * lap + 25.0 * u
+        errs.append(np.abs(O.apply_operator(med, u) - want).max())
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.8 < r1 < 4.2 and 3.9 < r2 < 4.1, errs
+
+
+# --------------------------------------------------------------------------
+# Nodes and hat weights (Section 4.1, Lemma 3, Section 4.4, Eqn. 405)
+# --------------------------------------------------------------------------
+
+def test_real_nodes_equispaced_and_co_node():
+    cr = O.real_nodes(1.0, 2.0, 5, None)
+    np.testing.assert_allclose(cr, [1.0, 1.25, 1.5, 1.75, 2.0], rtol=1e-15)
+    # c_o strictly inside: two equispaced segments meeting at c_o
+    cr = O.real_nodes(0.8, 3.6, 12, 1.0)
+    assert 1.0 in list(cr) and cr[0] == 0.8 and cr[-1] == 3.6 and len(cr) == 12
+    i = list(cr).index(1.0)
+    np.testing.assert_allclose(np.diff(cr[:i + 1]), (1.0 - 0.8) / i, rtol=1e-12)
+    np.testing.assert_allclose(np.diff(cr[i:]), (3.6 - 1.0) / (11 - i), rtol=1e-12)
+    assert O.real_nodes(1.0, 2.0, 1, 1.0).tolist() == [1.0]
+
+
+def _layered_small(shape=(12, 10), seed=3, M=5, Mt=3):
+    p = S.small_problem(shape, seed, M=M, Mt=Mt, width=2)
+    return p, O.make_medium(p.c, p.zeta, None, p.omega, M, Mt, 1.0, None, 0.2)
+
+
+def test_weights_partition_of_unity_and_reproduce_speed():
+    """Eqn. 405 with hats: weights are in [0,1], at most two are non-zero, they
+    sum to one, and (linear interpolation reproduces linear functions) the
+    weighted node speeds give back gamma(x) = c(x)(1 - i zeta(x)) exactly."""
+    p, med = _layered_small()
+    W = med.W
+    assert np.all(W >= -1e-15) and np.all(W <= 1 + 1e-15)
+    assert np.all((W != 0).sum(0) <= 2)
+    np.testing.assert_allclose(W.sum(0), 1.0, rtol=1e-14)
+    g = np.tensordot(med.nodes.gamma, W, axes=(0, 0))
+    np.testing.assert_allclose(g, O.complex_speed(p.c, p.zeta), atol=1e-14)
+    assert np.any(p.zeta > 0) and med.nodes.m_o >= 0
+
+
+def test_layer_nodes():
+    p, med = _layered_small()
+    zmax = p.zeta.max()
+    Mt = med.nodes.Mt
+    np.testing.assert_allclose(med.nodes.gamma[med.nodes.M:],
+                               [1.0 * (1 - 1j * m * zmax / Mt) for m in range(1, Mt + 1)], rtol=1e-15)
+    assert med.nodes.c_real[med.nodes.m_o] == 1.0
+
+
+# --------------------------------------------------------------------------
+# Preconditioner apply (Eqn. 103 / 403)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(8, 12), (6, 4, 10)])
+def test_constant_medium_is_fourier_multiplier(shape):
+    """Constant c: Q_M collapses to the Fourier multiplier q(c_o, xi) of
+    Eqn. 021 (the Q_1 of Eqn. OneInterpPoint): a plane wave comes back scaled."""
+    c, om, alpha, a_node = 1.4, 11.0, 0.2, 2.0
+    med = _const_medium(shape, c, 0.0, 0.0, om, M=4, alpha=alpha, a_node=a_node)
+    k0 = [3, 1, 2][:len(shape)]
+    grids = np.meshgrid(*[np.arange(s) for s in shape], indexing="ij")
+    u = np.exp(2j * np.pi * sum(k0[ax] * grids[ax] / shape[ax] for ax in range(len(shape))))
+    xi2 = sum((2 * np.pi * (k0[ax] if k0[ax] <= (shape[ax] - 1) // 2 else k0[ax] - shape[ax])) ** 2
+              for ax in range(len(shape)))
+    q = 1.0 / (om ** 2 + 1j * om * (a_node + alpha * om) - c ** 2 * xi2)
+    for exact in (True, False):
+        np.testing.assert_allclose(O.apply_preconditioner(med, u, exact=exact), q * u, atol=1e-14)
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (10, 6), (4, 6, 8)])
+def test_discrete_symbol_inverts_operator_exactly(shape):
+    """With the finite-difference symbol, damping a > 0 in both operator and
+    symbol (alpha = 0) and constant c, Q_{N,M} P_N = I exactly (both are the
+    same Fourier multiplier, one inverted)."""
+    med = _const_medium(shape, 1.7, 0.0, 4.0, 13.0, M=3, alpha=0.0, a_node=4.0, symbol_kind=1)
+    u = S.random_field(rng(5), shape)
+    np.testing.assert_allclose(O.apply_preconditioner(med, O.apply_operator(med, u)), u,
+                               atol=1e-11 * abs(u).max())
+
+
+def test_fft_apply_equals_direct_interpolated_operator():
+    """Q_M v by K FFTs equals the direct O(n^2) evaluation of Op(q_M)
+    (Eqn. 103 vs Eqn. GeneralPSDO with the symbol of Eqn. 405)."""
+    p, med = _layered_small((8, 6))
+    v = S.random_field(rng(6), p.shape)
+    a = O.apply_preconditioner(med, v, exact=True)
+    b = O.apply_pdo_direct(O.interpolated_symbol_at_point(med), v)
+    np.testing.assert_allclose(a, b, atol=1e-13 * abs(a).max())
+
+
+def test_node_exactness_against_direct_uninterpolated_operator():
+    """Where gamma(x) is a node, q_M(gamma(x), .) = q(gamma(x), .): Q_M v
+    equals the un-interpolated Q v of Eqn. Precond (direct sum) there."""
+    shape = (8, 8)
+    c = np.ones(shape)
+    zeta = np.zeros(shape)
+    c[2:6, 2:6] = 1.5
+    c[3:5, 3:5] = 2.0
+    zeta[0, :] = 0.3
+    zeta[:, 0] = 0.3
+    zeta[7, :] = 0.15
+    zeta[0, 0] = 0.3
+    med = O.make_medium(c, zeta, None, 10.0, M=3, Mt=2, c_o=1.0, alpha=0.2)
+    np.testing.assert_allclose(sorted(med.nodes.c_real), [1.0, 1.5, 2.0])
+    v = S.random_field(rng(7), shape)
+    a = O.apply_preconditioner(med, v, exact=True)
+    b = O.apply_pdo_direct(O.exact_symbol_at_point(med), v)
+    np.testing.assert_allclose(a, b, atol=1e-13 * abs(a).max())
+
+
+def test_symbol_interpolation_error_bound():
+    """Lemma 3 with the closed form of d^2 q / dc^2 printed in Section 4.3:
+    |q - q_M| <= h_M^2/8 (max|Re q''| + max|Im q''|) on every segment."""
+    om, a = 30.0, 6.0
+    A = om ** 2 + 1j * om * a
+    for M in (3, 5, 9):
+        cr = O.real_nodes(1.0, 2.0, M, None)
+        hM = 1.0 / (M - 1)
+        cs = np.linspace(1.0, 2.0, 401)
+        c = cs.reshape(-1, 1) * np.ones((1, 3))
+        med = O.make_medium(np.ones((2, 2)) * np.array([[1.0, 2.0], [1.5, 1.2]]), None, None, om,
+                            M=M, c_o=1.0, alpha=0.0, a_node=a)
+        np.testing.assert_allclose(med.nodes.c_real, cr)
+        W = O.hat_weights(c, np.zeros_like(c), med.nodes)[:, :, 0]
+        for s in (0.0, 100.0, om ** 2 / 2.25, 900.0, 5e4):
+            q = 1.0 / (A - cs ** 2 * s)
+            qn = 1.0 / (A - cr ** 2 * s)
+            qM = (W * qn.reshape(-1, 1)).sum(0)
+            d2 = (2 * s * (A - cs ** 2 * s) + 8 * cs ** 2 * s ** 2) / (A - cs ** 2 * s) ** 3
+            fine = np.linspace(1.0, 2.0, 20001)
+            d2f = (2 * s * (A - fine ** 2 * s) + 8 * fine ** 2 * s ** 2) / (A - fine ** 2 * s) ** 3
+            bound = hM ** 2 / 8 * (np.abs(d2f.real).max() + np.abs(d2f.imag).max())
+            assert np.abs(q - qM).max() <= bound * (1 + 1e-9) + 1e-15, (M, s)
+            assert np.abs(d2).max() <= np.abs(d2f).max() * (1 + 1e-9)
+
+
+def test_interpolation_converges_second_order_in_hM():
+    """Thm. Acc: ||(Q - Q_M) v|| <= C h_M^2 ||v||: the least-squares slope of
+    log error against log h_M is 2 (direct un-interpolated Q as reference)."""
+    shape = (12, 12)
+    X = S.coords(shape)
+    c = 1.0 + 0.5 * (1 + np.cos(2 * np.pi * X[1])) * (1 + np.cos(2 * np.pi * X[0])) / 4
+    v = S.random_field(rng(8), shape)
+    ref = None
+    errs, hs = [], []
+    for M in (3, 5, 9, 17, 33):
+        med = O.make_medium(c, None, None, 20.0, M=M, c_o=1.0, alpha=0.5)
+        if ref is None:
+            ref = O.apply_pdo_direct(O.exact_symbol_at_point(med), v)
+        errs.append(np.linalg.norm(O.apply_preconditioner(med, v) - ref))
+        hs.append((c.max() - c.min()) / (M - 1))
+    slope = np.polyfit(np.log(hs), np.log(errs), 1)[0]
+    assert 1.7 < slope < 2.3, (errs, slope)
+    assert all(errs[i + 1] < errs[i] / 2.5 for i in range(len(errs) - 1)), errs
+
+
+# --------------------------------------------------------------------------
+# GMRES (Section 5 "GMRES implementation")
+# --------------------------------------------------------------------------
+
+def test_gmres_matches_dense_lu():
+    p, med = _layered_small((10, 8))
+    f = p.f[0]
+    A = O.assemble_dense(lambda u: O.apply_operator(med, u), p.shape)
+    x_lu = np.linalg.solve(A, f.ravel()).reshape(p.shape)
+    for side in ("right", "left"):
+        x, st = O.gmres(lambda u: O.apply_operator(med, u), f,
+                        lambda v: O.apply_preconditioner(med, v), restart=12, tol=1e-12,
+                        maxit=2000, side=side)
+        assert st["converged"]
+        np.testing.assert_allclose(x, x_lu, atol=1e-8 * abs(x_lu).max())
+    # unpreconditioned
+    x, st = O.gmres(lambda u: O.apply_operator(med, u), f, None, restart=30, tol=1e-12, maxit=5000)
+    np.testing.assert_allclose(x, x_lu, atol=1e-7 * abs(x_lu).max())
+
+
+def test_gmres_preconditioner_helps_and_history_monotone():
+    p = S.bump_problem(48, 11, width=6, ppw=8.0, M=4, Mt=2)
+    med = O.make_medium(p.c, p.zeta, None, p.omega, 4, 2, 1.0, None, 0.2)
+    _, st_p = O.gmres(lambda u: O.apply_operator(med, u), p.f[0],
+                      lambda v: O.apply_preconditioner(med, v), restart=30, tol=1e-6,
+                      record_history=True, maxit=600)
+    _, st_u = O.gmres(lambda u: O.apply_operator(med, u), p.f[0], None, restart=30, tol=1e-6,
+                      maxit=600)
+    assert st_p["converged"] and st_p["rel_true_resid"] <= 1e-6
+    assert st_p["iters"] < st_u["iters"]
+    h = st_p["history"]
+    # the Givens estimate is non-increasing within the first cycle
+    first = h[:min(30, len(h))]
+    assert all(first[i + 1] <= first[i] * (1 + 1e-12) for i in range(len(first) - 1))
+
+
+# --------------------------------------------------------------------------
+# Workload recipe (Section 5.1)
+# --------------------------------------------------------------------------
+
+def test_paper_example1_grid_sizes():
+    """Section 5.1: PPW = 2 pi c_o N / (L omega) with PPW = 12 gives the
+    printed N and DOF for omega = 400 pi, 600 pi, 800 pi."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "paper_example1_grids.txt"))
+    for om_pi, ppw, N, dof in rows:
+        om = S.omega_for_ppw(1.0, int(N), ppw)
+        assert abs(om - om_pi * np.pi) < 1e-9 * om
+        assert abs(N * N - dof) <= 5e-4 * dof
+
+
+def test_synth_media_respect_layer_rule():
+    for p in (S.config1(), S.small_problem((16, 12), 1)):
+        O.validate_medium(p.c, p.zeta, p.c_o)
+        assert p.c.min() >= 1.0 - 1e-15

@@ -1,0 +1,180 @@
+/*
+ * hz.h -- C ABI of the GB300 interpolated pseudodifferential Helmholtz solver.
+ *
+ * The library solves the periodic finite-difference Helmholtz system
+ *     P_N u = f,   P_N u = gamma^2 Lap_h u + (omega^2 + i omega a) u
+ * (Eqn. 001 discretised as in Section 5 "Numerical experiments": second-order
+ * centred differences, periodic boundaries) with restarted GMRES, right- and
+ * flexibly preconditioned by the interpolated pseudodifferential operator
+ *     Q_M v = sum_k w_k(x) IFFT( q_k(xi) FFT(v) ),
+ *     q_k(xi) = 1 / (omega^2 + i omega a_k - gamma_k^2 |xi|^2)
+ * (Eqn. 021, Eqn. 103, and Eqn. 403/405 with the complex wave speed
+ * gamma = c (1 - i zeta) of Eqn. Complex_wave_speed, Section 4.4).
+ *
+ * Conventions shared by every entry point
+ *   - Grid: dim 2 or 3, n[0] = Nx (fastest), n[1] = Ny, n[2] = Nz; unit box of
+ *     side L with spacing h = L / N per axis; every axis periodic.  Supported
+ *     axis lengths: 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 512, 1024,
+ *     2048 (2048 only along x and y).
+ *   - Complex vectors are interleaved (re, im).  "c128" = two doubles, "c64" =
+ *     two floats.  Several right-hand sides are stored one after another with
+ *     stride n = Nx Ny Nz elements.
+ *   - Device pointers, unless an entry point says it also takes host memory.
+ *     The caller owns every buffer it passes; the library owns what it
+ *     allocates (media, plans, their workspace).
+ *   - stream: a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Work is enqueued asynchronously unless stated otherwise.
+ *   - Every call returns an hz_status; on failure hz_last_error() gives a
+ *     thread-local message.  No entry point traps on the device: device-side
+ *     failures are reported through a status word that the host reads.
+ */
+#ifndef HZ_H
+#define HZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HZ_OK = 0,
+  HZ_ERR_INVALID_ARG = 1,   /* bad pointer, size, option or unsupported grid  */
+  HZ_ERR_OOM = 2,           /* device allocation failed                       */
+  HZ_ERR_CUDA = 3,          /* a CUDA runtime call failed                     */
+  HZ_ERR_NOT_CONVERGED = 4, /* maxit reached; the best iterate is still written */
+  HZ_ERR_BREAKDOWN = 5,     /* NaN/Inf in the Krylov recurrence               */
+  HZ_ERR_TIMEOUT = 6,       /* a bounded device wait ran out                  */
+  HZ_ERR_BUSY = 7,          /* server queue full / HBM budget exhausted       */
+  HZ_ERR_MEDIUM = 8         /* c <= 0, zeta < 0, or c != c_o inside the layer  */
+} hz_status;
+
+typedef struct {
+  int dim;      /* 2 or 3                                  */
+  int n[3];     /* Nx, Ny, Nz (Nz ignored when dim == 2)   */
+  double L;     /* side of the periodic box, > 0           */
+} hz_grid;
+
+/* Interpolation set-up (Section 4.1, Lemma 3, Section 4.4).
+ *   M          number of real wave-speed nodes, equispaced on [c_min, c_max];
+ *              c_o is forced to be a node when a layer exists (two equispaced
+ *              segments when c_o lies strictly inside the range).  M = 1 gives
+ *              the single-node Q_1 of Eqn. OneInterpPoint at c_o.
+ *   Mt         number of layer nodes c_o (1 - i zeta_m), zeta_m = m zeta_max / Mt.
+ *   c_o        background speed; c must equal c_o wherever zeta > 0.
+ *   zeta_max   <= 0: take max(zeta) of the medium.
+ *   alpha      node symbols use the damping a_k = a_node + alpha * omega.
+ *   a_node     see alpha (the paper's a(c) assumption, Section 4, with one
+ *              value for every node).
+ *   symbol_kind 0: |xi|^2 = sum (2 pi k / L)^2 (Eqn. 021);
+ *               1: the finite-difference symbol sum (4/h^2) sin^2(pi k / N). */
+typedef struct {
+  int M;
+  int Mt;
+  double c_o;
+  double zeta_max;
+  double alpha;
+  double a_node;
+  int symbol_kind;
+} hz_interp;
+
+/* Solver options.
+ *   precision  0: plain FP64 path (complex128 preconditioner, GMRES storing
+ *                 no Z: u = u0 + Q(V y));
+ *              1: complex64 preconditioner inside flexible GMRES; Arnoldi,
+ *                 operator and residuals stay FP64.
+ *   restart    m, the Krylov dimension per cycle (1..128).
+ *   tol        stop when ||f - P_N u||_2 / ||f||_2 <= tol (true residual).
+ *   maxit      cap on the total number of Arnoldi steps.               */
+typedef struct {
+  int precision;
+  int restart;
+  double tol;
+  int maxit;
+} hz_solver_opts;
+
+typedef struct {
+  int iters;               /* Arnoldi steps taken                          */
+  int restarts;            /* cycles run                                   */
+  int status;              /* hz_status of this right-hand side            */
+  int converged;           /* 1 when the true residual met tol             */
+  double rel_true_resid;   /* ||f - P_N u|| / ||f|| in FP64 at return      */
+  double rel_est_resid;    /* last Givens estimate                          */
+  float ms_total;          /* wall time of the solve on the stream (events) */
+} hz_solve_stats;
+
+typedef struct hz_medium hz_medium;
+typedef struct hz_plan hz_plan;
+
+/* Thread-local description of the last failure in this thread. */
+const char* hz_last_error(void);
+
+/* Library version string. */
+const char* hz_version(void);
+
+/* Device allocator used for media and plans.  alloc(bytes, ctx) returns a
+ * device pointer or NULL; release(ptr, ctx) frees it.  Passing NULL for both
+ * restores cudaMalloc / cudaFree.  Not thread-safe against concurrent
+ * create/plan calls. */
+hz_status hz_set_allocator(void* (*alloc)(size_t bytes, void* ctx),
+                           void (*release)(void* ptr, void* ctx), void* ctx);
+
+/* Build a medium (Section 4.4 node table, per-point interpolation records and
+ * gamma^2 of Eqn. Complex_wave_speed) from HOST arrays of n doubles each,
+ * indexed [z][y][x].  c: wave speed (> 0); zeta: layer profile (>= 0, NULL =
+ * no layer); a: operator damping of Eqn. 001 (NULL = 0).  The arrays are
+ * copied; the call returns after the medium is ready.
+ * Errors: HZ_ERR_INVALID_ARG (grid, options), HZ_ERR_MEDIUM (c <= 0, zeta < 0,
+ * NaN, c != c_o in the layer, too few nodes), HZ_ERR_OOM, HZ_ERR_CUDA. */
+hz_status hz_create_medium(const hz_grid* grid, const double* c, const double* zeta,
+                           const double* a, double omega, const hz_interp* interp,
+                           hz_medium** out);
+
+/* Node table of a medium: K = number of symbol planes, M real nodes, Mt layer
+ * nodes; gamma_re/gamma_im/a_k receive K values each (may be NULL);
+ * c_min/c_max over the grid. */
+hz_status hz_medium_info(const hz_medium* med, int* K, int* M, int* Mt, double* gamma_re,
+                         double* gamma_im, double* a_k, double* c_min, double* c_max);
+
+hz_status hz_destroy_medium(hz_medium* med);
+
+/* A plan owns the workspace to apply and solve with up to max_nrhs
+ * right-hand sides at once on one medium (K symbol planes per right-hand
+ * side, the Krylov basis and the small Hessenberg systems). The medium must
+ * outlive the plan. */
+hz_status hz_plan_create(hz_medium* med, const hz_solver_opts* opts, int max_nrhs,
+                         hz_plan** out);
+
+/* Bytes of device memory the plan holds. */
+hz_status hz_plan_bytes(const hz_plan* plan, size_t* bytes);
+
+hz_status hz_destroy_plan(hz_plan* plan);
+
+/* y = P_N x for nrhs c128 vectors (device pointers, x != y), FP64
+ * (Eqn. 001, Section 5). */
+hz_status hz_apply_operator(hz_plan* plan, const void* x, void* y, int nrhs, void* stream);
+
+/* y = Q_M x for nrhs c128 device vectors (x may equal y).  precision 0
+ * computes in complex128, 1 in complex64 (input rounded to c64, output
+ * widened to c128).  Eqn. 103 / 403 with one forward FFT, K symbol
+ * multiplies each followed by an inverse FFT, and the weighted sum. */
+hz_status hz_apply_preconditioner(hz_plan* plan, const void* x, void* y, int nrhs,
+                                  int precision, void* stream);
+
+/* Solve P_N u = f for nrhs right-hand sides with restarted (F)GMRES(m):
+ * CGS2 Arnoldi in FP64, complex Givens rotations, true-residual check after
+ * each cycle whose estimate reached tol.  f and u are c128 arrays of
+ * nrhs * n elements in device OR host memory (host buffers are staged
+ * through the plan); u holds the initial guess on entry.  stats receives
+ * nrhs entries (may be NULL).  Synchronous: returns when the solve is done.
+ * Returns HZ_OK when every right-hand side converged, HZ_ERR_NOT_CONVERGED
+ * (u still holds the last iterate) or HZ_ERR_BREAKDOWN otherwise. */
+hz_status hz_gmres_solve(hz_plan* plan, const void* f, void* u, int nrhs,
+                         hz_solve_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HZ_H */

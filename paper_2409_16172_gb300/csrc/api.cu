@@ -1,0 +1,243 @@
+// C ABI: errors, allocator, plans, operator / preconditioner apply and the
+// restarted (F)GMRES driver (Section 5, "GMRES implementation"; right and
+// flexible preconditioning with Q_M of Eqn. 103 / 403).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "hz_internal.h"
+#include "kernels.h"
+
+namespace hz {
+
+// ---------------------------------------------------------------------------
+// errors and allocation
+// ---------------------------------------------------------------------------
+namespace {
+thread_local std::string g_err;
+void* (*g_alloc)(size_t, void*) = nullptr;
+void (*g_free)(void*, void*) = nullptr;
+void* g_ctx = nullptr;
+}  // namespace
+
+hz_status set_error(hz_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+hz_status cuda_error(cudaError_t e, const char* what) {
+  const hz_status st = e == cudaErrorMemoryAllocation ? HZ_ERR_OOM : HZ_ERR_CUDA;
+  return set_error(st, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void* dev_alloc(size_t bytes) {
+  if (g_alloc) return g_alloc(bytes, g_ctx);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(void* p) {
+  if (!p) return;
+  if (g_free) g_free(p, g_ctx);
+  else cudaFree(p);
+}
+
+const FftOps* fft_ops_8();
+const FftOps* fft_ops_12();
+const FftOps* fft_ops_16();
+const FftOps* fft_ops_24();
+const FftOps* fft_ops_32();
+const FftOps* fft_ops_48();
+const FftOps* fft_ops_64();
+const FftOps* fft_ops_96();
+const FftOps* fft_ops_128();
+const FftOps* fft_ops_192();
+const FftOps* fft_ops_256();
+const FftOps* fft_ops_512();
+const FftOps* fft_ops_1024();
+const FftOps* fft_ops_2048();
+
+const FftOps* fft_ops(int N) {
+  switch (N) {
+    case 8: return fft_ops_8();
+    case 12: return fft_ops_12();
+    case 16: return fft_ops_16();
+    case 24: return fft_ops_24();
+    case 32: return fft_ops_32();
+    case 48: return fft_ops_48();
+    case 64: return fft_ops_64();
+    case 96: return fft_ops_96();
+    case 128: return fft_ops_128();
+    case 192: return fft_ops_192();
+    case 256: return fft_ops_256();
+    case 512: return fft_ops_512();
+    case 1024: return fft_ops_1024();
+    case 2048: return fft_ops_2048();
+    default: return nullptr;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// preconditioner apply: Q_M v = sum_k w_k IFFT(q_k FFT(v)) / n
+// ---------------------------------------------------------------------------
+static hz_status ensure_planes(hz_plan* p, int prec) {
+  if (p->planes && p->planes_prec <= prec) return HZ_OK;  // c128 buffer also fits c64
+  const hz_medium* m = p->med;
+  const size_t es = prec == 0 ? 16 : 8;
+  void* np = dev_alloc(size_t(p->max_nrhs) * m->K * m->n * es);
+  if (!np) return set_error(HZ_ERR_OOM, "no memory for %d x %d symbol planes", p->max_nrhs, m->K);
+  if (p->planes) {
+    auto it = std::find(p->arena.ptrs.begin(), p->arena.ptrs.end(), p->planes);
+    if (it != p->arena.ptrs.end()) p->arena.ptrs.erase(it);
+    dev_free(p->planes);
+  }
+  p->arena.ptrs.push_back(np);
+  p->arena.bytes += size_t(p->max_nrhs) * m->K * m->n * es;
+  p->planes = np;
+  p->planes_prec = prec;
+  return HZ_OK;
+}
+
+// in: nrhs c128 vectors at stride n, each scaled by scale[b] (NULL = 1).
+// out_kind 0: c64 output, 1: c128 output.  prec 0: complex128 arithmetic.
+hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* scale, int nrhs,
+                        void* out, int out_kind, cudaStream_t st) {
+  const hz_medium* m = p->med;
+  HZ_TRY(ensure_planes(p, prec));
+  const int nx = m->nx, ny = m->ny, nz = m->nz;
+  const long n = m->n;
+  const FftOps* ox = fft_ops(nx);
+  const FftOps* oy = fft_ops(ny);
+  const AxisTables& tx = m->ax[0];
+  const AxisTables& ty = m->ax[1];
+  auto tw = [&](const AxisTables& t) -> const void* { return prec == 0 ? (const void*)t.tw64 : (const void*)t.tw32; };
+  auto xi = [&](const AxisTables& t) -> const void* { return prec == 0 ? (const void*)t.xi2_64 : (const void*)t.xi2_32; };
+  const void* A = prec == 0 ? (const void*)m->symA64 : (const void*)m->symA32;
+  const void* G = prec == 0 ? (const void*)m->symG64 : (const void*)m->symG32;
+  const void* rec = prec == 0 ? (const void*)m->rec64 : (const void*)m->rec32;
+  const long rows = n / nx;
+  HZ_TRY(ox->row_fwd(prec, in, scale, rows, rows * nrhs, tw(tx), p->tmp, st));
+  if (m->dim == 2) {
+    HZ_TRY(oy->line_fused(prec, p->tmp, p->planes, nx, 1, nx, 0, n, m->K, nrhs, xi(tx), nullptr,
+                          xi(ty), A, G, m->rowmask, 0, 1, tw(ty), st));
+  } else {
+    const FftOps* oz = fft_ops(nz);
+    const AxisTables& tz = m->ax[2];
+    const long slab = long(nx) * ny;
+    HZ_TRY(oy->line_pass(prec, -1, p->tmp, nx, nz, nx, slab, n, nrhs, nullptr, m->K, tw(ty), st));
+    HZ_TRY(oz->line_fused(prec, p->tmp, p->planes, nx, ny, slab, nx, n, m->K, nrhs, xi(tx), xi(ty),
+                          xi(tz), A, G, m->slabmask, 0, 1, tw(tz), st));
+    HZ_TRY(oy->line_pass(prec, +1, p->planes, nx, nz, nx, slab, n, nrhs * m->K, m->slabmask, m->K,
+                         tw(ty), st));
+  }
+  HZ_TRY(ox->row_inv_acc(prec, out_kind, p->planes, rec, m->segtab, m->nseg, m->rowmask, m->K,
+                         rows, rows * nrhs, n, 1.0 / double(n), tw(tx), out, st));
+  return HZ_OK;
+}
+
+}  // namespace hz
+
+using namespace hz;
+
+extern "C" const char* hz_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char* hz_version(void) { return "hz-pdo 0.1 (sm_103a)"; }
+
+extern "C" hz_status hz_set_allocator(void* (*alloc)(size_t, void*), void (*release)(void*, void*),
+                                      void* ctx) {
+  if ((alloc == nullptr) != (release == nullptr))
+    return set_error(HZ_ERR_INVALID_ARG, "alloc and release must both be set or both be NULL");
+  g_alloc = alloc;
+  g_free = release;
+  g_ctx = ctx;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_plan_create(hz_medium* med, const hz_solver_opts* opts, int max_nrhs,
+                                    hz_plan** out) {
+  if (!med || !opts || !out) return set_error(HZ_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (max_nrhs < 1) return set_error(HZ_ERR_INVALID_ARG, "max_nrhs must be >= 1");
+  if (opts->precision != 0 && opts->precision != 1)
+    return set_error(HZ_ERR_INVALID_ARG, "precision must be 0 or 1");
+  if (opts->restart < 1 || opts->restart > HZ_MAX_RESTART)
+    return set_error(HZ_ERR_INVALID_ARG, "restart must be in [1, %d]", HZ_MAX_RESTART);
+  if (!(opts->tol > 0) || opts->maxit < 1) return set_error(HZ_ERR_INVALID_ARG, "need tol > 0, maxit >= 1");
+  hz_plan* p = new hz_plan();
+  p->med = med;
+  p->opts = *opts;
+  p->max_nrhs = max_nrhs;
+  const long n = med->n;
+  const int m = opts->restart;
+  const int B = max_nrhs;
+  auto fail = [&](hz_status s) {
+    p->arena.release();
+    delete p;
+    return s;
+  };
+  hz_status st;
+  const size_t es = opts->precision == 0 ? 16 : 8;
+  void* tmp = nullptr;
+  if ((st = p->arena.alloc(reinterpret_cast<char**>(&tmp), size_t(B) * n * 16)) != HZ_OK) return fail(st);
+  p->tmp = tmp;
+  if ((st = ensure_planes(p, opts->precision)) != HZ_OK) return fail(st);
+  if ((st = p->arena.alloc(&p->V, size_t(m + 1) * B * n)) != HZ_OK) return fail(st);
+  // Z: FGMRES basis (c64); the FP64 path keeps one c128 work vector per rhs
+  void* Z = nullptr;
+  const size_t zlen = opts->precision == 1 ? size_t(m) * B * n * es : size_t(B) * n * 16;
+  if ((st = p->arena.alloc(reinterpret_cast<char**>(&Z), zlen)) != HZ_OK) return fail(st);
+  p->Z = Z;
+  if ((st = p->arena.alloc(&p->u, size_t(B) * n)) != HZ_OK) return fail(st);
+  if ((st = p->arena.alloc(&p->f, size_t(B) * n)) != HZ_OK) return fail(st);
+  const int nblk = std::max(stencil_blocks(n), krylov_blocks(n, 1, 1));
+  p->partial_len = size_t(B) * (m + 2) * std::max(nblk, 1024) * 2;
+  if ((st = p->arena.alloc(&p->partial, p->partial_len)) != HZ_OK) return fail(st);
+  *out = p;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_plan_bytes(const hz_plan* plan, size_t* bytes) {
+  if (!plan || !bytes) return set_error(HZ_ERR_INVALID_ARG, "null argument");
+  *bytes = plan->arena.bytes;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_destroy_plan(hz_plan* plan) {
+  if (!plan) return HZ_OK;
+  plan->arena.release();
+  delete plan;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_apply_operator(hz_plan* plan, const void* x, void* y, int nrhs, void* stream) {
+  if (!plan || !x || !y) return set_error(HZ_ERR_INVALID_ARG, "null argument");
+  if (nrhs < 1 || nrhs > plan->max_nrhs) return set_error(HZ_ERR_INVALID_ARG, "nrhs out of range");
+  if (x == y) return set_error(HZ_ERR_INVALID_ARG, "x and y must not alias");
+  const long n = plan->med->n;
+  return launch_stencil(plan->med, 0, x, n, static_cast<double2*>(y), n, nrhs, nullptr,
+                        static_cast<cudaStream_t>(stream));
+}
+
+extern "C" hz_status hz_apply_preconditioner(hz_plan* plan, const void* x, void* y, int nrhs,
+                                             int precision, void* stream) {
+  if (!plan || !x || !y) return set_error(HZ_ERR_INVALID_ARG, "null argument");
+  if (nrhs < 1 || nrhs > plan->max_nrhs) return set_error(HZ_ERR_INVALID_ARG, "nrhs out of range");
+  if (precision != 0 && precision != 1) return set_error(HZ_ERR_INVALID_ARG, "precision must be 0 or 1");
+  return precond_apply(plan, precision, static_cast<const double2*>(x), nullptr, nrhs, y, 1,
+                       static_cast<cudaStream_t>(stream));
+}

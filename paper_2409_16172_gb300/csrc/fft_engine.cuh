@@ -1,0 +1,228 @@
+// Shared-memory Stockham FFT engine for one line of length N per group of
+// TPL threads, E = N / TPL complex elements per thread in registers.
+//
+// The transform convention is the discrete form of the symmetric Fourier
+// pair (Section 2, Eqn. FT): forward X[k] = sum_j x[j] e^{-2 pi i jk/N}
+// (sign -1), inverse with e^{+2 pi i jk/N} (sign +1) and no scaling; the 1/n
+// of the inverse is applied once at the end of the preconditioner.
+//
+// Stage s has radix R and Ns = product of the earlier radices.  Butterfly j
+// (0 <= j < N/R) reads x[j + r N/R], multiplies input r by w_{Ns R}^{r (j mod Ns)},
+// runs an R-point DFT and writes y[(j / Ns) Ns R + (j mod Ns) + r Ns]; after
+// the last stage the line is in natural order (mixed-radix Stockham autosort).
+// Thread t of a line runs butterflies j = t + b TPL, b = 0 .. E/R - 1.
+//
+// Shared memory holds a line padded by one element every PAD_SHIFT elements
+// so that the stride-R writes of the early stages spread over the banks.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hz {
+
+template <typename R> struct cvec;
+template <> struct cvec<float> { using T = float2; };
+template <> struct cvec<double> { using T = double2; };
+
+template <typename V> __device__ __forceinline__ V cmk(decltype(V::x) a, decltype(V::x) b) {
+  V r; r.x = a; r.y = b; return r;
+}
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
+  return cmk<V>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V::x) s) { return cmk<V>(a.x * s, a.y * s); }
+// multiply by S*i  (S = +1: i a, S = -1: -i a)
+template <int S, typename V> __device__ __forceinline__ V cmul_si(V a) {
+  return (S > 0) ? cmk<V>(-a.y, a.x) : cmk<V>(a.y, -a.x);
+}
+
+// ---------------------------------------------------------------------------
+// Small DFTs, X[m] = sum_n x[n] e^{S 2 pi i n m / R}, in place on x[0..R-1].
+// ---------------------------------------------------------------------------
+template <int S, typename V> __device__ __forceinline__ void dft2(V* x) {
+  V a = x[0], b = x[1];
+  x[0] = cadd(a, b); x[1] = csub(a, b);
+}
+
+template <int S, typename V> __device__ __forceinline__ void dft3(V* x) {
+  using R = decltype(V::x);
+  const R h = R(0.86602540378443864676);  // sin(2 pi / 3)
+  V s = cadd(x[1], x[2]);
+  V d = csub(x[1], x[2]);
+  V t = cmk<V>(x[0].x - R(0.5) * s.x, x[0].y - R(0.5) * s.y);
+  V e = cmul_si<S>(cscale(d, h));
+  x[0] = cadd(x[0], s);
+  x[1] = cadd(t, e);
+  x[2] = csub(t, e);
+}
+
+template <int S, typename V> __device__ __forceinline__ void dft4(V* x) {
+  V a = cadd(x[0], x[2]), b = csub(x[0], x[2]);
+  V c = cadd(x[1], x[3]), d = cmul_si<S>(csub(x[1], x[3]));
+  x[0] = cadd(a, c); x[2] = csub(a, c);
+  x[1] = cadd(b, d); x[3] = csub(b, d);
+}
+
+template <int S, typename V> __device__ __forceinline__ void dft8(V* x) {
+  using R = decltype(V::x);
+  const R r2 = R(0.70710678118654752440);
+  V e[4] = {x[0], x[2], x[4], x[6]};
+  V o[4] = {x[1], x[3], x[5], x[7]};
+  dft4<S>(e);
+  dft4<S>(o);
+  // w8^1 = r2 (1 + S i), w8^2 = S i, w8^3 = r2 (-1 + S i)
+  V o1 = cscale(cadd(o[1], cmul_si<S>(o[1])), r2);
+  V o2 = cmul_si<S>(o[2]);
+  V o3 = cscale(csub(cmul_si<S>(o[3]), o[3]), r2);
+  x[0] = cadd(e[0], o[0]); x[4] = csub(e[0], o[0]);
+  x[1] = cadd(e[1], o1);   x[5] = csub(e[1], o1);
+  x[2] = cadd(e[2], o2);   x[6] = csub(e[2], o2);
+  x[3] = cadd(e[3], o3);   x[7] = csub(e[3], o3);
+}
+
+// w16^m = cos(2 pi m / 16) + S i sin(2 pi m / 16)
+template <int S, typename V> __device__ __forceinline__ V w16mul(V a, int m) {
+  using R = decltype(V::x);
+  const R c1 = R(0.92387953251128675613), s1 = R(0.38268343236508977173);
+  const R r2 = R(0.70710678118654752440);
+  R c, s;
+  switch (m) {
+    case 0: return a;
+    case 1: c = c1; s = s1; break;
+    case 2: c = r2; s = r2; break;
+    case 3: c = s1; s = c1; break;
+    case 4: return cmul_si<S>(a);
+    case 6: c = -r2; s = r2; break;
+    case 9: c = -c1; s = -s1; break;
+    default: c = R(1); s = R(0); break;  // not reached for the 4x4 split
+  }
+  return cmul(a, cmk<V>(c, R(S) * s));
+}
+
+template <int S, typename V> __device__ __forceinline__ void dft16(V* x) {
+  V y[16];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    V t[4] = {x[n2], x[n2 + 4], x[n2 + 8], x[n2 + 12]};
+    dft4<S>(t);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) y[n2 * 4 + k1] = w16mul<S>(t[k1], n2 * k1);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    V t[4] = {y[k1], y[4 + k1], y[8 + k1], y[12 + k1]};
+    dft4<S>(t);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) x[k1 + 4 * k2] = t[k2];
+  }
+}
+
+template <int RAD, int S, typename V> __device__ __forceinline__ void dftR(V* x) {
+  if constexpr (RAD == 2) dft2<S>(x);
+  else if constexpr (RAD == 3) dft3<S>(x);
+  else if constexpr (RAD == 4) dft4<S>(x);
+  else if constexpr (RAD == 8) dft8<S>(x);
+  else if constexpr (RAD == 16) dft16<S>(x);
+  else static_assert(RAD == 2, "unsupported radix");
+}
+
+// ---------------------------------------------------------------------------
+// Radix plans: N = prod(radices); E is a multiple of every radix.
+// ---------------------------------------------------------------------------
+template <int N> struct FftPlan;
+#define HZ_PLAN(NN, EE, ...)                                               \
+  template <> struct FftPlan<NN> {                                         \
+    static constexpr int E = EE;                                           \
+    static constexpr int rads[] = {__VA_ARGS__};                           \
+    static constexpr int NST = sizeof(rads) / sizeof(int);                 \
+    __host__ __device__ static constexpr int rad(int s) { return rads[s]; } \
+  };
+HZ_PLAN(8, 8, 8)
+HZ_PLAN(12, 12, 4, 3)
+HZ_PLAN(16, 16, 16)
+HZ_PLAN(24, 24, 8, 3)
+HZ_PLAN(32, 8, 8, 4)
+HZ_PLAN(48, 12, 4, 4, 3)
+HZ_PLAN(64, 8, 8, 8)
+HZ_PLAN(96, 24, 8, 4, 3)
+HZ_PLAN(128, 16, 16, 8)
+HZ_PLAN(192, 24, 8, 8, 3)
+HZ_PLAN(256, 16, 16, 16)
+HZ_PLAN(512, 8, 8, 8, 8)
+HZ_PLAN(1024, 16, 16, 16, 4)
+HZ_PLAN(2048, 16, 16, 16, 8)
+#undef HZ_PLAN
+
+constexpr int PAD_SHIFT = 4;
+__host__ __device__ constexpr int padded(int i) { return i + (i >> PAD_SHIFT); }
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> PAD_SHIFT) + 1; }
+
+template <typename R, int N, int S> struct LineFFT {
+  using V = typename cvec<R>::T;
+  using P = FftPlan<N>;
+  static constexpr int E = P::E;
+  static constexpr int TPL = N / E;
+  static constexpr int R0 = P::rad(0);
+
+  // Frequency / position index held in x[e] before stage 0 (the stage-0
+  // read pattern): b = e / R0, r = e % R0, j = t + b TPL, index = j + r N/R0.
+  __device__ static __forceinline__ int stage0_index(int t, int e) {
+    return (t + (e / R0) * TPL) + (e % R0) * (N / R0);
+  }
+
+  __device__ static __forceinline__ void load_stage0(const V* line, int t, V (&x)[E]) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = line[padded(stage0_index(t, e))];
+  }
+
+  template <int STAGE, int NS>
+  __device__ static __forceinline__ void stage(V* line, int t, V (&x)[E], const V* __restrict__ tw) {
+    if constexpr (STAGE < P::NST) {
+      constexpr int RAD = P::rad(STAGE);
+      if constexpr (STAGE > 0) {
+#pragma unroll
+        for (int b = 0; b < E / RAD; ++b) {
+          const int j = t + b * TPL;
+#pragma unroll
+          for (int r = 0; r < RAD; ++r) x[b * RAD + r] = line[padded(j + r * (N / RAD))];
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int b = 0; b < E / RAD; ++b) {
+        const int j = t + b * TPL;
+        const int k = j % NS;
+        if constexpr (NS > 1) {
+#pragma unroll
+          for (int r = 1; r < RAD; ++r) {
+            V w = __ldg(&tw[r * k * (N / (NS * RAD))]);
+            if constexpr (S > 0) w.y = -w.y;
+            x[b * RAD + r] = cmul(x[b * RAD + r], w);
+          }
+        }
+        dftR<RAD, S>(&x[b * RAD]);
+        const int d = (j / NS) * NS * RAD + k;
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) line[padded(d + r * NS)] = x[b * RAD + r];
+      }
+      __syncthreads();
+      stage<STAGE + 1, NS * RAD>(line, t, x, tw);
+    }
+  }
+
+  // Runs the whole transform.  On entry x holds the stage-0 inputs and every
+  // thread of the block has finished reading the line (the caller syncs).
+  // On exit the line holds the result in natural order and the block is
+  // synchronised.  tw[i] = exp(-2 pi i * i / N) for i < N.
+  __device__ static __forceinline__ void run(V* line, int t, V (&x)[E], const V* __restrict__ tw) {
+    stage<0, 1>(line, t, x, tw);
+  }
+};
+
+}  // namespace hz

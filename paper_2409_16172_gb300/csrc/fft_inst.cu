@@ -1,0 +1,147 @@
+// Instantiates the FFT pass kernels for one axis length, HZ_FFT_N, and
+// exposes them as an FftOps table.  The build compiles this file once per
+// supported length, in parallel.
+#include "fft_kernels.cuh"
+
+#ifndef HZ_FFT_N
+#error "HZ_FFT_N must be defined"
+#endif
+
+namespace hz {
+namespace {
+
+constexpr int N = HZ_FFT_N;
+
+template <typename K>
+hz_status smem_attr(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) {
+    HZ_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+  }
+  return HZ_OK;
+}
+
+template <typename R>
+hz_status row_fwd_t(const double2* in, const double* scale, long rows_per_rhs, long nrows,
+                    const void* tw, void* out, cudaStream_t st) {
+  using C = LineCfg<R, N>;
+  using V = typename cvec<R>::T;
+  auto k = row_fwd_kernel<R, N>;
+  HZ_TRY(smem_attr(k, C::row_smem()));
+  const long blocks = (nrows + C::ROW_LINES - 1) / C::ROW_LINES;
+  k<<<unsigned(blocks), C::ROW_THREADS, C::row_smem(), st>>>(
+      in, scale, rows_per_rhs, nrows, static_cast<const V*>(tw), static_cast<V*>(out));
+  HZ_CUDA(cudaGetLastError());
+  return HZ_OK;
+}
+
+hz_status row_fwd(int prec, const double2* in, const double* scale, long rows_per_rhs, long nrows,
+                  const void* tw, void* out, cudaStream_t st) {
+  return prec == 0 ? row_fwd_t<double>(in, scale, rows_per_rhs, nrows, tw, out, st)
+                   : row_fwd_t<float>(in, scale, rows_per_rhs, nrows, tw, out, st);
+}
+
+template <typename R, typename OutT>
+hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segtab, int nseg,
+                        const unsigned long long* rowmask, int K, long rows_per_rhs, long nrows,
+                        long n, double inv_n, const void* tw, void* out, cudaStream_t st) {
+  using C = LineCfg<R, N>;
+  using V = typename cvec<R>::T;
+  auto k = row_inv_acc_kernel<R, N, OutT>;
+  HZ_TRY(smem_attr(k, C::row_smem()));
+  const long blocks = (nrows + C::ROW_LINES - 1) / C::ROW_LINES;
+  k<<<unsigned(blocks), C::ROW_THREADS, C::row_smem(), st>>>(
+      static_cast<const V*>(planes), static_cast<const typename RecT<R>::T*>(rec), segtab, nseg,
+      rowmask, K, rows_per_rhs, nrows, n, R(inv_n), static_cast<const V*>(tw),
+      static_cast<OutT*>(out));
+  HZ_CUDA(cudaGetLastError());
+  return HZ_OK;
+}
+
+hz_status row_inv_acc(int prec, int out_kind, const void* planes, const void* rec,
+                      const uchar2* segtab, int nseg, const unsigned long long* rowmask, int K,
+                      long rows_per_rhs, long nrows, long n, double inv_n, const void* tw,
+                      void* out, cudaStream_t st) {
+  if (prec == 0)
+    return row_inv_acc_t<double, double2>(planes, rec, segtab, nseg, rowmask, K, rows_per_rhs,
+                                          nrows, n, inv_n, tw, out, st);
+  if (out_kind == 0)
+    return row_inv_acc_t<float, float2>(planes, rec, segtab, nseg, rowmask, K, rows_per_rhs,
+                                        nrows, n, inv_n, tw, out, st);
+  return row_inv_acc_t<float, double2>(planes, rec, segtab, nseg, rowmask, K, rows_per_rhs,
+                                       nrows, n, inv_n, tw, out, st);
+}
+
+template <typename R, int SIGN>
+hz_status line_pass_t(void* data, int nx, long outer, long S, long ostride, long bstride,
+                      int batch, const unsigned long long* omask, int K, const void* tw,
+                      cudaStream_t st) {
+  using C = LineCfg<R, N>;
+  using V = typename cvec<R>::T;
+  auto k = line_pass_kernel<R, N, SIGN>;
+  HZ_TRY(smem_attr(k, C::col_smem(false)));
+  const int ntile = (nx + C::TB - 1) / C::TB;
+  dim3 grid(unsigned(ntile * outer), 1, unsigned(batch));
+  k<<<grid, C::COL_THREADS, C::col_smem(false), st>>>(static_cast<V*>(data), nx, ntile, S,
+                                                       ostride, bstride, omask, K,
+                                                       static_cast<const V*>(tw));
+  HZ_CUDA(cudaGetLastError());
+  return HZ_OK;
+}
+
+hz_status line_pass(int prec, int sign, void* data, int nx, long outer, long S, long ostride,
+                    long bstride, int batch, const unsigned long long* omask, int K,
+                    const void* tw, cudaStream_t st) {
+  if (prec == 0)
+    return sign < 0 ? line_pass_t<double, -1>(data, nx, outer, S, ostride, bstride, batch, omask, K, tw, st)
+                    : line_pass_t<double, +1>(data, nx, outer, S, ostride, bstride, batch, omask, K, tw, st);
+  return sign < 0 ? line_pass_t<float, -1>(data, nx, outer, S, ostride, bstride, batch, omask, K, tw, st)
+                  : line_pass_t<float, +1>(data, nx, outer, S, ostride, bstride, batch, omask, K, tw, st);
+}
+
+template <typename R>
+hz_status line_fused_t(const void* in, void* planes, int nx, long outer, long S, long ostride,
+                       long n, int K, int batch, const void* xi2_x, const void* xi2_o,
+                       const void* xi2_l, const void* symA, const void* symG,
+                       const unsigned long long* smask, long smO, long smS, const void* tw,
+                       cudaStream_t st) {
+  using C = LineCfg<R, N>;
+  using V = typename cvec<R>::T;
+  auto k = line_fused_kernel<R, N>;
+  HZ_TRY(smem_attr(k, C::col_smem(true)));
+  const int ntile = (nx + C::TB - 1) / C::TB;
+  const long base_blocks = long(ntile) * outer * batch;
+  // split the K nodes over blocks until the grid covers the GPU about twice
+  int nks = int((2L * 152 + base_blocks - 1) / base_blocks);
+  if (nks < 1) nks = 1;
+  if (nks > K) nks = K;
+  dim3 grid(unsigned(ntile * outer), 1, unsigned(batch * nks));
+  k<<<grid, C::COL_THREADS, C::col_smem(true), st>>>(
+      static_cast<const V*>(in), static_cast<V*>(planes), nx, ntile, S, ostride, n, K, nks,
+      static_cast<const R*>(xi2_x), static_cast<const R*>(xi2_o), static_cast<const R*>(xi2_l),
+      static_cast<const V*>(symA), static_cast<const V*>(symG), smask, smO, smS,
+      static_cast<const V*>(tw));
+  HZ_CUDA(cudaGetLastError());
+  return HZ_OK;
+}
+
+hz_status line_fused(int prec, const void* in, void* planes, int nx, long outer, long S,
+                     long ostride, long n, int K, int batch, const void* xi2_x, const void* xi2_o,
+                     const void* xi2_l, const void* symA, const void* symG,
+                     const unsigned long long* smask, long smO, long smS, const void* tw,
+                     cudaStream_t st) {
+  return prec == 0
+             ? line_fused_t<double>(in, planes, nx, outer, S, ostride, n, K, batch, xi2_x, xi2_o,
+                                    xi2_l, symA, symG, smask, smO, smS, tw, st)
+             : line_fused_t<float>(in, planes, nx, outer, S, ostride, n, K, batch, xi2_x, xi2_o,
+                                   xi2_l, symA, symG, smask, smO, smS, tw, st);
+}
+
+const FftOps ops = {N, row_fwd, row_inv_acc, line_pass, line_fused};
+
+}  // namespace
+
+#define HZ_CAT2(a, b) a##b
+#define HZ_CAT(a, b) HZ_CAT2(a, b)
+const FftOps* HZ_CAT(fft_ops_, HZ_FFT_N)() { return &ops; }
+
+}  // namespace hz

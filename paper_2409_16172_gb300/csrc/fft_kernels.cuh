@@ -1,0 +1,290 @@
+// FFT pass kernels of the preconditioner apply Q_M v (Eqn. 103 / 403):
+//
+//   row_fwd       forward FFT along x of the input vector (c128 in, scaled by
+//                 the Krylov normalisation, rounded to the working precision)
+//   line_pass     forward or inverse FFT along a strided axis (3D y axis)
+//   line_fused    last axis: forward FFT completes vhat, then for each node k
+//                 multiply by q_k(|xi|^2) = 1 / (w^2 + i w a_k - gamma_k^2 |xi|^2)
+//                 (Eqn. 021, recomputed, never stored) and inverse FFT along
+//                 the same axis, writing plane k
+//   row_inv_acc   inverse FFT along x of every plane a row needs, then the
+//                 weighted sum z = (1/n) sum_k w_k(x) plane_k(x) (Eqn. 405:
+//                 two non-zero hat weights per point)
+//
+// Layout: vectors [rhs][z][y][x] (x fastest); planes [rhs][k][z][y][x].
+// Every kernel stages its lines through padded shared memory and runs the
+// Stockham engine of fft_engine.cuh; global loads and stores are coalesced
+// along x (rows directly, strided axes in tiles of TB adjacent columns).
+#pragma once
+#include "fft_engine.cuh"
+#include "hz_internal.h"
+
+namespace hz {
+
+// Launch shapes.  Row kernels: ROW_THREADS threads, ROW_THREADS / TPL lines.
+// Strided kernels: TB adjacent columns x TPL threads, TB chosen so that a
+// block moves at least 64 contiguous bytes per row, has >= 128 threads, at
+// most 512, and its shared memory stays under ~200 KB.
+template <typename R, int N> struct LineCfg {
+  static constexpr int TPL = N / FftPlan<N>::E;
+  static constexpr int ROW_THREADS = TPL > 128 ? TPL : 128;
+  static constexpr int ROW_LINES = ROW_THREADS / TPL;
+  static constexpr int VB = int(2 * sizeof(R));
+  static constexpr int BUFS = sizeof(R) == 4 ? 1 : 2;  // fused kernel: spectrum copy for FP64
+  static constexpr int tb_calc() {
+    int tb = 64 / VB;
+    if (tb * TPL < 128) tb = 128 / TPL;
+    while (tb > 1 && tb * TPL > 512) tb /= 2;
+    while (tb > 1 && long(BUFS) * tb * padded_len(N) * VB > 200 * 1024) tb /= 2;
+    return tb;
+  }
+  static constexpr int TB = tb_calc();
+  static constexpr int COL_THREADS = TB * TPL;
+  static constexpr size_t row_smem() { return size_t(ROW_LINES) * padded_len(N) * VB; }
+  static constexpr size_t col_smem(bool fused) {
+    return size_t(fused ? BUFS : 1) * TB * padded_len(N) * VB;
+  }
+};
+
+// Per-point interpolation record, complex64 path: segment in the top 8 bits,
+// t in [0, 1) as a 24-bit fraction.  The segment table maps a segment to
+// (k_lo, k_hi); w_{k_lo} = 1 - t, w_{k_hi} = t.
+__device__ __forceinline__ void decode_rec(uint32_t rec, int& seg, float& t) {
+  seg = int(rec >> 24);
+  t = float(rec & 0xFFFFFFu) * (1.0f / 16777216.0f);
+}
+__device__ __forceinline__ void decode_rec(double rec, int& seg, double& t) {
+  seg = int(rec);
+  t = rec - double(seg);
+}
+
+template <typename R> struct RecT;
+template <> struct RecT<float> { using T = uint32_t; };
+template <> struct RecT<double> { using T = double; };
+
+// ---------------------------------------------------------------------------
+// Forward FFT along x.  in: c128 rows (row gr at gr * N); scale[rhs] (or
+// NULL) multiplies the input; out: working-precision rows.
+// ---------------------------------------------------------------------------
+template <typename R, int N>
+__global__ void __launch_bounds__(LineCfg<R, N>::ROW_THREADS)
+row_fwd_kernel(const double2* __restrict__ in, const double* __restrict__ scale,
+               long rows_per_rhs, long nrows, const typename cvec<R>::T* __restrict__ tw,
+               typename cvec<R>::T* __restrict__ out) {
+  using V = typename cvec<R>::T;
+  using F = LineFFT<R, N, -1>;
+  constexpr int TPL = F::TPL, E = F::E, LPB = LineCfg<R, N>::ROW_LINES;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sm = reinterpret_cast<V*>(smem_raw);
+  const int li = threadIdx.x / TPL, t = threadIdx.x % TPL;
+  const long row = long(blockIdx.x) * LPB + li;
+  const bool valid = row < nrows;
+  V* line = sm + li * padded_len(N);
+  V x[E];
+  double s = 1.0;
+  if (valid && scale) s = scale[row / rows_per_rhs];
+  const double2* src = in + row * N;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    double2 v = valid ? src[F::stage0_index(t, e)] : make_double2(0.0, 0.0);
+    x[e] = cmk<V>(R(v.x * s), R(v.y * s));
+  }
+  F::run(line, t, x, tw);
+  if (valid) {
+    V* dst = out + row * N;
+#pragma unroll
+    for (int i = 0; i < E; ++i) dst[t + i * TPL] = line[padded(t + i * TPL)];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse FFT along x of the K planes and the weighted sum.
+// planes: [rhs][K][n]; rec: per-point record (shared by all rhs); segtab:
+// (k_lo, k_hi) per segment; rowmask[row % rows_per_rhs] bit k = some point of
+// the row has a non-zero weight on node k (only those planes were written).
+// out[rhs][n] = inv_n * sum_k w_k plane_k.
+// ---------------------------------------------------------------------------
+template <typename R, int N, typename OutT>
+__global__ void __launch_bounds__(LineCfg<R, N>::ROW_THREADS)
+row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
+                   const typename RecT<R>::T* __restrict__ rec, const uchar2* __restrict__ segtab,
+                   int nseg, const unsigned long long* __restrict__ rowmask, int K,
+                   long rows_per_rhs, long nrows, long n, R inv_n,
+                   const typename cvec<R>::T* __restrict__ tw, OutT* __restrict__ out) {
+  using V = typename cvec<R>::T;
+  using F = LineFFT<R, N, +1>;
+  constexpr int TPL = F::TPL, E = F::E, LPB = LineCfg<R, N>::ROW_LINES;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sm = reinterpret_cast<V*>(smem_raw);
+  __shared__ uchar2 seg_s[HZ_MAX_SEG];
+  __shared__ unsigned long long cta_mask;
+  for (int i = threadIdx.x; i < nseg; i += blockDim.x) seg_s[i] = segtab[i];
+  const int li = threadIdx.x / TPL, t = threadIdx.x % TPL;
+  const long row = long(blockIdx.x) * LPB + li;
+  const bool valid = row < nrows;
+  const long rhs = valid ? row / rows_per_rhs : 0;
+  const long lrow = valid ? row - rhs * rows_per_rhs : 0;
+  unsigned long long mymask = valid ? rowmask[lrow] : 0ull;
+  if (threadIdx.x == 0) cta_mask = 0ull;
+  __syncthreads();
+  if (t == 0 && mymask) atomicOr(&cta_mask, mymask);
+  V* line = sm + li * padded_len(N);
+  typename RecT<R>::T r_[E];
+  V acc[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    r_[i] = valid ? rec[lrow * N + t + i * TPL] : typename RecT<R>::T(0);
+    acc[i] = cmk<V>(R(0), R(0));
+  }
+  __syncthreads();
+  const unsigned long long cm = cta_mask;
+  const V* pbase = planes + (rhs * K) * n + lrow * N;
+  for (int k = 0; k < K; ++k) {
+    if (!((cm >> k) & 1ull)) continue;  // uniform over the block
+    const bool need = (mymask >> k) & 1ull;
+    V x[E];
+    const V* src = pbase + long(k) * n;
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = need ? src[F::stage0_index(t, e)] : cmk<V>(R(0), R(0));
+    __syncthreads();  // previous plane's results have been read
+    F::run(line, t, x, tw);
+    if (need) {
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        int seg;
+        R tf;
+        decode_rec(r_[i], seg, tf);
+        const uchar2 kk = seg_s[seg];
+        R w = R(0);
+        if (kk.x == k) w += R(1) - tf;
+        if (kk.y == k) w += tf;
+        if (w != R(0)) {
+          const V v = line[padded(t + i * TPL)];
+          acc[i].x += w * v.x;
+          acc[i].y += w * v.y;
+        }
+      }
+    }
+  }
+  if (valid) {
+    OutT* dst = out + rhs * n + lrow * N;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      OutT o;
+      o.x = acc[i].x * inv_n;
+      o.y = acc[i].y * inv_n;
+      dst[t + i * TPL] = o;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Strided-axis kernels.  A line has N elements at stride S; a block handles
+// TB lines at adjacent x (thread = t * TB + column) so that loads and stores
+// move TB contiguous elements.  Line (x, o, b) starts at
+//   b * bstride + o * ostride + x.
+// grid.x = ceil(nx / TB) * outer, grid.z = batch (times K splits for fused).
+// ---------------------------------------------------------------------------
+template <typename R, int N, int SIGN>
+__global__ void __launch_bounds__(LineCfg<R, N>::COL_THREADS)
+line_pass_kernel(typename cvec<R>::T* __restrict__ data, int nx, int ntile, long S, long ostride,
+                 long bstride, const unsigned long long* __restrict__ omask, int K,
+                 const typename cvec<R>::T* __restrict__ tw) {
+  using V = typename cvec<R>::T;
+  using F = LineFFT<R, N, SIGN>;
+  constexpr int TPL = F::TPL, E = F::E, TB = LineCfg<R, N>::TB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sm = reinterpret_cast<V*>(smem_raw);
+  const int col = threadIdx.x % TB, t = threadIdx.x / TB;
+  const int tile = blockIdx.x % ntile;
+  const long o = blockIdx.x / ntile;
+  const int x = tile * TB + col;
+  const bool valid = x < nx;
+  // omask (planes only): skip outer slices o that no row of plane k needs
+  if (omask && !((omask[o] >> (blockIdx.z % K)) & 1ull)) return;
+  V* base = data + long(blockIdx.z) * bstride + o * ostride + x;
+  V* line = sm + col * padded_len(N);
+  V v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = valid ? base[long(F::stage0_index(t, e)) * S] : cmk<V>(R(0), R(0));
+  F::run(line, t, v, tw);
+  if (valid) {
+#pragma unroll
+    for (int i = 0; i < E; ++i) base[long(t + i * TPL) * S] = line[padded(t + i * TPL)];
+  }
+}
+
+// Last-axis fused kernel.  in: forward transform along every other axis
+// ([rhs][n]); planes out: [rhs][K][n].  xi2_x[x] + xi2_o[o] + xi2_l[p] is
+// |xi|^2 at (x, o, p).  Block (tile, o) of K-split ks handles nodes
+// k = ks, ks + nks, ...  Plane k is only stored where smask[o smO + p smS]
+// has bit k: per row in 2D (the next pass is the x inverse), per z-slab in 3D
+// (the next pass is the y inverse, which needs the whole slab).
+template <typename R, int N>
+__global__ void __launch_bounds__(LineCfg<R, N>::COL_THREADS)
+line_fused_kernel(const typename cvec<R>::T* __restrict__ in, typename cvec<R>::T* __restrict__ planes,
+                  int nx, int ntile, long S, long ostride, long n, int K, int nks,
+                  const R* __restrict__ xi2_x, const R* __restrict__ xi2_o,
+                  const R* __restrict__ xi2_l, const typename cvec<R>::T* __restrict__ symA,
+                  const typename cvec<R>::T* __restrict__ symG,
+                  const unsigned long long* __restrict__ smask, long smO, long smS,
+                  const typename cvec<R>::T* __restrict__ tw) {
+  using V = typename cvec<R>::T;
+  using Ff = LineFFT<R, N, -1>;
+  using Fi = LineFFT<R, N, +1>;
+  constexpr int TPL = Ff::TPL, E = Ff::E, TB = LineCfg<R, N>::TB;
+  constexpr bool SPEC_REGS = sizeof(R) == 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sm = reinterpret_cast<V*>(smem_raw);
+  const int col = threadIdx.x % TB, t = threadIdx.x / TB;
+  const int tile = blockIdx.x % ntile;
+  const long o = blockIdx.x / ntile;
+  const int x = tile * TB + col;
+  const bool valid = x < nx;
+  const long rhs = blockIdx.z / nks;
+  const int ks = blockIdx.z % nks;
+  const long off = o * ostride + x;
+  const V* src = in + rhs * n + off;
+  V* line = sm + col * padded_len(N);
+  V* specs = sm + (TB + col) * padded_len(N);  // used when !SPEC_REGS
+  V v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = valid ? src[long(Ff::stage0_index(t, e)) * S] : cmk<V>(R(0), R(0));
+  Ff::run(line, t, v, tw);
+  // the spectrum in the inverse transform's stage-0 order, and |xi|^2 there
+  V spec[SPEC_REGS ? E : 1];
+  R s2[E];
+  const R sxo = (valid ? xi2_x[x] : R(0)) + (xi2_o ? xi2_o[o] : R(0));
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int p = Fi::stage0_index(t, e);
+    if constexpr (SPEC_REGS) spec[e] = line[padded(p)];
+    else specs[padded(p)] = line[padded(p)];
+    s2[e] = sxo + xi2_l[p];
+  }
+  for (int k = ks; k < K; k += nks) {
+    const V A = symA[k], G = symG[k];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int p = Fi::stage0_index(t, e);
+      const V sv = SPEC_REGS ? spec[SPEC_REGS ? e : 0] : specs[padded(p)];
+      // q = 1 / (A - G s) = conj(den) / |den|^2
+      const V den = cmk<V>(A.x - G.x * s2[e], A.y - G.y * s2[e]);
+      const R inv = R(1) / (den.x * den.x + den.y * den.y);
+      const V q = cmk<V>(den.x * inv, -den.y * inv);
+      v[e] = cmul(sv, q);
+    }
+    __syncthreads();  // every thread is done reading the previous result
+    Fi::run(line, t, v, tw);
+    if (valid) {
+      V* dst = planes + (rhs * K + k) * n + off;
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int p = t + i * TPL;
+        if ((smask[o * smO + long(p) * smS] >> k) & 1ull) dst[long(p) * S] = line[padded(p)];
+      }
+    }
+  }
+}
+
+}  // namespace hz

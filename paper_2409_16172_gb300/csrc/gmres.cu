@@ -1,0 +1,286 @@
+// Restarted (F)GMRES(m) driver (Section 5, "GMRES implementation"):
+//   r = f - P_N u;  v_0 = r / ||r||;  for j < m:
+//     z_j = Q_M v_j                          (complex64 or complex128 apply)
+//     w   = P_N z_j                          (FP64 stencil)
+//     CGS2: h = V^H w, w -= V h; h' = V^H w, w -= V h'; h += h'
+//     h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}
+//     Givens rotation of column j, residual estimate |g_{j+1}|
+//   u += Z y (flexible, precision 1) or u += Q_M (V y) (precision 0),
+//   then the true FP64 residual decides whether to stop or restart.
+// All right-hand sides of a call advance in lock step; each one retires on
+// its own device-side flag.  The host waits on the device once per Arnoldi
+// step (one step behind the launches) and once per cycle.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <complex>
+#include <vector>
+
+#include "hz_internal.h"
+#include "kernels.h"
+
+namespace hz {
+hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* scale, int nrhs,
+                        void* out, int out_kind, cudaStream_t st);
+}
+
+using namespace hz;
+
+namespace {
+
+bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct SolveWork {
+  DevArena ar;
+  KsDev ks{};
+  double* rnorm2 = nullptr;    // [B]
+  double2* y = nullptr;        // [B][m]
+  int* h_nact = nullptr;       // pinned, 2 slots
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  ~SolveWork() {
+    ar.release();
+    if (h_nact) cudaFreeHost(h_nact);
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+  }
+};
+
+}  // namespace
+
+extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs,
+                                    hz_solve_stats* stats, void* stream) {
+  if (!plan || !f_in || !u_io) return set_error(HZ_ERR_INVALID_ARG, "null argument");
+  if (nrhs < 1 || nrhs > plan->max_nrhs) return set_error(HZ_ERR_INVALID_ARG, "nrhs out of range");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hz_plan* p = plan;
+  const hz_medium* med = p->med;
+  const long n = med->n;
+  const int m = p->opts.restart;
+  const int B = p->max_nrhs;
+  const int prec = p->opts.precision;
+  const double tol = p->opts.tol;
+  const long ldb = B;  // basis vector i of rhs b at V + (i * B + b) * n
+
+  SolveWork w;
+  KsDev& ks = w.ks;
+  ks.m = m;
+  ks.ldsig = B;
+  ks.tol = tol;
+  HZ_TRY(w.ar.alloc(&ks.H, size_t(B) * m * (m + 1)));
+  HZ_TRY(w.ar.alloc(&ks.S1, size_t(B) * (m + 1)));
+  HZ_TRY(w.ar.alloc(&ks.S2, size_t(B) * (m + 1)));
+  HZ_TRY(w.ar.alloc(&ks.sigma, size_t(B) * (m + 1)));
+  HZ_TRY(w.ar.alloc(&ks.nrm2, B));
+  HZ_TRY(w.ar.alloc(&ks.cs, size_t(B) * m));
+  HZ_TRY(w.ar.alloc(&ks.sn, size_t(B) * m));
+  HZ_TRY(w.ar.alloc(&ks.g, size_t(B) * (m + 1)));
+  HZ_TRY(w.ar.alloc(&ks.est, B));
+  HZ_TRY(w.ar.alloc(&ks.bnorm, B));
+  HZ_TRY(w.ar.alloc(&ks.jend, B));
+  HZ_TRY(w.ar.alloc(&ks.active, B));
+  HZ_TRY(w.ar.alloc(&ks.status, B));
+  HZ_TRY(w.ar.alloc(&ks.n_active, 1));
+  HZ_TRY(w.ar.alloc(&w.rnorm2, B));
+  HZ_TRY(w.ar.alloc(&w.y, size_t(B) * m));
+  HZ_CUDA(cudaMallocHost(&w.h_nact, 2 * sizeof(int)));
+  for (auto& e : w.ev) HZ_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  HZ_CUDA(cudaEventCreate(&w.t0));
+  HZ_CUDA(cudaEventCreate(&w.t1));
+  HZ_CUDA(cudaEventRecord(w.t0, st));
+
+  // stage f and u
+  const bool f_dev = is_device_ptr(f_in), u_dev = is_device_ptr(u_io);
+  const double2* f = f_dev ? static_cast<const double2*>(f_in) : p->f;
+  double2* u = u_dev ? static_cast<double2*>(u_io) : p->u;
+  const size_t vbytes = size_t(nrhs) * n * sizeof(double2);
+  if (!f_dev) HZ_CUDA(cudaMemcpyAsync(p->f, f_in, vbytes, cudaMemcpyHostToDevice, st));
+  if (!u_dev) HZ_CUDA(cudaMemcpyAsync(p->u, u_io, vbytes, cudaMemcpyHostToDevice, st));
+
+  const int nblk_r = stencil_blocks(n);
+  const int nblk_k = krylov_blocks(n, nrhs, (m + 1 + 7) / 8);
+  const int nblk_n = krylov_blocks(n, nrhs, 1);
+  HZ_TRY(launch_norm2(f, n, n, nrhs, p->partial, nblk_n, ks.bnorm, st));
+  std::vector<double> bnorm(nrhs), rn2(nrhs);
+  HZ_CUDA(cudaMemcpyAsync(bnorm.data(), ks.bnorm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+  HZ_CUDA(cudaStreamSynchronize(st));
+  for (auto& b : bnorm) b = std::sqrt(b);
+  HZ_CUDA(cudaMemcpyAsync(ks.bnorm, bnorm.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+
+  std::vector<int> done(nrhs, 0), conv(nrhs, 0), iters(nrhs, 0), restarts(nrhs, 0),
+      status(nrhs, HZ_OK);
+  std::vector<double> rel(nrhs, 0.0), est(nrhs, 0.0);
+  for (int b = 0; b < nrhs; ++b) {
+    if (bnorm[b] == 0.0) {  // the solution is zero
+      HZ_CUDA(cudaMemsetAsync(u + long(b) * n, 0, n * sizeof(double2), st));
+      done[b] = conv[b] = 1;
+    }
+  }
+  std::vector<int> h_active(nrhs), h_jend(nrhs), h_status(nrhs);
+  std::vector<double> h_sigma0(B, 0.0);
+  std::vector<double2> h_g(size_t(nrhs) * (m + 1)), h_H(size_t(nrhs) * m * (m + 1)), h_y(size_t(B) * m);
+  std::vector<double> h_est(nrhs);
+  int total_iters = 0;
+
+  for (;;) {
+    // true FP64 residual r = f - P u into V_0
+    HZ_TRY(launch_residual(med, u, f, p->V, n, nrhs, nullptr, p->partial, st));
+    HZ_TRY(launch_reduce_r(p->partial, nblk_r, nrhs, w.rnorm2, st));
+    HZ_CUDA(cudaMemcpyAsync(rn2.data(), w.rnorm2, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HZ_CUDA(cudaStreamSynchronize(st));
+    int live = 0;
+    for (int b = 0; b < nrhs; ++b) {
+      if (bnorm[b] == 0.0) continue;
+      rel[b] = std::sqrt(rn2[b]) / bnorm[b];
+      if (done[b]) continue;
+      if (!std::isfinite(rel[b])) {
+        done[b] = 1;
+        status[b] = HZ_ERR_BREAKDOWN;
+      } else if (rel[b] <= tol) {
+        done[b] = conv[b] = 1;
+      } else if (iters[b] >= p->opts.maxit) {
+        done[b] = 1;
+        status[b] = HZ_ERR_NOT_CONVERGED;
+      }
+      live += !done[b];
+    }
+    if (!live) break;
+
+    // start a cycle for the live right-hand sides
+    std::fill(h_g.begin(), h_g.end(), make_double2(0.0, 0.0));
+    for (int b = 0; b < nrhs; ++b) {
+      h_active[b] = !done[b];
+      const double r = std::sqrt(rn2[b]);
+      h_sigma0[b] = (!done[b] && r > 0) ? 1.0 / r : 0.0;
+      h_g[size_t(b) * (m + 1)] = make_double2(done[b] ? 0.0 : r, 0.0);
+      h_status[b] = HZ_OK;
+    }
+    HZ_CUDA(cudaMemcpyAsync(ks.active, h_active.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+    HZ_CUDA(cudaMemcpyAsync(ks.status, h_status.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+    HZ_CUDA(cudaMemcpyAsync(ks.sigma, h_sigma0.data(), B * sizeof(double), cudaMemcpyHostToDevice, st));
+    HZ_CUDA(cudaMemcpyAsync(ks.g, h_g.data(), h_g.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    HZ_CUDA(cudaMemsetAsync(ks.jend, 0, nrhs * sizeof(int), st));
+    HZ_CUDA(cudaMemcpyAsync(ks.n_active, &live, sizeof(int), cudaMemcpyHostToDevice, st));
+    HZ_CUDA(cudaStreamSynchronize(st));  // host vectors above are reused next cycle
+
+    int maxit_left = 0;
+    for (int b = 0; b < nrhs; ++b)
+      if (!done[b]) maxit_left = std::max(maxit_left, p->opts.maxit - iters[b]);
+    const int jmax = std::min(m, maxit_left);
+    for (int j = 0; j < jmax; ++j) {
+      const double2* Vj = p->V + long(j) * ldb * n;
+      double2* Vn = p->V + long(j + 1) * ldb * n;
+      const double* sig_j = ks.sigma + long(j) * B;
+      if (prec == 1) {
+        float2* Zj = static_cast<float2*>(p->Z) + long(j) * ldb * n;
+        HZ_TRY(precond_apply(p, 1, Vj, sig_j, nrhs, Zj, 0, st));
+        HZ_TRY(launch_stencil(med, 1, Zj, n, Vn, n, nrhs, ks.active, st));
+      } else {
+        double2* zt = static_cast<double2*>(p->Z);
+        HZ_TRY(precond_apply(p, 0, Vj, sig_j, nrhs, zt, 1, st));
+        HZ_TRY(launch_stencil(med, 0, zt, n, Vn, n, nrhs, ks.active, st));
+      }
+      // CGS2
+      HZ_TRY(launch_dots(p->V, ldb, Vn, n, n, j, nrhs, ks.active, reinterpret_cast<double2*>(p->partial),
+                         nblk_k, ks.S1, m + 1, st));
+      HZ_TRY(launch_update(p->V, ldb, Vn, n, n, j, nrhs, ks.S1, m + 1, ks.sigma, B, ks.active, false,
+                           nullptr, nblk_k, nullptr, st));
+      HZ_TRY(launch_dots(p->V, ldb, Vn, n, n, j, nrhs, ks.active, reinterpret_cast<double2*>(p->partial),
+                         nblk_k, ks.S2, m + 1, st));
+      HZ_TRY(launch_update(p->V, ldb, Vn, n, n, j, nrhs, ks.S2, m + 1, ks.sigma, B, ks.active, true,
+                           p->partial, nblk_k, ks.nrm2, st));
+      HZ_TRY(launch_givens(ks, j, nrhs, st));
+      HZ_CUDA(cudaMemcpyAsync(&w.h_nact[j & 1], ks.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+      HZ_CUDA(cudaEventRecord(w.ev[j & 1], st));
+      if (j >= 1) {
+        HZ_CUDA(cudaEventSynchronize(w.ev[(j - 1) & 1]));
+        if (w.h_nact[(j - 1) & 1] == 0) break;
+      }
+    }
+    HZ_CUDA(cudaMemcpyAsync(h_jend.data(), ks.jend, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
+    HZ_CUDA(cudaMemcpyAsync(h_status.data(), ks.status, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
+    HZ_CUDA(cudaMemcpyAsync(h_est.data(), ks.est, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HZ_CUDA(cudaMemcpyAsync(h_H.data(), ks.H, h_H.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    HZ_CUDA(cudaMemcpyAsync(h_g.data(), ks.g, h_g.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    HZ_CUDA(cudaStreamSynchronize(st));
+
+    // back substitution R y = g on the host (m <= 128)
+    std::fill(h_y.begin(), h_y.end(), make_double2(0.0, 0.0));
+    std::vector<int> jn(nrhs, 0);
+    for (int b = 0; b < nrhs; ++b) {
+      if (done[b]) continue;
+      const int J = h_jend[b];
+      jn[b] = J;
+      iters[b] += J;
+      restarts[b] += 1;
+      est[b] = h_est[b] / bnorm[b];
+      if (h_status[b] != HZ_OK) {
+        status[b] = h_status[b];
+        done[b] = 1;
+        jn[b] = 0;
+        continue;
+      }
+      std::vector<std::complex<double>> yy(J);
+      auto Hc = [&](int i, int jj) {
+        const double2 v = h_H[(size_t(b) * m + jj) * (m + 1) + i];
+        return std::complex<double>(v.x, v.y);
+      };
+      for (int i = J - 1; i >= 0; --i) {
+        std::complex<double> s(h_g[size_t(b) * (m + 1) + i].x, h_g[size_t(b) * (m + 1) + i].y);
+        for (int k = i + 1; k < J; ++k) s -= Hc(i, k) * yy[k];
+        yy[i] = s / Hc(i, i);
+      }
+      for (int i = 0; i < J; ++i) h_y[size_t(b) * m + i] = make_double2(yy[i].real(), yy[i].imag());
+    }
+    total_iters += *std::max_element(jn.begin(), jn.end());
+    int* d_jn = ks.jend;  // reuse: per-rhs number of columns to add (0 = skip)
+    HZ_CUDA(cudaMemcpyAsync(d_jn, jn.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+    HZ_CUDA(cudaMemcpyAsync(w.y, h_y.data(), size_t(nrhs) * m * sizeof(double2), cudaMemcpyHostToDevice, st));
+    if (prec == 1) {
+      HZ_TRY(launch_solution_update(1, p->Z, ldb, u, n, n, nrhs, w.y, m, d_jn, st));
+    } else {
+      // t = V (sigma y), then u += Q_M t in complex128
+      double2* t = p->V + long(m) * ldb * n;  // V_m is free once the cycle is over
+      HZ_TRY(launch_combine(p->V, ldb, t, n, n, nrhs, w.y, m, ks.sigma, B, d_jn, st));
+      double2* zt = static_cast<double2*>(p->Z);
+      HZ_TRY(precond_apply(p, 0, t, nullptr, nrhs, zt, 1, st));
+      HZ_TRY(launch_axpy(u, zt, n, n, nrhs, d_jn, st));
+    }
+    HZ_CUDA(cudaStreamSynchronize(st));
+  }
+
+  if (!u_dev) HZ_CUDA(cudaMemcpyAsync(u_io, p->u, vbytes, cudaMemcpyDeviceToHost, st));
+  HZ_CUDA(cudaEventRecord(w.t1, st));
+  HZ_CUDA(cudaEventSynchronize(w.t1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, w.t0, w.t1);
+  hz_status ret = HZ_OK;
+  for (int b = 0; b < nrhs; ++b) {
+    if (stats) {
+      stats[b].iters = iters[b];
+      stats[b].restarts = restarts[b];
+      stats[b].status = conv[b] ? HZ_OK : (status[b] == HZ_OK ? HZ_ERR_NOT_CONVERGED : status[b]);
+      stats[b].converged = conv[b];
+      stats[b].rel_true_resid = rel[b];
+      stats[b].rel_est_resid = est[b];
+      stats[b].ms_total = ms;
+    }
+    if (!conv[b]) {
+      const hz_status sb = status[b] == HZ_OK ? HZ_ERR_NOT_CONVERGED : hz_status(status[b]);
+      if (ret == HZ_OK || sb == HZ_ERR_BREAKDOWN) ret = sb;
+    }
+  }
+  (void)total_iters;
+  if (ret != HZ_OK) set_error(ret, "%s", ret == HZ_ERR_BREAKDOWN ? "Krylov breakdown (NaN/Inf)" : "not converged within maxit");
+  return ret;
+}

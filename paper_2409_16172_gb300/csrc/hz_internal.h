@@ -1,0 +1,150 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hz.h"
+
+#define HZ_MAX_K 64     // symbol planes (node bit masks are 64-bit)
+#define HZ_MAX_SEG 72   // interpolation segments incl. the two end entries
+#define HZ_MAX_RESTART 128
+
+namespace hz {
+
+hz_status set_error(hz_status st, const char* fmt, ...);
+hz_status cuda_error(cudaError_t e, const char* what);
+
+#define HZ_CUDA(call)                                            \
+  do {                                                           \
+    cudaError_t e_ = (call);                                     \
+    if (e_ != cudaSuccess) return ::hz::cuda_error(e_, #call);   \
+  } while (0)
+
+#define HZ_TRY(call)                         \
+  do {                                       \
+    hz_status s_ = (call);                   \
+    if (s_ != HZ_OK) return s_;              \
+  } while (0)
+
+void* dev_alloc(size_t bytes);
+void dev_free(void* p);
+
+// RAII list of device allocations owned by a medium or plan.
+struct DevArena {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  template <typename T>
+  hz_status alloc(T** out, size_t count) {
+    size_t b = count * sizeof(T);
+    if (b == 0) b = 16;
+    void* p = dev_alloc(b);
+    if (!p) return set_error(HZ_ERR_OOM, "device allocation of %zu bytes failed", b);
+    ptrs.push_back(p);
+    bytes += b;
+    *out = static_cast<T*>(p);
+    return HZ_OK;
+  }
+  void release() {
+    for (void* p : ptrs) dev_free(p);
+    ptrs.clear();
+    bytes = 0;
+  }
+};
+
+// Supported axis lengths.
+bool fft_size_supported(int N);
+
+// Per-axis tables for one FFT length.
+struct AxisTables {
+  int N = 0;
+  double2* tw64 = nullptr;  // exp(-2 pi i j / N)
+  float2* tw32 = nullptr;
+  double* xi2_64 = nullptr;  // squared wavenumber per bin
+  float* xi2_32 = nullptr;
+};
+
+}  // namespace hz
+
+struct hz_medium {
+  int dim = 2;
+  int nx = 0, ny = 1, nz = 1;
+  long n = 0;
+  double L = 1.0, omega = 0.0;
+  hz_interp interp{};
+  // node table
+  int K = 0, M = 0, Mt = 0, m_o = -1;
+  double c_min = 0, c_max = 0, zeta_max = 0;
+  std::vector<double> gamma_re, gamma_im, a_k, c_real, zeta_nodes;
+  int nseg = 0;
+  std::vector<uchar2> segtab_h;
+  // device data
+  hz::DevArena arena;
+  double2* gamma2 = nullptr;        // per point gamma^2 (Eqn. Complex_wave_speed squared)
+  double* a = nullptr;              // per point operator damping (NULL when a == 0)
+  double* rec64 = nullptr;          // per point segment + t (complex128 path)
+  uint32_t* rec32 = nullptr;        // per point segment:8 | t:24 (complex64 path)
+  unsigned long long* rowmask = nullptr;   // per x-row: nodes with a non-zero weight
+  unsigned long long* slabmask = nullptr;  // 3D: per z-slab OR of its rows
+  uchar2* segtab = nullptr;
+  double2* symA64 = nullptr;        // w^2 + i w a_k
+  double2* symG64 = nullptr;        // gamma_k^2
+  float2* symA32 = nullptr;
+  float2* symG32 = nullptr;
+  hz::AxisTables ax[3];
+  double inv_h2[3] = {0, 0, 0};
+};
+
+namespace hz {
+
+// Launchers of the FFT passes for one axis length N (one translation unit per
+// N, see fft_inst.cu).  V = float2 (prec 1) or double2 (prec 0).
+struct FftOps {
+  int N;
+  // forward FFT along x, c128 input (optionally scaled per rhs)
+  hz_status (*row_fwd)(int prec, const double2* in, const double* scale, long rows_per_rhs,
+                       long nrows, const void* tw, void* out, cudaStream_t st);
+  // inverse FFT along x of the K planes + weighted sum; out_kind 0: c64, 1: c128
+  hz_status (*row_inv_acc)(int prec, int out_kind, const void* planes, const void* rec,
+                           const uchar2* segtab, int nseg, const unsigned long long* rowmask,
+                           int K, long rows_per_rhs, long nrows, long n, double inv_n,
+                           const void* tw, void* out, cudaStream_t st);
+  // FFT along a strided axis, in place; sign -1 forward, +1 inverse
+  hz_status (*line_pass)(int prec, int sign, void* data, int nx, long outer, long S,
+                         long ostride, long bstride, int batch,
+                         const unsigned long long* omask, int K, const void* tw,
+                         cudaStream_t st);
+  // last-axis fused forward * symbol * inverse
+  hz_status (*line_fused)(int prec, const void* in, void* planes, int nx, long outer, long S,
+                          long ostride, long n, int K, int batch, const void* xi2_x,
+                          const void* xi2_o, const void* xi2_l, const void* symA,
+                          const void* symG, const unsigned long long* smask, long smO,
+                          long smS, const void* tw, cudaStream_t st);
+};
+
+const FftOps* fft_ops(int N);
+
+}  // namespace hz
+
+struct hz_plan {
+  hz_medium* med = nullptr;
+  hz_solver_opts opts{};
+  int max_nrhs = 1;
+  hz::DevArena arena;
+  // preconditioner workspace
+  void* tmp = nullptr;     // working-precision transform of the input [max_nrhs][n]
+  void* planes = nullptr;  // [max_nrhs][K][n] in the working precision
+  int planes_prec = 1;     // precision the planes buffer is sized for (0 = c128)
+  // Krylov workspace (FP64)
+  double2* V = nullptr;    // [(m+1)][max_nrhs][n] unnormalised basis vectors
+  void* Z = nullptr;       // [m][max_nrhs][n] preconditioned vectors (c64 or unused)
+  double2* u = nullptr;    // staged solution for host buffers [max_nrhs][n]
+  double2* f = nullptr;    // staged right-hand side for host buffers
+  double* partial = nullptr;     // block partial sums
+  size_t partial_len = 0;
+  double2* hcol = nullptr;       // [max_nrhs][m+2] current Hessenberg column sums
+  double* nrm2 = nullptr;        // [max_nrhs] squared norms
+  struct Ks* ks = nullptr;       // device-side small Krylov state
+};

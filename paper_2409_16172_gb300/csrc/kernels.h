@@ -1,0 +1,57 @@
+// Launchers of the non-FFT kernels (stencil.cu, krylov.cu).
+#pragma once
+#include "hz_internal.h"
+
+namespace hz {
+
+// Device-side small Krylov state, one entry per right-hand side b.
+struct KsDev {
+  int m;            // restart length
+  int ldsig;        // leading dimension of sigma ([i][b])
+  double tol;
+  double2* H;       // [b][j][m+1] rotated Hessenberg columns (R factor)
+  double2* S1;      // [b][m+1] first CGS sums
+  double2* S2;      // [b][m+1] second CGS sums
+  double* sigma;    // [i][b] scale of stored basis vector i
+  double* nrm2;     // [b] |w|^2 after the second pass
+  double* cs;       // [b][m] rotation cosines
+  double2* sn;      // [b][m] rotation sines
+  double2* g;       // [b][m+1] rotated right-hand side
+  double* est;      // [b] |g_{j+1}|
+  double* bnorm;    // [b] ||f||
+  int* jend;        // [b] columns built in this cycle
+  int* active;      // [b] 1 while the cycle continues
+  int* status;      // [b] hz_status
+  int* n_active;    // number of active right-hand sides
+};
+
+int stencil_blocks(long n);
+hz_status launch_stencil(const hz_medium* m, int in_prec, const void* x, long in_stride,
+                         double2* y, long out_stride, int nrhs, const int* active,
+                         cudaStream_t st);
+hz_status launch_residual(const hz_medium* m, const double2* u, const double2* f, double2* r,
+                          long stride, int nrhs, const int* active, double* partial,
+                          cudaStream_t st);
+
+int krylov_blocks(long n, int nrhs, int nchunk);
+hz_status launch_dots(const double2* V, long ldb, const double2* w, long wstride, long n, int j,
+                      int nrhs, const int* active, double2* partial, int nblk, double2* S, int ldS,
+                      cudaStream_t st);
+hz_status launch_update(const double2* V, long ldb, double2* w, long wstride, long n, int j,
+                        int nrhs, const double2* S, int ldS, const double* sigma, int ldsig,
+                        const int* active, bool norm, double* partial, int nblk, double* nrm2,
+                        cudaStream_t st);
+hz_status launch_givens(const KsDev& ks, int j, int nrhs, cudaStream_t st);
+hz_status launch_solution_update(int zprec, const void* Z, long ldb, double2* u, long ustride,
+                                 long n, int nrhs, const double2* y, int ldy, const int* jn,
+                                 cudaStream_t st);
+hz_status launch_combine(const double2* V, long ldb, double2* out, long ostride, long n, int nrhs,
+                         const double2* y, int ldy, const double* sigma, int ldsig, const int* jn,
+                         cudaStream_t st);
+hz_status launch_axpy(double2* u, const double2* t, long stride, long n, int nrhs, const int* jn,
+                      cudaStream_t st);
+hz_status launch_norm2(const double2* x, long stride, long n, int nrhs, double* partial, int nblk,
+                       double* out, cudaStream_t st);
+hz_status launch_reduce_r(const double* partial, int nblk, int nq, double* out, cudaStream_t st);
+
+}  // namespace hz

@@ -1,0 +1,439 @@
+// Medium set-up (plan time): validation, the node table of Section 4.1 /
+// Section 4.4, per-point interpolation records of Eqn. 405, gamma^2 of
+// Eqn. Complex_wave_speed, row / slab node masks, FFT twiddles and the
+// per-axis |xi|^2 tables.
+#include <math.h>
+#include <stdarg.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "hz_internal.h"
+
+namespace hz {
+namespace {
+
+constexpr int VAL_THREADS = 256;
+
+struct ValPartial {
+  double cmin, cmax, zmax;
+  unsigned long long bad_c, bad_zeta, bad_layer, bad_a;
+};
+
+// One pass over the medium: min/max of c, max of zeta and counts of the
+// points that violate Section 3 (c > 0, finite) and Section 4.4 (zeta >= 0,
+// c = c_o where zeta > 0).
+__global__ void validate_kernel(const double* __restrict__ c, const double* __restrict__ zeta,
+                                const double* __restrict__ a, long n, double c_o,
+                                ValPartial* __restrict__ part) {
+  double cmin = INFINITY, cmax = -INFINITY, zmax = 0.0;
+  unsigned long long bc = 0, bz = 0, bl = 0, ba = 0;
+  for (long i = blockIdx.x * long(blockDim.x) + threadIdx.x; i < n; i += long(gridDim.x) * blockDim.x) {
+    const double ci = c[i];
+    const double zi = zeta ? zeta[i] : 0.0;
+    if (!(ci > 0.0) || !isfinite(ci)) {
+      ++bc;
+    } else {
+      cmin = fmin(cmin, ci);
+      cmax = fmax(cmax, ci);
+    }
+    if (!(zi >= 0.0) || !isfinite(zi)) ++bz;
+    else zmax = fmax(zmax, zi);
+    if (zi > 0.0 && fabs(ci - c_o) > 1e-12 * c_o) ++bl;
+    if (a && !isfinite(a[i])) ++ba;
+  }
+  __shared__ ValPartial sh[VAL_THREADS];
+  sh[threadIdx.x] = ValPartial{cmin, cmax, zmax, bc, bz, bl, ba};
+  __syncthreads();
+  for (int s = VAL_THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      ValPartial& p = sh[threadIdx.x];
+      const ValPartial& q = sh[threadIdx.x + s];
+      p.cmin = fmin(p.cmin, q.cmin);
+      p.cmax = fmax(p.cmax, q.cmax);
+      p.zmax = fmax(p.zmax, q.zmax);
+      p.bad_c += q.bad_c;
+      p.bad_zeta += q.bad_zeta;
+      p.bad_layer += q.bad_layer;
+      p.bad_a += q.bad_a;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+struct NodeDev {
+  double c_real[HZ_MAX_K];
+  double zeta_nodes[HZ_MAX_K + 1];
+  int M, Mt;
+  uchar2 seg[HZ_MAX_SEG];
+};
+
+// Per point: the hat segment and t of Eqn. 405 (real hats in c where
+// zeta = 0, hats in zeta on the layer segment where zeta > 0), gamma^2,
+// and the row mask bits of the nodes with a non-zero weight.
+__global__ void record_kernel(const double* __restrict__ c, const double* __restrict__ zeta,
+                              long n, int nx, NodeDev nd, double* __restrict__ rec64,
+                              uint32_t* __restrict__ rec32, double2* __restrict__ gamma2,
+                              unsigned long long* __restrict__ rowmask) {
+  const long i = blockIdx.x * long(blockDim.x) + threadIdx.x;
+  unsigned long long bits = 0ull;
+  long row = -1;
+  if (i < n) {
+    const double ci = c[i];
+    const double zi = zeta ? zeta[i] : 0.0;
+    int seg;
+    double t;
+    if (zi > 0.0) {
+      int m = 0;
+      while (m + 1 < nd.Mt && zi >= nd.zeta_nodes[m + 1]) ++m;
+      t = (zi - nd.zeta_nodes[m]) / (nd.zeta_nodes[m + 1] - nd.zeta_nodes[m]);
+      seg = nd.M + m;
+    } else if (nd.M == 1) {
+      seg = 0;
+      t = 0.0;
+    } else {
+      int m = 0;
+      while (m + 2 < nd.M && ci >= nd.c_real[m + 1]) ++m;
+      t = (ci - nd.c_real[m]) / (nd.c_real[m + 1] - nd.c_real[m]);
+      seg = m;
+    }
+    t = fmin(fmax(t, 0.0), 1.0);
+    const double r = double(seg) + t;
+    rec64[i] = r;
+    rec32[i] = uint32_t(llrint(r * 16777216.0));
+    const uchar2 kk = nd.seg[seg];
+    if (t < 1.0) bits |= 1ull << kk.x;
+    if (t > 0.0) bits |= 1ull << kk.y;
+    const double c2 = ci * ci;
+    gamma2[i] = make_double2(c2 * (1.0 - zi * zi), -2.0 * c2 * zi);
+    row = i / nx;
+  }
+  // OR the bits of the warp's points that share a row, then one atomic each
+  const unsigned full = __activemask();
+  const long row0 = __shfl_sync(full, row, 0);
+  const bool same = __all_sync(full, row == row0);
+  if (same && row0 >= 0) {
+    const unsigned lo = __reduce_or_sync(full, unsigned(bits & 0xFFFFFFFFull));
+    const unsigned hi = __reduce_or_sync(full, unsigned(bits >> 32));
+    if ((threadIdx.x & 31) == 0) atomicOr(&rowmask[row0], (unsigned long long)lo | ((unsigned long long)hi << 32));
+  } else if (row >= 0 && bits) {
+    atomicOr(&rowmask[row], bits);
+  }
+}
+
+// 3D: slabmask[z] = OR over y of rowmask[z * ny + y].
+__global__ void slab_kernel(const unsigned long long* __restrict__ rowmask, int ny, int nz,
+                            unsigned long long* __restrict__ slabmask) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= nz) return;
+  unsigned long long m = 0ull;
+  for (int y = 0; y < ny; ++y) m |= rowmask[long(z) * ny + y];
+  slabmask[z] = m;
+}
+
+// exp(-2 pi i j / N) with the angle reduced to the first quadrant so that
+// every entry is accurate to a few ulp.
+void twiddles(int N, std::vector<double2>& w) {
+  w.resize(N);
+  for (int j = 0; j < N; ++j) {
+    const int q = (4 * j) / N;          // quadrant (N is a multiple of 4)
+    const int r = j - q * (N / 4);
+    const double th = 2.0 * M_PI * double(r) / double(N);
+    const double c = std::cos(th), s = std::sin(th);
+    double cr, sr;  // cos/sin of 2 pi j / N
+    switch (q) {
+      case 0: cr = c; sr = s; break;
+      case 1: cr = -s; sr = c; break;
+      case 2: cr = -c; sr = -s; break;
+      default: cr = s; sr = -c; break;
+    }
+    w[j] = make_double2(cr, -sr);
+  }
+}
+
+void xi2_table(int N, double L, int kind, std::vector<double>& t) {
+  t.resize(N);
+  for (int k = 0; k < N; ++k) {
+    if (kind == 0) {
+      const int ks = (k <= (N - 1) / 2) ? k : k - N;
+      const double xi = 2.0 * M_PI * double(ks) / L;
+      t[k] = xi * xi;
+    } else {
+      const double h = L / N;
+      const double s = std::sin(M_PI * double(k) / double(N));
+      t[k] = 4.0 / (h * h) * s * s;
+    }
+  }
+}
+
+template <typename T>
+hz_status upload(DevArena& ar, T** d, const std::vector<T>& h) {
+  HZ_TRY(ar.alloc(d, h.size()));
+  HZ_CUDA(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return HZ_OK;
+}
+
+// Real nodes (Lemma 3: equispaced, c_1 = c_lo, c_M = c_hi).  With force_co
+// the background speed c_o is a node (Section 4.4): a c_o strictly inside
+// the range splits it into two equispaced segments of s1 and M-1-s1
+// intervals, s1 = clamp(round((M-1)(c_o-c_lo)/(c_hi-c_lo)), 1, M-2).
+hz_status real_nodes(double c_lo, double c_hi, int M, bool force_co, double c_o,
+                     std::vector<double>& out) {
+  out.clear();
+  if (M == 1) {
+    out.push_back(force_co ? c_o : c_lo);
+    return HZ_OK;
+  }
+  if (c_hi - c_lo <= 1e-12 * c_hi) {
+    out.push_back(c_lo);
+    return HZ_OK;
+  }
+  if (force_co && c_lo < c_o && c_o < c_hi) {
+    if (M < 3) return set_error(HZ_ERR_MEDIUM, "c_o inside (c_min, c_max) needs M >= 3");
+    int s1 = int(std::floor((M - 1) * (c_o - c_lo) / (c_hi - c_lo) + 0.5));
+    s1 = std::min(std::max(s1, 1), M - 2);
+    const int s2 = (M - 1) - s1;
+    for (int i = 0; i < s1; ++i) out.push_back(c_lo + (c_o - c_lo) * i / s1);
+    for (int i = 0; i < s2; ++i) out.push_back(c_o + (c_hi - c_o) * i / s2);
+    out.push_back(c_hi);
+    return HZ_OK;
+  }
+  for (int i = 0; i < M - 1; ++i) out.push_back(c_lo + (c_hi - c_lo) * i / (M - 1));
+  out.push_back(c_hi);
+  return HZ_OK;
+}
+
+}  // namespace
+
+bool fft_size_supported(int N) {
+  switch (N) {
+    case 8: case 12: case 16: case 24: case 32: case 48: case 64: case 96: case 128:
+    case 192: case 256: case 512: case 1024: case 2048:
+      return true;
+    default:
+      return false;
+  }
+}
+
+}  // namespace hz
+
+using namespace hz;
+
+extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, const double* zeta,
+                                      const double* a, double omega, const hz_interp* interp,
+                                      hz_medium** out) {
+  if (!grid || !c || !interp || !out) return set_error(HZ_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (grid->dim != 2 && grid->dim != 3) return set_error(HZ_ERR_INVALID_ARG, "dim must be 2 or 3");
+  if (!(grid->L > 0) || !std::isfinite(grid->L)) return set_error(HZ_ERR_INVALID_ARG, "L must be > 0");
+  for (int d = 0; d < grid->dim; ++d) {
+    if (!fft_size_supported(grid->n[d]))
+      return set_error(HZ_ERR_INVALID_ARG, "unsupported axis length %d", grid->n[d]);
+  }
+  if (grid->dim == 3 && grid->n[2] > 1024)
+    return set_error(HZ_ERR_INVALID_ARG, "z axis longer than 1024");
+  if (!(omega > 0) || !std::isfinite(omega)) return set_error(HZ_ERR_INVALID_ARG, "omega must be > 0");
+  if (interp->M < 1 || interp->Mt < 0 || interp->M + interp->Mt > HZ_MAX_K)
+    return set_error(HZ_ERR_INVALID_ARG, "need 1 <= M and M + Mt <= %d", HZ_MAX_K);
+  if (!(interp->c_o > 0) || interp->alpha < 0 || interp->a_node < 0 ||
+      (interp->symbol_kind != 0 && interp->symbol_kind != 1))
+    return set_error(HZ_ERR_INVALID_ARG, "bad interpolation options");
+
+  hz_medium* m = new hz_medium();
+  m->dim = grid->dim;
+  m->nx = grid->n[0];
+  m->ny = grid->n[1];
+  m->nz = grid->dim == 3 ? grid->n[2] : 1;
+  m->n = long(m->nx) * m->ny * m->nz;
+  m->L = grid->L;
+  m->omega = omega;
+  m->interp = *interp;
+  const long n = m->n;
+  auto fail = [&](hz_status s) {
+    m->arena.release();
+    delete m;
+    return s;
+  };
+
+  // stage the medium on the device (dc, dz, dpart live in a scratch arena)
+  DevArena scratch;
+  struct ScratchGuard {
+    DevArena& s;
+    ~ScratchGuard() { s.release(); }
+  } guard{scratch};
+  double *dc = nullptr, *dz = nullptr;
+  hz_status st = scratch.alloc(&dc, n);
+  if (st == HZ_OK && zeta) st = scratch.alloc(&dz, n);
+  if (st == HZ_OK && a) st = m->arena.alloc(&m->a, n);
+  if (st != HZ_OK) return fail(st);
+  cudaError_t ce = cudaMemcpy(dc, c, n * sizeof(double), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess && zeta) ce = cudaMemcpy(dz, zeta, n * sizeof(double), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess && a) ce = cudaMemcpy(m->a, a, n * sizeof(double), cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) return fail(cuda_error(ce, "medium upload"));
+
+  // validation and ranges
+  const int vblocks = 304;
+  ValPartial* dpart = nullptr;
+  if ((st = scratch.alloc(&dpart, vblocks)) != HZ_OK) return fail(st);
+  validate_kernel<<<vblocks, VAL_THREADS>>>(dc, dz, m->a, n, interp->c_o, dpart);
+  std::vector<ValPartial> hp(vblocks);
+  ce = cudaMemcpy(hp.data(), dpart, vblocks * sizeof(ValPartial), cudaMemcpyDeviceToHost);
+  if (ce != cudaSuccess) return fail(cuda_error(ce, "validate"));
+  double cmin = INFINITY, cmax = -INFINITY, zmax = 0;
+  unsigned long long bc = 0, bz = 0, bl = 0, ba = 0;
+  for (const auto& p : hp) {
+    cmin = std::min(cmin, p.cmin);
+    cmax = std::max(cmax, p.cmax);
+    zmax = std::max(zmax, p.zmax);
+    bc += p.bad_c; bz += p.bad_zeta; bl += p.bad_layer; ba += p.bad_a;
+  }
+  if (bc) return fail(set_error(HZ_ERR_MEDIUM, "%llu points with c <= 0 or not finite", bc));
+  if (bz) return fail(set_error(HZ_ERR_MEDIUM, "%llu points with zeta < 0 or not finite", bz));
+  if (bl) return fail(set_error(HZ_ERR_MEDIUM, "%llu layer points with c != c_o", bl));
+  if (ba) return fail(set_error(HZ_ERR_MEDIUM, "%llu points with a not finite", ba));
+  m->c_min = cmin;
+  m->c_max = cmax;
+
+  // node table (Section 4.1 / 4.4)
+  const bool layer = zmax > 0 && interp->Mt > 0;
+  if (zmax > 0 && interp->Mt == 0)
+    return fail(set_error(HZ_ERR_MEDIUM, "medium has a layer (zeta > 0) but Mt == 0"));
+  double c_lo = cmin, c_hi = cmax;
+  if (layer) {
+    c_lo = std::min(c_lo, interp->c_o);
+    c_hi = std::max(c_hi, interp->c_o);
+  }
+  if ((st = real_nodes(c_lo, c_hi, interp->M, layer || interp->M == 1, interp->c_o, m->c_real)) != HZ_OK)
+    return fail(st);
+  m->M = int(m->c_real.size());
+  m->m_o = -1;
+  m->zeta_nodes.assign(1, 0.0);
+  if (layer) {
+    for (int i = 0; i < m->M; ++i)
+      if (m->c_real[i] == interp->c_o) m->m_o = i;
+    if (m->m_o < 0) return fail(set_error(HZ_ERR_MEDIUM, "c_o is not a node"));
+    double zm = interp->zeta_max > 0 ? interp->zeta_max : zmax;
+    if (zm < zmax) return fail(set_error(HZ_ERR_MEDIUM, "zeta_max below max(zeta)"));
+    for (int i = 1; i < interp->Mt; ++i) m->zeta_nodes.push_back(i * zm / interp->Mt);
+    m->zeta_nodes.push_back(zm);
+    m->zeta_max = zm;
+  }
+  m->Mt = int(m->zeta_nodes.size()) - 1;
+  m->K = m->M + m->Mt;
+  m->gamma_re.clear();
+  m->gamma_im.clear();
+  for (double cr : m->c_real) {
+    m->gamma_re.push_back(cr);
+    m->gamma_im.push_back(0.0);
+  }
+  for (int i = 1; i <= m->Mt; ++i) {  // gamma = c_o (1 - i zeta_m)
+    m->gamma_re.push_back(interp->c_o);
+    m->gamma_im.push_back(-interp->c_o * m->zeta_nodes[i]);
+  }
+  m->a_k.assign(m->K, interp->a_node + interp->alpha * omega);
+
+  // segment table: real segments, end entry, layer segments, end entry
+  m->segtab_h.clear();
+  for (int s = 0; s + 1 < m->M; ++s) m->segtab_h.push_back(make_uchar2(s, s + 1));
+  m->segtab_h.push_back(make_uchar2(m->M - 1, m->M - 1));
+  if (m->Mt > 0) {
+    std::vector<int> node_of(m->Mt + 1);
+    node_of[0] = m->m_o;
+    for (int i = 1; i <= m->Mt; ++i) node_of[i] = m->M + i - 1;
+    for (int i = 0; i < m->Mt; ++i) m->segtab_h.push_back(make_uchar2(node_of[i], node_of[i + 1]));
+    m->segtab_h.push_back(make_uchar2(m->K - 1, m->K - 1));
+  }
+  m->nseg = int(m->segtab_h.size());
+
+  NodeDev nd;
+  memset(&nd, 0, sizeof(nd));
+  nd.M = m->M;
+  nd.Mt = m->Mt;
+  for (int i = 0; i < m->M; ++i) nd.c_real[i] = m->c_real[i];
+  for (int i = 0; i <= m->Mt; ++i) nd.zeta_nodes[i] = m->zeta_nodes[i];
+  for (int i = 0; i < m->nseg; ++i) nd.seg[i] = m->segtab_h[i];
+
+  const long nrows = n / m->nx;
+  st = m->arena.alloc(&m->rec64, n);
+  if (st == HZ_OK) st = m->arena.alloc(&m->rec32, n);
+  if (st == HZ_OK) st = m->arena.alloc(&m->gamma2, n);
+  if (st == HZ_OK) st = m->arena.alloc(&m->rowmask, nrows);
+  if (st == HZ_OK) st = m->arena.alloc(&m->slabmask, m->nz);
+  if (st != HZ_OK) return fail(st);
+  ce = cudaMemset(m->rowmask, 0, nrows * sizeof(unsigned long long));
+  if (ce != cudaSuccess) return fail(cuda_error(ce, "memset"));
+  record_kernel<<<unsigned((n + 255) / 256), 256>>>(dc, dz, n, m->nx, nd, m->rec64, m->rec32,
+                                                   m->gamma2, m->rowmask);
+  slab_kernel<<<(m->nz + 127) / 128, 128>>>(m->rowmask, m->ny, m->nz, m->slabmask);
+  ce = cudaGetLastError();
+  if (ce != cudaSuccess) return fail(cuda_error(ce, "record kernel"));
+
+  // symbol constants A_k = w^2 + i w a_k, G_k = gamma_k^2
+  std::vector<double2> A(m->K), G(m->K);
+  std::vector<float2> Af(m->K), Gf(m->K);
+  for (int k = 0; k < m->K; ++k) {
+    A[k] = make_double2(omega * omega, omega * m->a_k[k]);
+    const double gr = m->gamma_re[k], gi = m->gamma_im[k];
+    G[k] = make_double2(gr * gr - gi * gi, 2.0 * gr * gi);
+    Af[k] = make_float2(float(A[k].x), float(A[k].y));
+    Gf[k] = make_float2(float(G[k].x), float(G[k].y));
+  }
+  if ((st = upload(m->arena, &m->symA64, A)) != HZ_OK) return fail(st);
+  if ((st = upload(m->arena, &m->symG64, G)) != HZ_OK) return fail(st);
+  if ((st = upload(m->arena, &m->symA32, Af)) != HZ_OK) return fail(st);
+  if ((st = upload(m->arena, &m->symG32, Gf)) != HZ_OK) return fail(st);
+  if ((st = upload(m->arena, &m->segtab, m->segtab_h)) != HZ_OK) return fail(st);
+
+  // per-axis tables
+  const int nax[3] = {m->nx, m->ny, m->nz};
+  for (int d = 0; d < m->dim; ++d) {
+    const int N = nax[d];
+    std::vector<double2> tw;
+    std::vector<double> xi;
+    twiddles(N, tw);
+    xi2_table(N, m->L, interp->symbol_kind, xi);
+    std::vector<float2> twf(N);
+    std::vector<float> xif(N);
+    for (int j = 0; j < N; ++j) {
+      twf[j] = make_float2(float(tw[j].x), float(tw[j].y));
+      xif[j] = float(xi[j]);
+    }
+    AxisTables& t = m->ax[d];
+    t.N = N;
+    if ((st = upload(m->arena, &t.tw64, tw)) != HZ_OK) return fail(st);
+    if ((st = upload(m->arena, &t.tw32, twf)) != HZ_OK) return fail(st);
+    if ((st = upload(m->arena, &t.xi2_64, xi)) != HZ_OK) return fail(st);
+    if ((st = upload(m->arena, &t.xi2_32, xif)) != HZ_OK) return fail(st);
+    const double h = m->L / N;
+    m->inv_h2[d] = 1.0 / (h * h);
+  }
+  ce = cudaDeviceSynchronize();
+  if (ce != cudaSuccess) return fail(cuda_error(ce, "create_medium"));
+  *out = m;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_medium_info(const hz_medium* med, int* K, int* M, int* Mt, double* gamma_re,
+                                    double* gamma_im, double* a_k, double* c_min, double* c_max) {
+  if (!med) return set_error(HZ_ERR_INVALID_ARG, "null medium");
+  if (K) *K = med->K;
+  if (M) *M = med->M;
+  if (Mt) *Mt = med->Mt;
+  for (int k = 0; k < med->K; ++k) {
+    if (gamma_re) gamma_re[k] = med->gamma_re[k];
+    if (gamma_im) gamma_im[k] = med->gamma_im[k];
+    if (a_k) a_k[k] = med->a_k[k];
+  }
+  if (c_min) *c_min = med->c_min;
+  if (c_max) *c_max = med->c_max;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_destroy_medium(hz_medium* med) {
+  if (!med) return HZ_OK;
+  med->arena.release();
+  delete med;
+  return HZ_OK;
+}

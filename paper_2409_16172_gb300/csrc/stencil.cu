@@ -1,0 +1,121 @@
+// Finite-difference Helmholtz operator P_N (Eqn. 001 discretised as in
+// Section 5: second-order centred differences, periodic boundaries), FP64:
+//   (P x)_j = gamma_j^2 sum_axes (x_{j+e} - 2 x_j + x_{j-e}) / h_axis^2
+//             + (omega^2 + i omega a_j) x_j,
+// with gamma^2 = c^2 (1 - i zeta)^2 (Eqn. Complex_wave_speed).
+// Mode RESID computes r = f - P x and per-block partial sums of |r|^2.
+#include "hz_internal.h"
+#include "kernels.h"
+
+namespace hz {
+namespace {
+
+constexpr int ST_THREADS = 256;
+
+__device__ __forceinline__ double2 ld2(const double2* p, long i) { return p[i]; }
+__device__ __forceinline__ double2 ld2(const float2* p, long i) {
+  const float2 v = p[i];
+  return make_double2(double(v.x), double(v.y));
+}
+
+template <typename InT, bool RESID>
+__global__ void __launch_bounds__(ST_THREADS)
+stencil_kernel(const InT* __restrict__ x, double2* __restrict__ y, const double2* __restrict__ f,
+               const double2* __restrict__ gamma2, const double* __restrict__ a, double omega,
+               double ih2x, double ih2y, double ih2z, int nx, int ny, int nz, long n,
+               long in_stride, long out_stride, const int* __restrict__ active,
+               double* __restrict__ partial) {
+  const int b = blockIdx.y;
+  double nrm = 0.0;
+  const bool on = !active || active[b];
+  if (on) {
+    const InT* xb = x + b * in_stride;
+    const long i = long(blockIdx.x) * ST_THREADS + threadIdx.x;
+    if (i < n) {
+      const int ix = int(i % nx);
+      const long r = i / nx;
+      const int iy = int(r % ny);
+      const int iz = int(r / ny);
+      const long xl = ix == 0 ? i + nx - 1 : i - 1;
+      const long xr = ix == nx - 1 ? i - (nx - 1) : i + 1;
+      const long sy = nx;
+      const long yd = iy == 0 ? i + sy * (ny - 1) : i - sy;
+      const long yu = iy == ny - 1 ? i - sy * (ny - 1) : i + sy;
+      const double2 c = ld2(xb, i);
+      const double2 vxl = ld2(xb, xl), vxr = ld2(xb, xr), vyd = ld2(xb, yd), vyu = ld2(xb, yu);
+      double sr = ih2x * (vxl.x + vxr.x) + ih2y * (vyd.x + vyu.x);
+      double si = ih2x * (vxl.y + vxr.y) + ih2y * (vyd.y + vyu.y);
+      double diag = 2.0 * (ih2x + ih2y);
+      if (nz > 1) {
+        const long sz = long(nx) * ny;
+        const long zd = iz == 0 ? i + sz * (nz - 1) : i - sz;
+        const long zu = iz == nz - 1 ? i - sz * (nz - 1) : i + sz;
+        const double2 vzd = ld2(xb, zd), vzu = ld2(xb, zu);
+        sr += ih2z * (vzd.x + vzu.x);
+        si += ih2z * (vzd.y + vzu.y);
+        diag += 2.0 * ih2z;
+      }
+      sr -= diag * c.x;
+      si -= diag * c.y;
+      const double2 g = gamma2[i];
+      const double w2 = omega * omega;
+      const double wa = a ? omega * a[i] : 0.0;
+      // gamma^2 * lap + (w^2 + i w a) x
+      double yr = g.x * sr - g.y * si + w2 * c.x - wa * c.y;
+      double yi = g.x * si + g.y * sr + w2 * c.y + wa * c.x;
+      if (RESID) {
+        const double2 fv = f[b * out_stride + i];
+        yr = fv.x - yr;
+        yi = fv.y - yi;
+        nrm = yr * yr + yi * yi;
+      }
+      y[b * out_stride + i] = make_double2(yr, yi);
+    }
+  }
+  if (RESID) {
+    // fixed-shape block reduction of |r|^2
+    __shared__ double sh[ST_THREADS];
+    sh[threadIdx.x] = nrm;
+    __syncthreads();
+    for (int s = ST_THREADS / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[long(b) * gridDim.x + blockIdx.x] = sh[0];
+  }
+}
+
+}  // namespace
+
+int stencil_blocks(long n) { return int((n + ST_THREADS - 1) / ST_THREADS); }
+
+hz_status launch_stencil(const hz_medium* m, int in_prec, const void* x, long in_stride,
+                         double2* y, long out_stride, int nrhs, const int* active,
+                         cudaStream_t st) {
+  dim3 grid(unsigned(stencil_blocks(m->n)), unsigned(nrhs));
+  const double ih2z = m->dim == 3 ? m->inv_h2[2] : 0.0;
+  if (in_prec == 0)
+    stencil_kernel<double2, false><<<grid, ST_THREADS, 0, st>>>(
+        static_cast<const double2*>(x), y, nullptr, m->gamma2, m->a, m->omega, m->inv_h2[0],
+        m->inv_h2[1], ih2z, m->nx, m->ny, m->nz, m->n, in_stride, out_stride, active, nullptr);
+  else
+    stencil_kernel<float2, false><<<grid, ST_THREADS, 0, st>>>(
+        static_cast<const float2*>(x), y, nullptr, m->gamma2, m->a, m->omega, m->inv_h2[0],
+        m->inv_h2[1], ih2z, m->nx, m->ny, m->nz, m->n, in_stride, out_stride, active, nullptr);
+  HZ_CUDA(cudaGetLastError());
+  return HZ_OK;
+}
+
+hz_status launch_residual(const hz_medium* m, const double2* u, const double2* f, double2* r,
+                          long stride, int nrhs, const int* active, double* partial,
+                          cudaStream_t st) {
+  dim3 grid(unsigned(stencil_blocks(m->n)), unsigned(nrhs));
+  const double ih2z = m->dim == 3 ? m->inv_h2[2] : 0.0;
+  stencil_kernel<double2, true><<<grid, ST_THREADS, 0, st>>>(
+      u, r, f, m->gamma2, m->a, m->omega, m->inv_h2[0], m->inv_h2[1], ih2z, m->nx, m->ny, m->nz,
+      m->n, stride, stride, active, partial);
+  HZ_CUDA(cudaGetLastError());
+  return HZ_OK;
+}
+
+}  // namespace hz

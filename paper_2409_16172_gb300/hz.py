@@ -1,0 +1,251 @@
+"""ctypes binding of the C ABI in include/hz.h (argument marshalling only).
+
+Every computation runs in the CUDA library libhz.so; importing this module
+loads it and raises ImportError when it has not been built (call
+``paper_2409_16172_gb300.build.build()``).  Device buffers are torch tensors
+(complex128, contiguous, on the current CUDA device); streams are torch
+streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhz.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "hz.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"CUDA library not built: {LIB_PATH} is missing "
+                      "(run paper_2409_16172_gb300.build.build())")
+lib = C.CDLL(LIB_PATH)
+
+HZ_OK = 0
+STATUS = {0: "HZ_OK", 1: "HZ_ERR_INVALID_ARG", 2: "HZ_ERR_OOM", 3: "HZ_ERR_CUDA",
+          4: "HZ_ERR_NOT_CONVERGED", 5: "HZ_ERR_BREAKDOWN", 6: "HZ_ERR_TIMEOUT",
+          7: "HZ_ERR_BUSY", 8: "HZ_ERR_MEDIUM"}
+
+
+class HzError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class hz_grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("L", C.c_double)]
+
+
+class hz_interp(C.Structure):
+    _fields_ = [("M", C.c_int), ("Mt", C.c_int), ("c_o", C.c_double), ("zeta_max", C.c_double),
+                ("alpha", C.c_double), ("a_node", C.c_double), ("symbol_kind", C.c_int)]
+
+
+class hz_solver_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("restart", C.c_int), ("tol", C.c_double),
+                ("maxit", C.c_int)]
+
+
+class hz_solve_stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("status", C.c_int),
+                ("converged", C.c_int), ("rel_true_resid", C.c_double),
+                ("rel_est_resid", C.c_double), ("ms_total", C.c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_vp = C.c_void_p
+_dp = C.POINTER(C.c_double)
+_SIGS = {
+    "hz_last_error": (C.c_char_p, []),
+    "hz_version": (C.c_char_p, []),
+    "hz_set_allocator": (C.c_int, [_vp, _vp, _vp]),
+    "hz_create_medium": (C.c_int, [C.POINTER(hz_grid), _dp, _dp, _dp, C.c_double,
+                                   C.POINTER(hz_interp), C.POINTER(_vp)]),
+    "hz_medium_info": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                 _dp, _dp, _dp, _dp, _dp]),
+    "hz_destroy_medium": (C.c_int, [_vp]),
+    "hz_plan_create": (C.c_int, [_vp, C.POINTER(hz_solver_opts), C.c_int, C.POINTER(_vp)]),
+    "hz_plan_bytes": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
+    "hz_destroy_plan": (C.c_int, [_vp]),
+    "hz_apply_operator": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
+    "hz_apply_preconditioner": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
+    "hz_gmres_solve": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(hz_solve_stats), _vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    if hasattr(lib, _name):
+        _f = getattr(lib, _name)
+        _f.restype = _res
+        _f.argtypes = _args
+
+
+def header_symbols(path: str = HEADER) -> list[str]:
+    """Every function name declared in include/hz.h."""
+    with open(path) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\*?\s+\**(hz_[a-z0-9_]+)\s*\(",
+                                 text, re.M)))
+
+
+def last_error() -> str:
+    return lib.hz_last_error().decode()
+
+
+def version() -> str:
+    return lib.hz_version().decode()
+
+
+def check(status: int, ok=(HZ_OK,)):
+    if status not in ok:
+        raise HzError(status, last_error())
+    return status
+
+
+def _dptr(a):
+    """double* of a C-contiguous float64 numpy array (or NULL)."""
+    if a is None:
+        return None
+    return a.ctypes.data_as(_dp)
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _vp(s.cuda_stream)
+
+
+def _check_dev(x, name):
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.complex128
+            and x.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous complex128 CUDA tensor")
+
+
+class Medium:
+    """A medium on the GPU: node table, interpolation records, gamma^2."""
+
+    def __init__(self, c, zeta=None, a=None, *, omega: float, M: int, Mt: int = 0,
+                 c_o: float = 1.0, zeta_max: float = 0.0, alpha: float = 0.15,
+                 a_node: float = 0.0, symbol_kind: int = 0, L: float = 1.0):
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        self.shape = c.shape
+        if c.ndim not in (2, 3):
+            raise ValueError("c must be 2D or 3D")
+        zeta = None if zeta is None else np.ascontiguousarray(zeta, dtype=np.float64)
+        a = None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+        for arr in (zeta, a):
+            if arr is not None and arr.shape != c.shape:
+                raise ValueError("zeta / a must have the shape of c")
+        g = hz_grid()
+        g.dim = c.ndim
+        dims = list(reversed(c.shape)) + [1] * (3 - c.ndim)
+        for i in range(3):
+            g.n[i] = dims[i]
+        g.L = L
+        it = hz_interp(M, Mt, c_o, zeta_max, alpha, a_node, symbol_kind)
+        h = _vp()
+        check(lib.hz_create_medium(C.byref(g), _dptr(c), _dptr(zeta), _dptr(a), float(omega),
+                                   C.byref(it), C.byref(h)))
+        self._h = h
+        self.omega = float(omega)
+        self.n = int(np.prod(c.shape))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        K, M, Mt = C.c_int(), C.c_int(), C.c_int()
+        cmin, cmax = C.c_double(), C.c_double()
+        check(lib.hz_medium_info(self._h, C.byref(K), C.byref(M), C.byref(Mt), None, None, None,
+                                 C.byref(cmin), C.byref(cmax)))
+        gr = np.zeros(K.value)
+        gi = np.zeros(K.value)
+        ak = np.zeros(K.value)
+        check(lib.hz_medium_info(self._h, None, None, None, _dptr(gr), _dptr(gi), _dptr(ak), None,
+                                 None))
+        return dict(K=K.value, M=M.value, Mt=Mt.value, gamma=gr + 1j * gi, a=ak,
+                    c_min=cmin.value, c_max=cmax.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.hz_destroy_medium(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+class Plan:
+    """Workspace for applying and solving on one medium."""
+
+    def __init__(self, medium: Medium, *, precision: int = 1, restart: int = 40,
+                 tol: float = 1e-6, maxit: int = 4000, max_nrhs: int = 1):
+        self.medium = medium
+        self.max_nrhs = max_nrhs
+        self.opts = hz_solver_opts(precision, restart, tol, maxit)
+        h = _vp()
+        check(lib.hz_plan_create(medium.handle, C.byref(self.opts), max_nrhs, C.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def nbytes(self) -> int:
+        b = C.c_size_t()
+        check(lib.hz_plan_bytes(self._h, C.byref(b)))
+        return b.value
+
+    def apply_operator(self, x, out=None, stream=None):
+        import torch
+        _check_dev(x, "x")
+        nrhs = x.numel() // self.medium.n
+        out = torch.empty_like(x) if out is None else out
+        _check_dev(out, "out")
+        check(lib.hz_apply_operator(self._h, _vp(x.data_ptr()), _vp(out.data_ptr()), nrhs,
+                                    _stream(stream)))
+        return out
+
+    def apply_preconditioner(self, x, precision: int = 1, out=None, stream=None):
+        import torch
+        _check_dev(x, "x")
+        nrhs = x.numel() // self.medium.n
+        out = torch.empty_like(x) if out is None else out
+        _check_dev(out, "out")
+        check(lib.hz_apply_preconditioner(self._h, _vp(x.data_ptr()), _vp(out.data_ptr()), nrhs,
+                                          precision, _stream(stream)))
+        return out
+
+    def solve(self, f, u=None, stream=None, raise_on_fail: bool = False):
+        """Solve P u = f.  f, u: complex128 CUDA tensors or numpy arrays
+        (host buffers are staged by the library).  Returns (u, [stats])."""
+        import torch
+        if isinstance(f, torch.Tensor):
+            _check_dev(f, "f")
+            nrhs = f.numel() // self.medium.n
+            u = torch.zeros_like(f) if u is None else u
+            _check_dev(u, "u")
+            fp, up = _vp(f.data_ptr()), _vp(u.data_ptr())
+        else:
+            f = np.ascontiguousarray(f, dtype=np.complex128)
+            nrhs = f.size // self.medium.n
+            u = np.zeros_like(f) if u is None else u
+            if not (isinstance(u, np.ndarray) and u.dtype == np.complex128 and u.flags.c_contiguous):
+                raise TypeError("u must be a contiguous complex128 numpy array")
+            fp, up = _vp(f.ctypes.data), _vp(u.ctypes.data)
+        stats = (hz_solve_stats * nrhs)()
+        st = lib.hz_gmres_solve(self._h, fp, up, nrhs, stats, _stream(stream))
+        ok = (HZ_OK,) if raise_on_fail else (HZ_OK, 4, 5)
+        check(st, ok)
+        return u, [s.as_dict() for s in stats]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.hz_destroy_plan(self._h)
+            self._h = None
+
+    __del__ = close

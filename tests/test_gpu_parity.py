@@ -1,0 +1,174 @@
+"""Parity of the CUDA path against the CPU oracle, element by element, on
+seeded synthetic media (several tiles, ragged tails, 2D and 3D), through the
+C ABI.  Tolerances: 1e-10 relative (2-norm) for the FP64 apply, operator and
+solve pieces; 5e-5 for the complex64 preconditioner apply (FP32 rounding,
+~eps32 log2(n), amplified near |xi| = omega / c_k by at most 1/alpha)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2409_16172_gb300 import synth as S
+
+from gpu_util import hz_module, media, rel
+
+pytestmark = pytest.mark.gpu
+
+SHAPES_2D = [(16, 16), (24, 48), (96, 12), (64, 32), (128, 128), (48, 192), (8, 2048)]
+SHAPES_3D = [(8, 12, 16), (16, 16, 16), (24, 16, 32), (12, 48, 8)]
+
+
+@pytest.fixture(scope="module")
+def hz():
+    import torch
+    assert torch.cuda.is_available()
+    return hz_module()
+
+
+def _dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def test_node_table_matches_oracle(hz):
+    for p in (S.small_problem((32, 24), 3, M=5, Mt=3, width=3), S.config1()):
+        med_g, med_o = media(hz, p)
+        info = med_g.info()
+        assert info["K"] == med_o.nodes.K and info["M"] == med_o.nodes.M
+        np.testing.assert_allclose(info["gamma"], med_o.nodes.gamma, rtol=1e-15, atol=1e-15)
+        np.testing.assert_allclose(info["a"], med_o.nodes.a, rtol=1e-15)
+    # c_o strictly inside the speed range: two equispaced segments
+    p = S.small_problem((16, 16), 4, M=6, Mt=2, width=2, contrast=0.5)
+    c = p.c.copy()
+    c[c == 1.0] = 1.0
+    c[6:10, 6:10] = 0.8
+    p.c = c
+    med_g, med_o = media(hz, p)
+    np.testing.assert_allclose(med_g.info()["gamma"], med_o.nodes.gamma, rtol=1e-15)
+
+
+@pytest.mark.parametrize("shape", SHAPES_2D + SHAPES_3D)
+def test_apply_preconditioner_fp64(hz, shape):
+    p = S.small_problem(shape, 11, M=5, Mt=3, width=2)
+    med_g, med_o = media(hz, p)
+    plan = hz.Plan(med_g, precision=0, max_nrhs=2)
+    v = S.random_field(np.random.Generator(np.random.PCG64(5)), shape, 2)
+    ref = np.stack([O.apply_preconditioner(med_o, v[b]) for b in range(2)])
+    got = plan.apply_preconditioner(_dev(v), precision=0).cpu().numpy()
+    assert rel(got, ref) <= 1e-10, rel(got, ref)
+    # element-wise as well: every point within 1e-10 of the largest value
+    assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("shape", SHAPES_2D + SHAPES_3D)
+def test_apply_preconditioner_c64(hz, shape):
+    p = S.small_problem(shape, 12, M=5, Mt=3, width=2)
+    med_g, med_o = media(hz, p)
+    plan = hz.Plan(med_g, precision=1)
+    v = S.random_field(np.random.Generator(np.random.PCG64(6)), shape)
+    ref = O.apply_preconditioner(med_o, v)
+    got = plan.apply_preconditioner(_dev(v), precision=1).cpu().numpy()
+    assert rel(got, ref) <= 5e-5, rel(got, ref)
+
+
+@pytest.mark.parametrize("shape", [(16, 16), (24, 48), (8, 12, 16)])
+def test_apply_preconditioner_variants(hz, shape):
+    """No layer; single node (Q_1); finite-difference symbol; damping in the
+    operator and the symbol."""
+    p = S.small_problem(shape, 13, M=4, Mt=0, width=0, a_const=2.0)
+    for kw in (dict(), dict(M=1), dict(symbol_kind=1), dict(a_node=2.0, alpha=0.0)):
+        med_g, med_o = media(hz, p, **kw)
+        plan = hz.Plan(med_g, precision=0)
+        v = S.random_field(np.random.Generator(np.random.PCG64(7)), shape)
+        ref = O.apply_preconditioner(med_o, v)
+        got = plan.apply_preconditioner(_dev(v), precision=0).cpu().numpy()
+        assert rel(got, ref) <= 1e-10, (kw, rel(got, ref))
+
+
+@pytest.mark.parametrize("shape", SHAPES_2D[:4] + SHAPES_3D[:3])
+def test_apply_operator(hz, shape):
+    p = S.small_problem(shape, 14, M=4, Mt=2, width=2, a_const=1.5)
+    med_g, med_o = media(hz, p)
+    plan = hz.Plan(med_g, precision=0, max_nrhs=3)
+    v = S.random_field(np.random.Generator(np.random.PCG64(8)), shape, 3)
+    ref = np.stack([O.apply_operator(med_o, v[b]) for b in range(3)])
+    got = plan.apply_operator(_dev(v)).cpu().numpy()
+    assert rel(got, ref) <= 1e-12, rel(got, ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_gmres_small_matches_dense_and_oracle(hz, prec):
+    p = S.small_problem((24, 32), 15, M=5, Mt=3, width=3)
+    med_g, med_o = media(hz, p)
+    plan = hz.Plan(med_g, precision=prec, restart=20, tol=1e-10, maxit=2000)
+    u, st = plan.solve(_dev(p.f[0]))
+    u = u.cpu().numpy()
+    assert st[0]["converged"], st
+    r = rel(O.apply_operator(med_o, u), p.f[0])
+    assert r <= 1e-10, r
+    A = O.assemble_dense(lambda x: O.apply_operator(med_o, x), p.shape)
+    x_lu = np.linalg.solve(A, p.f[0].ravel()).reshape(p.shape)
+    assert rel(u, x_lu) <= 1e-7
+
+
+def test_gmres_config1_fp64(hz):
+    """2D 128^2, K = 8, GMRES(30), FP64 throughout, tol 1e-6: the true residual
+    computed by the oracle's own operator meets the tolerance and the
+    iteration count is close to the oracle's GMRES."""
+    p = S.config1()
+    med_g, med_o = media(hz, p)
+    plan = hz.Plan(med_g, precision=0, restart=30, tol=1e-6, maxit=4000)
+    u, st = plan.solve(_dev(p.f[0]))
+    u = u.cpu().numpy()
+    r = rel(O.apply_operator(med_o, u), p.f[0])
+    assert st[0]["converged"] and r <= 1e-6, (st, r)
+    uo, sto = O.gmres(lambda x: O.apply_operator(med_o, x), p.f[0],
+                      lambda v: O.apply_preconditioner(med_o, v), restart=30, tol=1e-6)
+    assert abs(st[0]["iters"] - sto["iters"]) <= 2, (st, sto["iters"])
+    assert rel(u, uo) <= 1e-4
+
+
+def test_gmres_multi_rhs_and_host_buffers(hz):
+    p = S.bump_problem(64, 21, width=8, ppw=8.0, M=4, Mt=2, nrhs=3)
+    med_g, med_o = media(hz, p)
+    plan = hz.Plan(med_g, precision=1, restart=25, tol=1e-6, maxit=2000, max_nrhs=3)
+    f = np.ascontiguousarray(p.f)
+    u, st = plan.solve(f)  # host numpy buffers, staged by the library
+    for b in range(3):
+        r = rel(O.apply_operator(med_o, u[b]), f[b])
+        assert st[b]["converged"] and r <= 1e-6, (b, st[b], r)
+    # each right-hand side alone gives the same answer as in the batch
+    plan1 = hz.Plan(med_g, precision=1, restart=25, tol=1e-6, maxit=2000, max_nrhs=1)
+    u1, st1 = plan1.solve(np.ascontiguousarray(f[1:2]))
+    assert st1[0]["iters"] == st[1]["iters"]
+    assert rel(u1[0], u[1]) <= 1e-12
+
+
+def test_edge_cases(hz):
+    p = S.small_problem((16, 16), 16, M=4, Mt=2, width=2)
+    med_g, med_o = media(hz, p)
+    plan = hz.Plan(med_g, precision=1, restart=10, tol=1e-6, maxit=3)
+    # zero right-hand side: zero solution, converged at once
+    u, st = plan.solve(np.zeros((1, 16, 16), complex))
+    assert st[0]["converged"] and np.all(u == 0) and st[0]["iters"] == 0
+    # maxit reached: NOT_CONVERGED with the iterate and its stats
+    u, st = plan.solve(_dev(p.f[0]))
+    assert not st[0]["converged"] and st[0]["iters"] == 3 and st[0]["status"] == 4
+    with pytest.raises(hz.HzError) as e:
+        plan.solve(_dev(p.f[0]), raise_on_fail=True)
+    assert e.value.status == 4
+    # invalid media and grids are rejected on the host
+    bad = p.c.copy()
+    bad[3, 3] = -1.0
+    with pytest.raises(hz.HzError) as e:
+        hz.Medium(bad, p.zeta, omega=p.omega, M=4, Mt=2)
+    assert e.value.status == 8
+    bad = p.c.copy()
+    bad[0, 0] = 1.3  # inside the layer, c != c_o
+    with pytest.raises(hz.HzError) as e:
+        hz.Medium(bad, p.zeta, omega=p.omega, M=4, Mt=2)
+    assert e.value.status == 8
+    with pytest.raises(hz.HzError) as e:
+        hz.Medium(np.ones((20, 16)), omega=3.0, M=2)
+    assert e.value.status == 1
+    with pytest.raises(hz.HzError):
+        plan.apply_operator(_dev(np.zeros((2, 16, 16), complex)))  # nrhs > max_nrhs

@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark: Helmholtz solves per second at a 1e-6 true relative residual.
+
+Workload (one step = one full solve, every row of the hot path): the 2D
+1024 x 1024 periodic FD Helmholtz problem with c in [1, 2] from 20 seeded
+Gaussian bumps plus a linear gradient, a 32-cell complex-speed absorbing
+layer, omega for 8 points per wavelength, K = 16 symbol planes (12 real + 4
+layer nodes), FGMRES(40) with the complex64 preconditioner and FP64 Krylov
+work, tol 1e-6 on the true residual.  The medium and right-hand side are
+resident in HBM before timing starts; the Krylov basis (0.7 GB) and the
+symbol planes exceed L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gb300,reference}]
+
+With N > 1 (torchrun, one rank per GPU) every rank solves its own copy:
+replicas, no collective on the data path ("scaling": "weak").
+--impl reference times the CPU oracle (numpy / scipy FP64) on this host's
+cores on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALPHA = 0.1          # node-symbol damping a_k = alpha * omega (sweep in the design doc)
+METRIC = "Helmholtz solves/s at 1e-6 true relative residual"
+WORKLOAD = "2d-1024x1024-bumps20+gradient-layer32-ppw8-K16-fgmres40"
+
+
+def workload_config(p):
+    return {"workload": WORKLOAD, "grid": list(p.shape), "K": p.K, "M": p.M, "Mt": p.Mt,
+            "omega": round(p.omega, 4), "restart": p.restart, "tol": p.tol, "nrhs": 1,
+            "alpha": ALPHA, "precond": "complex64", "krylov": "FP64 CGS2",
+            "l2": "working set larger than L2 (basis 0.7 GB, planes 134 MB); no flush"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons, pw = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+                pw.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "power_w_max": float(max(pw)), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_solve_sample(p, iters: int, workers: int):
+    """Bounded oracle sample: one FGMRES cycle of `iters` Arnoldi steps of the
+    same workload (oracle as it stands, FP64 numpy / scipy)."""
+    import oracle as O
+    med = O.make_medium(p.c, p.zeta, None, p.omega, p.M, p.Mt, p.c_o, None, ALPHA)
+    t0 = time.perf_counter()
+    _, st = O.gmres(lambda u: O.apply_operator(med, u), p.f[0],
+                    lambda v: O.apply_preconditioner(med, v, workers=workers),
+                    restart=p.restart, tol=p.tol, maxit=iters)
+    dt = time.perf_counter() - t0
+    return dt, st["iters"]
+
+
+def run_reference(args, p):
+    world, rank, local, dist = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    import oracle as O  # noqa: F401
+    workers = os.cpu_count() or 1
+    # iterations per solve: the oracle's own full solve (run once, untimed)
+    med_iters = None
+    if args.ref_iters <= 0:
+        import oracle as O
+        med = O.make_medium(p.c, p.zeta, None, p.omega, p.M, p.Mt, p.c_o, None, ALPHA)
+        _, st = O.gmres(lambda u: O.apply_operator(med, u), p.f[0],
+                        lambda v: O.apply_preconditioner(med, v, workers=workers),
+                        restart=p.restart, tol=p.tol, maxit=4000)
+        med_iters = st["iters"]
+    iters_per_solve = med_iters or args.ref_iters
+    for _ in range(args.warmup):
+        oracle_solve_sample(p, 2, workers)
+    per_it = []
+    for _ in range(args.steps):
+        dt, it = oracle_solve_sample(p, args.ref_sample, workers)
+        per_it.append(dt / max(it, 1))
+    t_it = float(np.mean(per_it))
+    value = 1.0 / (t_it * iters_per_solve)
+    sample = (f"{args.ref_sample} FGMRES(40) Arnoldi steps of the workload per step; solves/s = "
+              f"1 / (s per step x {iters_per_solve} steps per solve"
+              f"{' (oracle full solve)' if med_iters else ' (GPU-measured count)'})")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t_it * args.ref_sample, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+           "config": workload_config(p),
+           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": workers,
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_gpu(args, p):
+    import torch
+    world, rank, local, dist = dist_setup(args.gpus)
+    if world == 1:
+        torch.cuda.set_device(0)
+    from paper_2409_16172_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    barrier(dist)
+    from paper_2409_16172_gb300 import hz
+
+    med = hz.Medium(p.c, p.zeta, omega=p.omega, M=p.M, Mt=p.Mt, c_o=p.c_o, alpha=ALPHA)
+    plan = hz.Plan(med, precision=1, restart=p.restart, tol=p.tol, maxit=4000, max_nrhs=1)
+    f = torch.from_numpy(np.ascontiguousarray(p.f[0])).cuda()
+    u = torch.zeros_like(f)
+    stream = torch.cuda.current_stream()
+
+    def solve():
+        u.zero_()
+        _, st = plan.solve(f, u, stream=stream)
+        return st[0]
+
+    for _ in range(args.warmup):
+        st0 = solve()
+    torch.cuda.synchronize()
+    fp64_gflops = hz.measure_fp64_peak()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    hz.profile_enable(True)
+    hz.profile_read(reset=True)
+    launches0 = hz.launch_count()
+    barrier(dist)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = [solve() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    launches = hz.launch_count() - launches0
+    prof = hz.profile_read(reset=True)
+    hz.profile_enable(False)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(dist, ms)
+    value = world * args.steps / (ms_max / 1e3)
+
+    # end to end through the C ABI with host buffers: H2D of f and the
+    # initial guess, D2H of the solution, inside the timed region
+    fh = np.ascontiguousarray(p.f[0])
+    e2e_steps = max(1, min(args.steps, 5))
+    uh = np.zeros_like(fh)
+    torch.cuda.synchronize()
+    barrier(dist)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        uh[...] = 0
+        plan.solve(fh, uh, stream=stream)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
+    e2e_val = world * e2e_steps / e2e_s
+
+    ok = all(s["converged"] and s["rel_true_resid"] <= p.tol for s in stats)
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
+    # dominant kernel by summed event time
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    name, d = dom
+    fp64_phases = {"cgs2_dots", "cgs2_update", "stencil", "residual", "solution_update", "norm"}
+    if name in fp64_phases:
+        achieved = d["flops"] / d["ms"] / 1e9  # TFLOP/s
+        roof = {"kernel": name, "bound": "alu", "achieved": achieved,
+                "peak": fp64_gflops / 1e3, "unit": "TFLOP/s",
+                "frac": achieved / (fp64_gflops / 1e3), "traffic": None,
+                "peak_source": "FP64 FMA probe on this GPU (hz_measure_fp64_peak)",
+                "launches": d["launches"], "avg_launch_us": 1e3 * d["ms"] / d["launches"],
+                "hbm_gbs_achieved": d["bytes"] / d["ms"] / 1e6}
+    else:
+        achieved = d["bytes"] / d["ms"] / 1e6  # GB/s
+        roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "peak_source": hbm_src, "launches": d["launches"],
+                "avg_launch_us": 1e3 * d["ms"] / d["launches"]}
+    fft = [k for k in prof if k.startswith("fft_")]
+    pb = sum(prof[k]["bytes"] for k in fft)
+    pm = sum(prof[k]["ms"] for k in fft)
+    precond = {"bound": "hbm", "achieved": pb / pm / 1e6, "peak": hbm, "unit": "GB/s",
+               "frac": pb / pm / 1e6 / hbm, "peak_source": hbm_src,
+               "apply_us": 1e3 * pm / max(prof["fft_row_fwd"]["launches"], 1),
+               "kernels": {k: {"launches": prof[k]["launches"],
+                               "avg_us": 1e3 * prof[k]["ms"] / prof[k]["launches"],
+                               "gbs": prof[k]["bytes"] / prof[k]["ms"] / 1e6}
+                           for k in fft}}
+    total_ms = sum(v["ms"] for v in prof.values())
+    phases = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                  "share": round(v["ms"] / total_ms, 4),
+                  "gbs": round(v["bytes"] / v["ms"] / 1e6, 1) if v["ms"] else None,
+                  "tflops": round(v["flops"] / v["ms"] / 1e9, 4) if v["ms"] else None}
+              for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        workers = os.cpu_count() or 1
+        dt, it = oracle_solve_sample(p, args.cpu_iters, workers)
+        iters = stats[0]["iters"]
+        cpu = {"value": 1.0 / (dt / max(it, 1) * iters), "unit": "solves/s", "cores": workers,
+               "kind": "oracle",
+               "sample": f"{it} oracle FGMRES(40) Arnoldi steps of the workload ({dt:.1f} s); "
+                         f"scaled by the {iters} steps of the GPU solve"}
+    n = p.n
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "c64+c128", "data": "synthetic", "config": workload_config(p),
+           "iters": stats[0]["iters"], "rel_true_resid": stats[0]["rel_true_resid"],
+           "all_converged": ok,
+           "roofline": roof, "roofline_precond": precond,
+           "cpu_baseline": cpu,
+           "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": 2 * 16 * n,
+                   "d2h_bytes_per_step": 16 * n},
+           "gpu_launches": launches, "clocks": clocks, "phases": phases,
+           "fp64_peak_tflops": fp64_gflops / 1e3}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--cpu-iters", type=int, default=6, help="Arnoldi steps in the CPU sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample", type=int, default=3, help="reference arm: steps per sample")
+    ap.add_argument("--ref-iters", type=int, default=0,
+                    help="reference arm: Arnoldi steps per solve (0: count them with one full "
+                         "untimed oracle solve)")
+    args = ap.parse_args()
+    from paper_2409_16172_gb300 import synth as S
+    p = S.config2()
+    if args.impl == "reference":
+        run_reference(args, p)
+    else:
+        run_gpu(args, p)
+
+
+if __name__ == "__main__":
+    main()

@@ -173,6 +173,35 @@ hz_status hz_apply_preconditioner(hz_plan* plan, const void* x, void* y, int nrh
 hz_status hz_gmres_solve(hz_plan* plan, const void* f, void* u, int nrhs,
                          hz_solve_stats* stats, void* stream);
 
+/* ---- measurement ------------------------------------------------------
+ * Per-phase timing with CUDA events recorded on the stream each kernel is
+ * launched on, plus the algorithmic bytes and flops of every launch (the
+ * compulsory traffic of the phase: each input read once, each output written
+ * once; the symbol planes only for the rows that use them).  Phases:
+ * fft_row_fwd, fft_line, fft_fused, fft_row_inv_acc, stencil, cgs2_dots,
+ * cgs2_update, givens, solution_update, residual, norm.
+ * hz_profile_enable(1) turns recording on for the whole process (it adds two
+ * event records per launch); hz_profile_read waits for the recorded events,
+ * fills up to max entries and optionally resets the counters. */
+typedef struct {
+  char name[24];
+  long long launches;
+  double ms;      /* summed event time                        */
+  double bytes;   /* summed algorithmic bytes                  */
+  double flops;   /* summed algorithmic floating-point ops     */
+} hz_phase_stats;
+
+hz_status hz_profile_enable(int on);
+hz_status hz_profile_read(hz_phase_stats* out, int max, int* count, int reset);
+
+/* Number of kernels this library has launched in this process. */
+unsigned long long hz_launch_count(void);
+
+/* Measures this GPU's FP64 FMA throughput (GFLOP/s, 2 flops per FMA) with a
+ * kernel of independent FMA chains filling every SM for about 0.1 s; the
+ * denominator for the FP64-bound Krylov kernels.  Synchronous. */
+hz_status hz_measure_fp64_peak(double* gflops);
+
 #ifdef __cplusplus
 }
 #endif

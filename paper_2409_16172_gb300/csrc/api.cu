@@ -131,22 +131,53 @@ hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* s
   const void* G = prec == 0 ? (const void*)m->symG64 : (const void*)m->symG32;
   const void* rec = prec == 0 ? (const void*)m->rec64 : (const void*)m->rec32;
   const long rows = n / nx;
-  HZ_TRY(ox->row_fwd(prec, in, scale, rows, rows * nrhs, tw(tx), p->tmp, st));
+  const double s = prec == 0 ? 16.0 : 8.0;          // working complex element
+  const double so = out_kind == 1 ? 16.0 : 8.0;     // output element
+  const double rb = prec == 0 ? 8.0 : 4.0;          // interpolation record
+  const double B = nrhs, K = m->K, dn = double(n);
+  auto l2 = [](int N) { return std::log2(double(N)); };
+  {
+    PhaseScope ps(st, PH_ROW_FWD, B * dn * (16.0 + s), B * 5.0 * dn * l2(nx));
+    HZ_TRY(ox->row_fwd(prec, in, scale, rows, rows * nrhs, tw(tx), p->tmp, st));
+  }
+  // forward FFT along every axis but x, in place on tmp
+  {
+    PhaseScope ps(st, PH_LINE, B * 2.0 * s * dn, B * 5.0 * dn * l2(ny));
+    HZ_TRY(oy->line_pass(prec, -1, p->tmp, nx, nz, nx, long(nx) * ny, n, nrhs, nullptr, m->K,
+                         tw(ty), st));
+  }
   if (m->dim == 2) {
-    HZ_TRY(oy->line_fused(prec, p->tmp, p->planes, nx, 1, nx, 0, n, m->K, nrhs, xi(tx), nullptr,
-                          xi(ty), A, G, m->rowmask, 0, 1, tw(ty), st));
+    PhaseScope ps(st, PH_SYMINV, B * (dn * s + m->rowk_used * nx * s),
+                  B * K * (5.0 * dn * l2(ny) + 14.0 * dn));
+    HZ_TRY(oy->line_sym_inv(prec, p->tmp, p->planes, nx, 1, nx, 0, n, m->K, nrhs, xi(tx), nullptr,
+                            xi(ty), A, G, m->rowmask, 0, 1, tw(ty), st));
   } else {
     const FftOps* oz = fft_ops(nz);
     const AxisTables& tz = m->ax[2];
     const long slab = long(nx) * ny;
-    HZ_TRY(oy->line_pass(prec, -1, p->tmp, nx, nz, nx, slab, n, nrhs, nullptr, m->K, tw(ty), st));
-    HZ_TRY(oz->line_fused(prec, p->tmp, p->planes, nx, ny, slab, nx, n, m->K, nrhs, xi(tx), xi(ty),
-                          xi(tz), A, G, m->slabmask, 0, 1, tw(tz), st));
-    HZ_TRY(oy->line_pass(prec, +1, p->planes, nx, nz, nx, slab, n, nrhs * m->K, m->slabmask, m->K,
-                         tw(ty), st));
+    {
+      PhaseScope ps(st, PH_LINE, B * 2.0 * s * dn, B * 5.0 * dn * l2(nz));
+      HZ_TRY(oz->line_pass(prec, -1, p->tmp, nx, ny, slab, nx, n, nrhs, nullptr, m->K, tw(tz), st));
+    }
+    {
+      PhaseScope ps(st, PH_SYMINV, B * (dn * s + m->slabk_used * slab * s),
+                    B * K * (5.0 * dn * l2(nz) + 14.0 * dn));
+      HZ_TRY(oz->line_sym_inv(prec, p->tmp, p->planes, nx, ny, slab, nx, n, m->K, nrhs, xi(tx),
+                              xi(ty), xi(tz), A, G, m->slabmask, 0, 1, tw(tz), st));
+    }
+    {
+      PhaseScope ps(st, PH_LINE, B * 2.0 * s * m->slabk_used * slab,
+                    B * 5.0 * m->slabk_used * slab * l2(ny));
+      HZ_TRY(oy->line_pass(prec, +1, p->planes, nx, nz, nx, slab, n, nrhs * m->K, m->slabmask, m->K,
+                           tw(ty), st));
+    }
   }
-  HZ_TRY(ox->row_inv_acc(prec, out_kind, p->planes, rec, m->segtab, m->nseg, m->rowmask, m->K,
-                         rows, rows * nrhs, n, 1.0 / double(n), tw(tx), out, st));
+  {
+    PhaseScope ps(st, PH_ROW_INV, B * (m->rowk_used * nx * s + dn * (rb + so)),
+                  B * (m->rowk_used * 5.0 * nx * l2(nx) + 8.0 * dn));
+    HZ_TRY(ox->row_inv_acc(prec, out_kind, p->planes, rec, m->segtab, m->nseg, m->rowmask, m->K,
+                           rows, rows * nrhs, n, 1.0 / double(n), tw(tx), out, st));
+  }
   return HZ_OK;
 }
 
@@ -229,8 +260,10 @@ extern "C" hz_status hz_apply_operator(hz_plan* plan, const void* x, void* y, in
   if (nrhs < 1 || nrhs > plan->max_nrhs) return set_error(HZ_ERR_INVALID_ARG, "nrhs out of range");
   if (x == y) return set_error(HZ_ERR_INVALID_ARG, "x and y must not alias");
   const long n = plan->med->n;
-  return launch_stencil(plan->med, 0, x, n, static_cast<double2*>(y), n, nrhs, nullptr,
-                        static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  PhaseScope ps(st, PH_STENCIL, double(nrhs) * n * (48.0 + (plan->med->a ? 8.0 : 0.0)),
+                double(nrhs) * n * (plan->med->dim == 3 ? 30.0 : 26.0));
+  return launch_stencil(plan->med, 0, x, n, static_cast<double2*>(y), n, nrhs, nullptr, st);
 }
 
 extern "C" hz_status hz_apply_preconditioner(hz_plan* plan, const void* x, void* y, int nrhs,

@@ -163,7 +163,9 @@ constexpr int PAD_SHIFT = 4;
 __host__ __device__ constexpr int padded(int i) { return i + (i >> PAD_SHIFT); }
 __host__ __device__ constexpr int padded_len(int n) { return n + (n >> PAD_SHIFT) + 1; }
 
-template <typename R, int N, int S> struct LineFFT {
+// LS: distance in elements between consecutive positions of a line in shared
+// memory (1 for a private line, TB when TB lines are interleaved).
+template <typename R, int N, int S, int LS = 1> struct LineFFT {
   using V = typename cvec<R>::T;
   using P = FftPlan<N>;
   static constexpr int E = P::E;
@@ -178,7 +180,7 @@ template <typename R, int N, int S> struct LineFFT {
 
   __device__ static __forceinline__ void load_stage0(const V* line, int t, V (&x)[E]) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = line[padded(stage0_index(t, e))];
+    for (int e = 0; e < E; ++e) x[e] = line[padded(stage0_index(t, e)) * LS];
   }
 
   template <int STAGE, int NS>
@@ -190,7 +192,7 @@ template <typename R, int N, int S> struct LineFFT {
         for (int b = 0; b < E / RAD; ++b) {
           const int j = t + b * TPL;
 #pragma unroll
-          for (int r = 0; r < RAD; ++r) x[b * RAD + r] = line[padded(j + r * (N / RAD))];
+          for (int r = 0; r < RAD; ++r) x[b * RAD + r] = line[padded(j + r * (N / RAD)) * LS];
         }
         __syncthreads();
       }
@@ -209,7 +211,7 @@ template <typename R, int N, int S> struct LineFFT {
         dftR<RAD, S>(&x[b * RAD]);
         const int d = (j / NS) * NS * RAD + k;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) line[padded(d + r * NS)] = x[b * RAD + r];
+        for (int r = 0; r < RAD; ++r) line[padded(d + r * NS) * LS] = x[b * RAD + r];
       }
       __syncthreads();
       stage<STAGE + 1, NS * RAD>(line, t, x, tw);

@@ -47,9 +47,9 @@ hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segta
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
   auto k = row_inv_acc_kernel<R, N, OutT>;
-  HZ_TRY(smem_attr(k, C::row_smem()));
+  HZ_TRY(smem_attr(k, C::row_acc_smem()));
   const long blocks = (nrows + C::ROW_LINES - 1) / C::ROW_LINES;
-  k<<<unsigned(blocks), C::ROW_THREADS, C::row_smem(), st>>>(
+  k<<<unsigned(blocks), C::ROW_THREADS, C::row_acc_smem(), st>>>(
       static_cast<const V*>(planes), static_cast<const typename RecT<R>::T*>(rec), segtab, nseg,
       rowmask, K, rows_per_rhs, nrows, n, R(inv_n), static_cast<const V*>(tw),
       static_cast<OutT*>(out));
@@ -78,10 +78,10 @@ hz_status line_pass_t(void* data, int nx, long outer, long S, long ostride, long
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
   auto k = line_pass_kernel<R, N, SIGN>;
-  HZ_TRY(smem_attr(k, C::col_smem(false)));
+  HZ_TRY(smem_attr(k, C::col_smem()));
   const int ntile = (nx + C::TB - 1) / C::TB;
   dim3 grid(unsigned(ntile * outer), 1, unsigned(batch));
-  k<<<grid, C::COL_THREADS, C::col_smem(false), st>>>(static_cast<V*>(data), nx, ntile, S,
+  k<<<grid, C::COL_THREADS, C::col_smem(), st>>>(static_cast<V*>(data), nx, ntile, S,
                                                        ostride, bstride, omask, K,
                                                        static_cast<const V*>(tw));
   HZ_CUDA(cudaGetLastError());
@@ -99,24 +99,19 @@ hz_status line_pass(int prec, int sign, void* data, int nx, long outer, long S, 
 }
 
 template <typename R>
-hz_status line_fused_t(const void* in, void* planes, int nx, long outer, long S, long ostride,
-                       long n, int K, int batch, const void* xi2_x, const void* xi2_o,
-                       const void* xi2_l, const void* symA, const void* symG,
-                       const unsigned long long* smask, long smO, long smS, const void* tw,
-                       cudaStream_t st) {
+hz_status line_sym_inv_t(const void* vhat, void* planes, int nx, long outer, long S, long ostride,
+                         long n, int K, int batch, const void* xi2_x, const void* xi2_o,
+                         const void* xi2_l, const void* symA, const void* symG,
+                         const unsigned long long* smask, long smO, long smS, const void* tw,
+                         cudaStream_t st) {
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
-  auto k = line_fused_kernel<R, N>;
-  HZ_TRY(smem_attr(k, C::col_smem(true)));
+  auto k = line_sym_inv_kernel<R, N>;
+  HZ_TRY(smem_attr(k, C::col_smem()));
   const int ntile = (nx + C::TB - 1) / C::TB;
-  const long base_blocks = long(ntile) * outer * batch;
-  // split the K nodes over blocks until the grid covers the GPU about twice
-  int nks = int((2L * 152 + base_blocks - 1) / base_blocks);
-  if (nks < 1) nks = 1;
-  if (nks > K) nks = K;
-  dim3 grid(unsigned(ntile * outer), 1, unsigned(batch * nks));
-  k<<<grid, C::COL_THREADS, C::col_smem(true), st>>>(
-      static_cast<const V*>(in), static_cast<V*>(planes), nx, ntile, S, ostride, n, K, nks,
+  dim3 grid(unsigned(ntile * outer), unsigned(K), unsigned(batch));
+  k<<<grid, C::COL_THREADS, C::col_smem(), st>>>(
+      static_cast<const V*>(vhat), static_cast<V*>(planes), nx, ntile, S, ostride, n, K,
       static_cast<const R*>(xi2_x), static_cast<const R*>(xi2_o), static_cast<const R*>(xi2_l),
       static_cast<const V*>(symA), static_cast<const V*>(symG), smask, smO, smS,
       static_cast<const V*>(tw));
@@ -124,19 +119,19 @@ hz_status line_fused_t(const void* in, void* planes, int nx, long outer, long S,
   return HZ_OK;
 }
 
-hz_status line_fused(int prec, const void* in, void* planes, int nx, long outer, long S,
-                     long ostride, long n, int K, int batch, const void* xi2_x, const void* xi2_o,
-                     const void* xi2_l, const void* symA, const void* symG,
-                     const unsigned long long* smask, long smO, long smS, const void* tw,
-                     cudaStream_t st) {
+hz_status line_sym_inv(int prec, const void* vhat, void* planes, int nx, long outer, long S,
+                       long ostride, long n, int K, int batch, const void* xi2_x,
+                       const void* xi2_o, const void* xi2_l, const void* symA, const void* symG,
+                       const unsigned long long* smask, long smO, long smS, const void* tw,
+                       cudaStream_t st) {
   return prec == 0
-             ? line_fused_t<double>(in, planes, nx, outer, S, ostride, n, K, batch, xi2_x, xi2_o,
-                                    xi2_l, symA, symG, smask, smO, smS, tw, st)
-             : line_fused_t<float>(in, planes, nx, outer, S, ostride, n, K, batch, xi2_x, xi2_o,
-                                   xi2_l, symA, symG, smask, smO, smS, tw, st);
+             ? line_sym_inv_t<double>(vhat, planes, nx, outer, S, ostride, n, K, batch, xi2_x,
+                                      xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, st)
+             : line_sym_inv_t<float>(vhat, planes, nx, outer, S, ostride, n, K, batch, xi2_x,
+                                     xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, st);
 }
 
-const FftOps ops = {N, row_fwd, row_inv_acc, line_pass, line_fused};
+const FftOps ops = {N, row_fwd, row_inv_acc, line_pass, line_sym_inv};
 
 }  // namespace
 

@@ -2,11 +2,11 @@
 //
 //   row_fwd       forward FFT along x of the input vector (c128 in, scaled by
 //                 the Krylov normalisation, rounded to the working precision)
-//   line_pass     forward or inverse FFT along a strided axis (3D y axis)
-//   line_fused    last axis: forward FFT completes vhat, then for each node k
+//   line_pass     forward or inverse FFT along a strided axis (y, and z in 3D)
+//   line_sym_inv  last axis, one block per (column tile, node k): read vhat,
 //                 multiply by q_k(|xi|^2) = 1 / (w^2 + i w a_k - gamma_k^2 |xi|^2)
-//                 (Eqn. 021, recomputed, never stored) and inverse FFT along
-//                 the same axis, writing plane k
+//                 (Eqn. 021, recomputed, never stored), inverse FFT along the
+//                 axis, write plane k
 //   row_inv_acc   inverse FFT along x of every plane a row needs, then the
 //                 weighted sum z = (1/n) sum_k w_k(x) plane_k(x) (Eqn. 405:
 //                 two non-zero hat weights per point)
@@ -14,7 +14,8 @@
 // Layout: vectors [rhs][z][y][x] (x fastest); planes [rhs][k][z][y][x].
 // Every kernel stages its lines through padded shared memory and runs the
 // Stockham engine of fft_engine.cuh; global loads and stores are coalesced
-// along x (rows directly, strided axes in tiles of TB adjacent columns).
+// along x (rows directly, strided axes in tiles of TB adjacent columns whose
+// lines are interleaved in shared memory).
 #pragma once
 #include "fft_engine.cuh"
 #include "hz_internal.h"
@@ -30,21 +31,31 @@ template <typename R, int N> struct LineCfg {
   static constexpr int ROW_THREADS = TPL > 128 ? TPL : 128;
   static constexpr int ROW_LINES = ROW_THREADS / TPL;
   static constexpr int VB = int(2 * sizeof(R));
-  static constexpr int BUFS = sizeof(R) == 4 ? 1 : 2;  // fused kernel: spectrum copy for FP64
   static constexpr int tb_calc() {
-    int tb = 64 / VB;
+    int tb = 32 / VB;                 // one 32-byte sector per row at least
+    if (tb < 1) tb = 1;
     if (tb * TPL < 128) tb = 128 / TPL;
-    while (tb > 1 && tb * TPL > 512) tb /= 2;
-    while (tb > 1 && long(BUFS) * tb * padded_len(N) * VB > 200 * 1024) tb /= 2;
+    while (tb > 1 && tb * TPL > 256) tb /= 2;
+    while (tb > 1 && long(tb) * padded_len(N) * VB > 100 * 1024) tb /= 2;
     return tb;
   }
   static constexpr int TB = tb_calc();
   static constexpr int COL_THREADS = TB * TPL;
   static constexpr size_t row_smem() { return size_t(ROW_LINES) * padded_len(N) * VB; }
-  static constexpr size_t col_smem(bool fused) {
-    return size_t(fused ? BUFS : 1) * TB * padded_len(N) * VB;
-  }
+  // row_inv_acc: padded work lines, then (16-byte aligned for cp.async) two
+  // unpadded staging rows per line
+  static constexpr size_t stage_offset() { return (row_smem() + 15) / 16 * 16; }
+  static constexpr size_t row_acc_smem() { return stage_offset() + size_t(ROW_LINES) * 2 * N * VB; }
+  static constexpr size_t col_smem() { return size_t(TB) * padded_len(N) * VB; }
 };
+
+// 16-byte asynchronous global -> shared copies (L2 only), in groups.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = unsigned(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // Per-point interpolation record, complex64 path: segment in the top 8 bits,
 // t in [0, 1) as a 24-bit fraction.  The segment table maps a segment to
@@ -102,7 +113,9 @@ row_fwd_kernel(const double2* __restrict__ in, const double* __restrict__ scale,
 // planes: [rhs][K][n]; rec: per-point record (shared by all rhs); segtab:
 // (k_lo, k_hi) per segment; rowmask[row % rows_per_rhs] bit k = some point of
 // the row has a non-zero weight on node k (only those planes were written).
-// out[rhs][n] = inv_n * sum_k w_k plane_k.
+// out[rhs][n] = inv_n * sum_k w_k plane_k.  The block walks the planes its
+// rows need; the next plane's rows are copied into a shared staging buffer
+// with cp.async while the current plane is transformed.
 // ---------------------------------------------------------------------------
 template <typename R, int N, typename OutT>
 __global__ void __launch_bounds__(LineCfg<R, N>::ROW_THREADS)
@@ -114,6 +127,7 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
   using V = typename cvec<R>::T;
   using F = LineFFT<R, N, +1>;
   constexpr int TPL = F::TPL, E = F::E, LPB = LineCfg<R, N>::ROW_LINES;
+  constexpr int CH = N * int(sizeof(V)) / 16;  // 16-byte chunks per row
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
   __shared__ uchar2 seg_s[HZ_MAX_SEG];
@@ -129,6 +143,8 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
   __syncthreads();
   if (t == 0 && mymask) atomicOr(&cta_mask, mymask);
   V* line = sm + li * padded_len(N);
+  // two staging rows of this line; cp.async needs 16-byte aligned destinations
+  V* stg = reinterpret_cast<V*>(smem_raw + LineCfg<R, N>::stage_offset()) + li * 2 * N;
   typename RecT<R>::T r_[E];
   V acc[E];
 #pragma unroll
@@ -139,14 +155,35 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
   __syncthreads();
   const unsigned long long cm = cta_mask;
   const V* pbase = planes + (rhs * K) * n + lrow * N;
-  for (int k = 0; k < K; ++k) {
-    if (!((cm >> k) & 1ull)) continue;  // uniform over the block
-    const bool need = (mymask >> k) & 1ull;
+  auto issue = [&](int kk, int buf) {
+    if ((mymask >> kk) & 1ull) {
+      const char* src = reinterpret_cast<const char*>(pbase + long(kk) * n);
+      char* dst = reinterpret_cast<char*>(stg + buf * N);
+      for (int c = t; c < CH; c += TPL) cp_async16(dst + 16 * c, src + 16 * c);
+    }
+    cp_async_commit();
+  };
+  unsigned long long todo = cm;
+  int kc = todo ? __ffsll((long long)todo) - 1 : -1;
+  if (kc >= 0) {
+    todo &= todo - 1;
+    issue(kc, 0);
+  }
+  int buf = 0;
+  while (kc >= 0) {
+    const int kn = todo ? __ffsll((long long)todo) - 1 : -1;
+    if (kn >= 0) {
+      todo &= todo - 1;
+      issue(kn, buf ^ 1);
+    } else {
+      cp_async_commit();  // keep one group in flight per step
+    }
+    cp_async_wait1();   // this thread's copies of plane kc are done
+    __syncthreads();    // ... and everyone's; the previous results were read
+    const bool need = (mymask >> kc) & 1ull;
     V x[E];
-    const V* src = pbase + long(k) * n;
 #pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = need ? src[F::stage0_index(t, e)] : cmk<V>(R(0), R(0));
-    __syncthreads();  // previous plane's results have been read
+    for (int e = 0; e < E; ++e) x[e] = need ? stg[buf * N + F::stage0_index(t, e)] : cmk<V>(R(0), R(0));
     F::run(line, t, x, tw);
     if (need) {
 #pragma unroll
@@ -156,8 +193,8 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
         decode_rec(r_[i], seg, tf);
         const uchar2 kk = seg_s[seg];
         R w = R(0);
-        if (kk.x == k) w += R(1) - tf;
-        if (kk.y == k) w += tf;
+        if (kk.x == kc) w += R(1) - tf;
+        if (kk.y == kc) w += tf;
         if (w != R(0)) {
           const V v = line[padded(t + i * TPL)];
           acc[i].x += w * v.x;
@@ -165,6 +202,8 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
         }
       }
     }
+    kc = kn;
+    buf ^= 1;
   }
   if (valid) {
     OutT* dst = out + rhs * n + lrow * N;
@@ -180,10 +219,10 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
 
 // ---------------------------------------------------------------------------
 // Strided-axis kernels.  A line has N elements at stride S; a block handles
-// TB lines at adjacent x (thread = t * TB + column) so that loads and stores
-// move TB contiguous elements.  Line (x, o, b) starts at
-//   b * bstride + o * ostride + x.
-// grid.x = ceil(nx / TB) * outer, grid.z = batch (times K splits for fused).
+// TB lines at adjacent x (thread = t * TB + column), so that loads and stores
+// move TB contiguous elements, and keeps them interleaved in shared memory
+// (position p of column col at padded(p) * TB + col).  Line (x, o, b) starts
+// at b * bstride + o * ostride + x; grid.x = ceil(nx / TB) * outer.
 // ---------------------------------------------------------------------------
 template <typename R, int N, int SIGN>
 __global__ void __launch_bounds__(LineCfg<R, N>::COL_THREADS)
@@ -191,8 +230,9 @@ line_pass_kernel(typename cvec<R>::T* __restrict__ data, int nx, int ntile, long
                  long bstride, const unsigned long long* __restrict__ omask, int K,
                  const typename cvec<R>::T* __restrict__ tw) {
   using V = typename cvec<R>::T;
-  using F = LineFFT<R, N, SIGN>;
-  constexpr int TPL = F::TPL, E = F::E, TB = LineCfg<R, N>::TB;
+  constexpr int TB = LineCfg<R, N>::TB;
+  using F = LineFFT<R, N, SIGN, TB>;
+  constexpr int TPL = F::TPL, E = F::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
   const int col = threadIdx.x % TB, t = threadIdx.x / TB;
@@ -203,86 +243,68 @@ line_pass_kernel(typename cvec<R>::T* __restrict__ data, int nx, int ntile, long
   // omask (planes only): skip outer slices o that no row of plane k needs
   if (omask && !((omask[o] >> (blockIdx.z % K)) & 1ull)) return;
   V* base = data + long(blockIdx.z) * bstride + o * ostride + x;
-  V* line = sm + col * padded_len(N);
+  V* line = sm + col;
   V v[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) v[e] = valid ? base[long(F::stage0_index(t, e)) * S] : cmk<V>(R(0), R(0));
   F::run(line, t, v, tw);
   if (valid) {
 #pragma unroll
-    for (int i = 0; i < E; ++i) base[long(t + i * TPL) * S] = line[padded(t + i * TPL)];
+    for (int i = 0; i < E; ++i) base[long(t + i * TPL) * S] = line[padded(t + i * TPL) * TB];
   }
 }
 
-// Last-axis fused kernel.  in: forward transform along every other axis
-// ([rhs][n]); planes out: [rhs][K][n].  xi2_x[x] + xi2_o[o] + xi2_l[p] is
-// |xi|^2 at (x, o, p).  Block (tile, o) of K-split ks handles nodes
-// k = ks, ks + nks, ...  Plane k is only stored where smask[o smO + p smS]
-// has bit k: per row in 2D (the next pass is the x inverse), per z-slab in 3D
-// (the next pass is the y inverse, which needs the whole slab).
+// Last axis, one block per (column tile and outer index, node k, rhs): the
+// spectrum vhat (transformed along every axis) times q_k, inverse FFT along
+// the axis, written to plane k.  |xi|^2 = xi2_x[x] + xi2_o[o] + xi2_l[p].
+// Plane k is only stored where smask[o smO + p smS] has bit k: per row in 2D
+// (the next pass is the x inverse), per z-slab in 3D (the next pass is the y
+// inverse, which needs the whole slab).
 template <typename R, int N>
 __global__ void __launch_bounds__(LineCfg<R, N>::COL_THREADS)
-line_fused_kernel(const typename cvec<R>::T* __restrict__ in, typename cvec<R>::T* __restrict__ planes,
-                  int nx, int ntile, long S, long ostride, long n, int K, int nks,
-                  const R* __restrict__ xi2_x, const R* __restrict__ xi2_o,
-                  const R* __restrict__ xi2_l, const typename cvec<R>::T* __restrict__ symA,
-                  const typename cvec<R>::T* __restrict__ symG,
-                  const unsigned long long* __restrict__ smask, long smO, long smS,
-                  const typename cvec<R>::T* __restrict__ tw) {
+line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
+                    typename cvec<R>::T* __restrict__ planes, int nx, int ntile, long S,
+                    long ostride, long n, int K, const R* __restrict__ xi2_x,
+                    const R* __restrict__ xi2_o, const R* __restrict__ xi2_l,
+                    const typename cvec<R>::T* __restrict__ symA,
+                    const typename cvec<R>::T* __restrict__ symG,
+                    const unsigned long long* __restrict__ smask, long smO, long smS,
+                    const typename cvec<R>::T* __restrict__ tw) {
   using V = typename cvec<R>::T;
-  using Ff = LineFFT<R, N, -1>;
-  using Fi = LineFFT<R, N, +1>;
-  constexpr int TPL = Ff::TPL, E = Ff::E, TB = LineCfg<R, N>::TB;
-  constexpr bool SPEC_REGS = sizeof(R) == 4;
+  constexpr int TB = LineCfg<R, N>::TB;
+  using F = LineFFT<R, N, +1, TB>;
+  constexpr int TPL = F::TPL, E = F::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
   const int col = threadIdx.x % TB, t = threadIdx.x / TB;
   const int tile = blockIdx.x % ntile;
   const long o = blockIdx.x / ntile;
+  const int k = blockIdx.y;
+  const long rhs = blockIdx.z;
   const int x = tile * TB + col;
   const bool valid = x < nx;
-  const long rhs = blockIdx.z / nks;
-  const int ks = blockIdx.z % nks;
   const long off = o * ostride + x;
-  const V* src = in + rhs * n + off;
-  V* line = sm + col * padded_len(N);
-  V* specs = sm + (TB + col) * padded_len(N);  // used when !SPEC_REGS
+  const V* src = vhat + rhs * n + off;
+  const V A = symA[k], G = symG[k];
+  const R sxo = (valid ? xi2_x[x] : R(0)) + (xi2_o ? xi2_o[o] : R(0));
   V v[E];
 #pragma unroll
-  for (int e = 0; e < E; ++e) v[e] = valid ? src[long(Ff::stage0_index(t, e)) * S] : cmk<V>(R(0), R(0));
-  Ff::run(line, t, v, tw);
-  // the spectrum in the inverse transform's stage-0 order, and |xi|^2 there
-  V spec[SPEC_REGS ? E : 1];
-  R s2[E];
-  const R sxo = (valid ? xi2_x[x] : R(0)) + (xi2_o ? xi2_o[o] : R(0));
-#pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int p = Fi::stage0_index(t, e);
-    if constexpr (SPEC_REGS) spec[e] = line[padded(p)];
-    else specs[padded(p)] = line[padded(p)];
-    s2[e] = sxo + xi2_l[p];
+    const int p = F::stage0_index(t, e);
+    const V sv = valid ? src[long(p) * S] : cmk<V>(R(0), R(0));
+    const R s2 = sxo + xi2_l[p];
+    // q = 1 / (A - G s) = conj(den) / |den|^2
+    const V den = cmk<V>(A.x - G.x * s2, A.y - G.y * s2);
+    const R inv = R(1) / (den.x * den.x + den.y * den.y);
+    v[e] = cmul(sv, cmk<V>(den.x * inv, -den.y * inv));
   }
-  for (int k = ks; k < K; k += nks) {
-    const V A = symA[k], G = symG[k];
+  F::run(sm + col, t, v, tw);
+  if (valid) {
+    V* dst = planes + (rhs * K + k) * n + off;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int p = Fi::stage0_index(t, e);
-      const V sv = SPEC_REGS ? spec[SPEC_REGS ? e : 0] : specs[padded(p)];
-      // q = 1 / (A - G s) = conj(den) / |den|^2
-      const V den = cmk<V>(A.x - G.x * s2[e], A.y - G.y * s2[e]);
-      const R inv = R(1) / (den.x * den.x + den.y * den.y);
-      const V q = cmk<V>(den.x * inv, -den.y * inv);
-      v[e] = cmul(sv, q);
-    }
-    __syncthreads();  // every thread is done reading the previous result
-    Fi::run(line, t, v, tw);
-    if (valid) {
-      V* dst = planes + (rhs * K + k) * n + off;
-#pragma unroll
-      for (int i = 0; i < E; ++i) {
-        const int p = t + i * TPL;
-        if ((smask[o * smO + long(p) * smS] >> k) & 1ull) dst[long(p) * S] = line[padded(p)];
-      }
+    for (int i = 0; i < E; ++i) {
+      const int p = t + i * TPL;
+      if ((smask[o * smO + long(p) * smS] >> k) & 1ull) dst[long(p) * S] = sm[padded(p) * TB + col];
     }
   }
 }

@@ -110,7 +110,11 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
   const int nblk_r = stencil_blocks(n);
   const int nblk_k = krylov_blocks(n, nrhs, (m + 1 + 7) / 8);
   const int nblk_n = krylov_blocks(n, nrhs, 1);
-  HZ_TRY(launch_norm2(f, n, n, nrhs, p->partial, nblk_n, ks.bnorm, st));
+  const double Bn = double(nrhs) * n;
+  {
+    PhaseScope ps(st, PH_NORM, 16.0 * Bn, 4.0 * Bn, 2);
+    HZ_TRY(launch_norm2(f, n, n, nrhs, p->partial, nblk_n, ks.bnorm, st));
+  }
   std::vector<double> bnorm(nrhs), rn2(nrhs);
   HZ_CUDA(cudaMemcpyAsync(bnorm.data(), ks.bnorm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
   HZ_CUDA(cudaStreamSynchronize(st));
@@ -134,8 +138,11 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
 
   for (;;) {
     // true FP64 residual r = f - P u into V_0
-    HZ_TRY(launch_residual(med, u, f, p->V, n, nrhs, nullptr, p->partial, st));
-    HZ_TRY(launch_reduce_r(p->partial, nblk_r, nrhs, w.rnorm2, st));
+    {
+      PhaseScope ps(st, PH_RESID, 64.0 * Bn + (med->a ? 8.0 * Bn : 0.0), 30.0 * Bn, 2);
+      HZ_TRY(launch_residual(med, u, f, p->V, n, nrhs, nullptr, p->partial, st));
+      HZ_TRY(launch_reduce_r(p->partial, nblk_r, nrhs, w.rnorm2, st));
+    }
     HZ_CUDA(cudaMemcpyAsync(rn2.data(), w.rnorm2, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
     HZ_CUDA(cudaStreamSynchronize(st));
     int live = 0;
@@ -181,25 +188,36 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
       const double2* Vj = p->V + long(j) * ldb * n;
       double2* Vn = p->V + long(j + 1) * ldb * n;
       const double* sig_j = ks.sigma + long(j) * B;
+      const double stb = Bn * ((prec == 1 ? 8.0 : 16.0) + 32.0 + (med->a ? 8.0 : 0.0));
+      const double stf = Bn * (med->dim == 3 ? 30.0 : 26.0);
       if (prec == 1) {
         float2* Zj = static_cast<float2*>(p->Z) + long(j) * ldb * n;
         HZ_TRY(precond_apply(p, 1, Vj, sig_j, nrhs, Zj, 0, st));
+        PhaseScope ps(st, PH_STENCIL, stb, stf);
         HZ_TRY(launch_stencil(med, 1, Zj, n, Vn, n, nrhs, ks.active, st));
       } else {
         double2* zt = static_cast<double2*>(p->Z);
         HZ_TRY(precond_apply(p, 0, Vj, sig_j, nrhs, zt, 1, st));
+        PhaseScope ps(st, PH_STENCIL, stb, stf);
         HZ_TRY(launch_stencil(med, 0, zt, n, Vn, n, nrhs, ks.active, st));
       }
-      // CGS2
-      HZ_TRY(launch_dots(p->V, ldb, Vn, n, n, j, nrhs, ks.active, reinterpret_cast<double2*>(p->partial),
-                         nblk_k, ks.S1, m + 1, st));
-      HZ_TRY(launch_update(p->V, ldb, Vn, n, n, j, nrhs, ks.S1, m + 1, ks.sigma, B, ks.active, false,
-                           nullptr, nblk_k, nullptr, st));
-      HZ_TRY(launch_dots(p->V, ldb, Vn, n, n, j, nrhs, ks.active, reinterpret_cast<double2*>(p->partial),
-                         nblk_k, ks.S2, m + 1, st));
-      HZ_TRY(launch_update(p->V, ldb, Vn, n, n, j, nrhs, ks.S2, m + 1, ks.sigma, B, ks.active, true,
-                           p->partial, nblk_k, ks.nrm2, st));
-      HZ_TRY(launch_givens(ks, j, nrhs, st));
+      // CGS2: two passes of classical Gram-Schmidt against v_0 .. v_j
+      const double db = 16.0 * Bn * (j + 2), ub = 16.0 * Bn * (j + 3), fl = 8.0 * Bn * (j + 1);
+      for (int pass = 0; pass < 2; ++pass) {
+        double2* S = pass == 0 ? ks.S1 : ks.S2;
+        {
+          PhaseScope ps(st, PH_DOTS, db, fl, 2);
+          HZ_TRY(launch_dots(p->V, ldb, Vn, n, n, j, nrhs, ks.active,
+                             reinterpret_cast<double2*>(p->partial), nblk_k, S, m + 1, st));
+        }
+        PhaseScope ps(st, PH_UPDATE, ub, fl + (pass ? 4.0 * Bn : 0.0), pass ? 2 : 1);
+        HZ_TRY(launch_update(p->V, ldb, Vn, n, n, j, nrhs, S, m + 1, ks.sigma, B, ks.active, pass == 1,
+                             p->partial, nblk_k, ks.nrm2, st));
+      }
+      {
+        PhaseScope ps(st, PH_GIVENS, 0.0, 0.0);
+        HZ_TRY(launch_givens(ks, j, nrhs, st));
+      }
       HZ_CUDA(cudaMemcpyAsync(&w.h_nact[j & 1], ks.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
       HZ_CUDA(cudaEventRecord(w.ev[j & 1], st));
       if (j >= 1) {
@@ -246,14 +264,20 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
     int* d_jn = ks.jend;  // reuse: per-rhs number of columns to add (0 = skip)
     HZ_CUDA(cudaMemcpyAsync(d_jn, jn.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
     HZ_CUDA(cudaMemcpyAsync(w.y, h_y.data(), size_t(nrhs) * m * sizeof(double2), cudaMemcpyHostToDevice, st));
+    const int Jmax = *std::max_element(jn.begin(), jn.end());
     if (prec == 1) {
+      PhaseScope ps(st, PH_SOLUPD, Bn * (8.0 * Jmax + 32.0), Bn * 8.0 * Jmax);
       HZ_TRY(launch_solution_update(1, p->Z, ldb, u, n, n, nrhs, w.y, m, d_jn, st));
     } else {
       // t = V (sigma y), then u += Q_M t in complex128
       double2* t = p->V + long(m) * ldb * n;  // V_m is free once the cycle is over
-      HZ_TRY(launch_combine(p->V, ldb, t, n, n, nrhs, w.y, m, ks.sigma, B, d_jn, st));
+      {
+        PhaseScope ps(st, PH_SOLUPD, Bn * (16.0 * Jmax + 16.0), Bn * 8.0 * Jmax);
+        HZ_TRY(launch_combine(p->V, ldb, t, n, n, nrhs, w.y, m, ks.sigma, B, d_jn, st));
+      }
       double2* zt = static_cast<double2*>(p->Z);
       HZ_TRY(precond_apply(p, 0, t, nullptr, nrhs, zt, 1, st));
+      PhaseScope ps(st, PH_SOLUPD, Bn * 48.0, Bn * 2.0);
       HZ_TRY(launch_axpy(u, zt, n, n, nrhs, d_jn, st));
     }
     HZ_CUDA(cudaStreamSynchronize(st));

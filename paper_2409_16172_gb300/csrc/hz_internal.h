@@ -95,6 +95,9 @@ struct hz_medium {
   float2* symG32 = nullptr;
   hz::AxisTables ax[3];
   double inv_h2[3] = {0, 0, 0};
+  // sum over x-rows (3D: also z-slabs) of the number of nodes used there;
+  // the symbol planes are only written and read for these (row, k) pairs
+  double rowk_used = 0, slabk_used = 0;
 };
 
 namespace hz {
@@ -116,15 +119,33 @@ struct FftOps {
                          long ostride, long bstride, int batch,
                          const unsigned long long* omask, int K, const void* tw,
                          cudaStream_t st);
-  // last-axis fused forward * symbol * inverse
-  hz_status (*line_fused)(int prec, const void* in, void* planes, int nx, long outer, long S,
-                          long ostride, long n, int K, int batch, const void* xi2_x,
-                          const void* xi2_o, const void* xi2_l, const void* symA,
-                          const void* symG, const unsigned long long* smask, long smO,
-                          long smS, const void* tw, cudaStream_t st);
+  // last axis: symbol multiply of the spectrum and inverse FFT, one plane per k
+  hz_status (*line_sym_inv)(int prec, const void* vhat, void* planes, int nx, long outer, long S,
+                            long ostride, long n, int K, int batch, const void* xi2_x,
+                            const void* xi2_o, const void* xi2_l, const void* symA,
+                            const void* symG, const unsigned long long* smask, long smO,
+                            long smS, const void* tw, cudaStream_t st);
 };
 
 const FftOps* fft_ops(int N);
+
+// ---- measurement (profile.cu) ----
+enum Phase {
+  PH_ROW_FWD = 0, PH_LINE, PH_SYMINV, PH_ROW_INV, PH_STENCIL, PH_DOTS, PH_UPDATE, PH_GIVENS,
+  PH_SOLUPD, PH_RESID, PH_NORM, PH_COUNT
+};
+void count_launches(int k);
+bool profiling();
+// Records an event pair around the launches made while it is alive.
+struct PhaseScope {
+  PhaseScope(cudaStream_t st, Phase ph, double bytes, double flops, int launches = 1);
+  ~PhaseScope();
+  cudaStream_t st;
+  Phase ph;
+  double bytes, flops;
+  int launches;
+  int slot = -1;
+};
 
 }  // namespace hz
 

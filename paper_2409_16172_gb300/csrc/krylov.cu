@@ -42,10 +42,12 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
   __syncthreads();
 }
 
-// S[b][i] partials: raw sums sum_p conj(V_i[p]) w[p] for i in [i0, i0 + VC),
-// i <= j.  grid = (nblk, nrhs, nchunk).  partial layout
-// [(b * (j+1) + i) * nblk + blk] as double2.
-__global__ void __launch_bounds__(KT)
+// S[b][i] partials: raw sums sum_p conj(V_i[p]) w[p] for i in [i0, i0 + nv),
+// nv = min(VC, j + 1 - i0).  grid = (nblk, nrhs, nchunk).  partial layout
+// [(b * (j+1) + i) * nblk + blk] as double2.  The next point's operands are
+// loaded before the current point's FMAs so that the FP64 pipe, the limit
+// here, does not wait on memory; only the nv live accumulators are reduced.
+__global__ void __launch_bounds__(KT, 2)
 dots_kernel(const double2* __restrict__ V, long ldb, const double2* __restrict__ w, long wstride,
             long n, int j, const int* __restrict__ active, double2* __restrict__ partial) {
   const int b = blockIdx.y;
@@ -57,25 +59,60 @@ dots_kernel(const double2* __restrict__ V, long ldb, const double2* __restrict__
   const bool on = active[b] != 0;
   if (on) {
     const double2* wb = w + b * wstride;
-    for (long p = long(blockIdx.x) * KT + threadIdx.x; p < n; p += long(gridDim.x) * KT) {
-      const double2 x = wb[p];
+    const double2* Vb = V + (long(i0) * ldb + b) * n;
+    const long vs = ldb * n;
+    const long step = long(gridDim.x) * KT;
+    long p = long(blockIdx.x) * KT + threadIdx.x;
+    double2 x, v[VC];
+    if (p < n) {
+      x = wb[p];
+#pragma unroll
+      for (int c = 0; c < VC; ++c)
+        if (c < nv) v[c] = Vb[c * vs + p];
+    }
+    while (p < n) {
+      const long q = p + step;
+      double2 xn, vn[VC];
+      if (q < n) {
+        xn = wb[q];
+#pragma unroll
+        for (int c = 0; c < VC; ++c)
+          if (c < nv) vn[c] = Vb[c * vs + q];
+      }
 #pragma unroll
       for (int c = 0; c < VC; ++c) {
         if (c < nv) {
-          const double2 v = V[(long(i0 + c) * ldb + b) * n + p];
-          acc[2 * c] = fma(v.x, x.x, fma(v.y, x.y, acc[2 * c]));
-          acc[2 * c + 1] = fma(v.x, x.y, fma(-v.y, x.x, acc[2 * c + 1]));
+          acc[2 * c] = fma(v[c].x, x.x, fma(v[c].y, x.y, acc[2 * c]));
+          acc[2 * c + 1] = fma(v[c].x, x.y, fma(-v[c].y, x.x, acc[2 * c + 1]));
         }
       }
+      p = q;
+      x = xn;
+#pragma unroll
+      for (int c = 0; c < VC; ++c) v[c] = vn[c];
     }
   }
-  __shared__ double sh[(KT / 32 + 1) * 2 * VC];
-  block_sum<2 * VC>(acc, sh);
-  if (threadIdx.x < nv) {
-    const double* r = sh + (KT / 32) * 2 * VC;
-    partial[(long(b) * (j + 1) + i0 + threadIdx.x) * gridDim.x + blockIdx.x] =
-        make_double2(r[2 * threadIdx.x], r[2 * threadIdx.x + 1]);
+  // block reduction of the 2 nv live sums (warp shuffles, then one value per warp)
+  __shared__ double sh[(KT / 32) * 2 * VC];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < 2 * VC; ++c) {
+    if (c < 2 * nv) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
+      if (lane == 0) sh[warp * 2 * VC + c] = acc[c];
+    }
   }
+  __syncthreads();
+  if (threadIdx.x < 2 * nv) {
+    double s = 0.0;
+    for (int wi = 0; wi < KT / 32; ++wi) s += sh[wi * 2 * VC + threadIdx.x];
+    sh[threadIdx.x] = s;  // rows 0..: warp 0's slots are no longer needed
+  }
+  __syncthreads();
+  if (threadIdx.x < nv)
+    partial[(long(b) * (j + 1) + i0 + threadIdx.x) * gridDim.x + blockIdx.x] =
+        make_double2(sh[2 * threadIdx.x], sh[2 * threadIdx.x + 1]);
 }
 
 // Sum partials in a fixed order: q = b * jp1 + i,
@@ -126,14 +163,34 @@ update_kernel(const double2* __restrict__ V, long ldb, double2* __restrict__ w, 
   double nrm[1] = {0.0};
   if (on) {
     double2* wb = w + b * wstride;
+    const double2* Vb = V + long(b) * n;
+    const long vs = ldb * n;  // stride between basis vectors
     for (long p = long(blockIdx.x) * KT + threadIdx.x; p < n; p += long(gridDim.x) * KT) {
-      double2 x = wb[p];
-      for (int i = 0; i <= j; ++i) {
-        const double2 v = V[(long(i) * ldb + b) * n + p];
-        const double2 c = coef[i];
-        x.x = fma(-c.x, v.x, fma(c.y, v.y, x.x));
-        x.y = fma(-c.x, v.y, fma(-c.y, v.x, x.y));
+      // d = sum_i c_i V_i[p] in two interleaved partial sums; loads hoisted
+      double dr0 = 0.0, di0 = 0.0, dr1 = 0.0, di1 = 0.0;
+      int i = 0;
+      for (; i + 3 <= j; i += 4) {
+        const double2 v0 = Vb[(i + 0) * vs + p], v1 = Vb[(i + 1) * vs + p];
+        const double2 v2 = Vb[(i + 2) * vs + p], v3 = Vb[(i + 3) * vs + p];
+        const double2 c0 = coef[i], c1 = coef[i + 1], c2 = coef[i + 2], c3 = coef[i + 3];
+        dr0 = fma(c0.x, v0.x, fma(-c0.y, v0.y, dr0));
+        di0 = fma(c0.x, v0.y, fma(c0.y, v0.x, di0));
+        dr1 = fma(c1.x, v1.x, fma(-c1.y, v1.y, dr1));
+        di1 = fma(c1.x, v1.y, fma(c1.y, v1.x, di1));
+        dr0 = fma(c2.x, v2.x, fma(-c2.y, v2.y, dr0));
+        di0 = fma(c2.x, v2.y, fma(c2.y, v2.x, di0));
+        dr1 = fma(c3.x, v3.x, fma(-c3.y, v3.y, dr1));
+        di1 = fma(c3.x, v3.y, fma(c3.y, v3.x, di1));
       }
+      for (; i <= j; ++i) {
+        const double2 v = Vb[i * vs + p];
+        const double2 c = coef[i];
+        dr0 = fma(c.x, v.x, fma(-c.y, v.y, dr0));
+        di0 = fma(c.x, v.y, fma(c.y, v.x, di0));
+      }
+      double2 x = wb[p];
+      x.x -= dr0 + dr1;
+      x.y -= di0 + di1;
       wb[p] = x;
       if (NORM) nrm[0] = fma(x.x, x.x, fma(x.y, x.y, nrm[0]));
     }
@@ -150,72 +207,100 @@ __device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 conj_d(double2 a) { return make_double2(a.x, -a.y); }
 
-// One thread per right-hand side: form column j of the Hessenberg matrix,
-// apply the earlier rotations, build the new one (c real, G [a;b] = [r;0]),
-// update g and the residual estimate, and retire converged / broken rows.
+// One warp per right-hand side: form column j of the Hessenberg matrix in
+// shared memory, apply the earlier rotations (serial, lane 0), build the new
+// one (c real, G [a;b] = [r;0]), update g and the residual estimate, and
+// retire converged / broken rows.
 __global__ void givens_kernel(KsDev ks, int j, int nrhs) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.x;
+  const int lane = threadIdx.x;
   if (b >= nrhs || !ks.active[b]) return;
   const int m = ks.m;
-  double2* col = ks.H + (long(b) * m + j) * (m + 1);
+  __shared__ double2 col[HZ_MAX_RESTART + 2];
+  __shared__ double2 sn_s[HZ_MAX_RESTART];
+  __shared__ double cs_s[HZ_MAX_RESTART];
+  double2* colg = ks.H + (long(b) * m + j) * (m + 1);
   const double2* S1 = ks.S1 + long(b) * (m + 1);
   const double2* S2 = ks.S2 + long(b) * (m + 1);
-  bool bad = false;
-  double hmax = 0.0;
-  for (int i = 0; i <= j; ++i) {
-    const double s = ks.sigma[long(i) * ks.ldsig + b];
-    col[i] = make_double2(s * (S1[i].x + S2[i].x), s * (S1[i].y + S2[i].y));
-    hmax = fmax(hmax, hypot(col[i].x, col[i].y));
-    bad |= !isfinite(col[i].x) || !isfinite(col[i].y);
-  }
-  const double hn = sqrt(ks.nrm2[b]);
-  bad |= !isfinite(hn);
-  col[j + 1] = make_double2(hn, 0.0);
-  const bool happy = hn <= 1e-14 * hmax;
-  ks.sigma[long(j + 1) * ks.ldsig + b] = (hn > 0.0 && !happy) ? 1.0 / hn : 0.0;
   double* cs = ks.cs + long(b) * m;
   double2* sn = ks.sn + long(b) * m;
   double2* g = ks.g + long(b) * (m + 1);
-  for (int i = 0; i < j; ++i) {
-    const double2 t = make_double2(cs[i] * col[i].x, cs[i] * col[i].y);
-    const double2 u = cmul_d(sn[i], col[i + 1]);
-    const double2 lo = cmul_d(conj_d(sn[i]), col[i]);
-    col[i + 1] = make_double2(cs[i] * col[i + 1].x - lo.x, cs[i] * col[i + 1].y - lo.y);
-    col[i] = make_double2(t.x + u.x, t.y + u.y);
+  double hmax = 0.0;
+  bool bad = false;
+  for (int i = lane; i <= j; i += 32) {
+    const double s = ks.sigma[long(i) * ks.ldsig + b];
+    const double2 h = make_double2(s * (S1[i].x + S2[i].x), s * (S1[i].y + S2[i].y));
+    col[i] = h;
+    hmax = fmax(hmax, fmax(fabs(h.x), fabs(h.y)));
+    bad |= !isfinite(h.x) || !isfinite(h.y);
   }
-  const double2 a = col[j];
-  const double aa = hypot(a.x, a.y);
-  double c;
-  double2 s, r;
-  if (hn == 0.0) {
-    c = 1.0; s = make_double2(0.0, 0.0); r = a;
-  } else if (aa == 0.0) {
-    c = 0.0; s = make_double2(1.0, 0.0); r = make_double2(hn, 0.0);
-  } else {
-    const double rho = hypot(aa, hn);
-    c = aa / rho;
-    const double2 ph = make_double2(a.x / aa, a.y / aa);
-    s = make_double2(ph.x * hn / rho, ph.y * hn / rho);   // ph * conj(hn) / rho, hn real
-    r = make_double2(ph.x * rho, ph.y * rho);
+  for (int i = lane; i < j; i += 32) {
+    cs_s[i] = cs[i];
+    sn_s[i] = sn[i];
   }
-  cs[j] = c;
-  sn[j] = s;
-  col[j] = r;
-  col[j + 1] = make_double2(0.0, 0.0);
-  const double2 gj = g[j];
-  g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));  // -conj(s) g_j
-  g[j] = make_double2(c * gj.x, c * gj.y);
-  const double est = hypot(g[j + 1].x, g[j + 1].y);
-  ks.est[b] = est;
-  ks.jend[b] = j + 1;
-  bad |= !isfinite(est) || !isfinite(r.x) || !isfinite(r.y);
-  if (bad) {
-    ks.status[b] = HZ_ERR_BREAKDOWN;
-    ks.active[b] = 0;
-  } else if (est <= ks.tol * ks.bnorm[b] || happy) {
-    ks.active[b] = 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) hmax = fmax(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+  bad = __any_sync(0xffffffffu, bad);
+  __syncwarp();
+  if (lane == 0) {
+    const double hn = sqrt(ks.nrm2[b]);
+    bad |= !isfinite(hn);
+    const bool happy = hn <= 1e-14 * hmax;
+    ks.sigma[long(j + 1) * ks.ldsig + b] = (hn > 0.0 && !happy) ? 1.0 / hn : 0.0;
+    for (int i = 0; i < j; ++i) {
+      const double c = cs_s[i];
+      const double2 sv = sn_s[i], a0 = col[i], a1 = col[i + 1];
+      const double2 u = cmul_d(sv, a1);
+      const double2 lo = cmul_d(conj_d(sv), a0);
+      col[i] = make_double2(c * a0.x + u.x, c * a0.y + u.y);
+      col[i + 1] = make_double2(c * a1.x - lo.x, c * a1.y - lo.y);
+    }
+    const double2 a = col[j];
+    const double aa = hypot(a.x, a.y);
+    double c;
+    double2 s, r;
+    if (hn == 0.0) {
+      c = 1.0; s = make_double2(0.0, 0.0); r = a;
+    } else if (aa == 0.0) {
+      c = 0.0; s = make_double2(1.0, 0.0); r = make_double2(hn, 0.0);
+    } else {
+      const double rho = hypot(aa, hn);
+      const double inv_aa = 1.0 / aa, inv_rho = 1.0 / rho;
+      c = aa * inv_rho;
+      const double2 ph = make_double2(a.x * inv_aa, a.y * inv_aa);
+      s = make_double2(ph.x * hn * inv_rho, ph.y * hn * inv_rho);  // ph conj(hn) / rho
+      r = make_double2(ph.x * rho, ph.y * rho);
+    }
+    cs[j] = c;
+    sn[j] = s;
+    col[j] = r;
+    col[j + 1] = make_double2(0.0, 0.0);
+    const double2 gj = g[j];
+    const double2 gn = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
+    g[j + 1] = gn;  // -conj(s) g_j
+    g[j] = make_double2(c * gj.x, c * gj.y);
+    const double est = hypot(gn.x, gn.y);
+    ks.est[b] = est;
+    ks.jend[b] = j + 1;
+    bad |= !isfinite(est) || !isfinite(r.x) || !isfinite(r.y);
+    int act = 1;
+    if (bad) {
+      ks.status[b] = HZ_ERR_BREAKDOWN;
+      act = 0;
+    } else if (est <= ks.tol * ks.bnorm[b] || happy) {
+      act = 0;
+    }
+    if (!act) {
+      ks.active[b] = 0;
+      atomicSub(ks.n_active, 1);
+    }
   }
-  if (!ks.active[b]) atomicSub(ks.n_active, 1);
+  __syncwarp();
+  for (int i = lane; i <= j + 1; i += 32) colg[i] = col[i];
+  for (int i = lane; i < j; i += 32) {
+    cs[i] = cs_s[i];
+    sn[i] = sn_s[i];
+  }
 }
 
 // u += sum_{i < jn} y[b][i] Z_i  (Z in c64 or c128), one pass.
@@ -308,9 +393,14 @@ int krylov_blocks(long n, int nrhs, int nchunk) {
 }
 
 hz_status launch_dots(const double2* V, long ldb, const double2* w, long wstride, long n, int j,
-                      int nrhs, const int* active, double2* partial, int nblk, double2* S, int ldS,
-                      cudaStream_t st) {
+                      int nrhs, const int* active, double2* partial, int /*unused*/, double2* S,
+                      int ldS, cudaStream_t st) {
   const int nchunk = (j + 1 + VC - 1) / VC;
+  // enough blocks to fill the GPU, but >= 16 points per thread when n allows,
+  // so that the block reductions stay small next to the FMAs
+  int nblk = krylov_blocks(n, nrhs, nchunk);
+  const long cap = (n + 16L * KT - 1) / (16L * KT);
+  if (nblk > cap) nblk = int(cap > 0 ? cap : 1);
   dots_kernel<<<dim3(nblk, nrhs, nchunk), KT, 0, st>>>(V, ldb, w, wstride, n, j, active, partial);
   reduce_c_kernel<<<unsigned(nrhs * (j + 1)), KT, 0, st>>>(partial, nblk, j + 1, ldS, S);
   HZ_CUDA(cudaGetLastError());
@@ -319,8 +409,9 @@ hz_status launch_dots(const double2* V, long ldb, const double2* w, long wstride
 
 hz_status launch_update(const double2* V, long ldb, double2* w, long wstride, long n, int j,
                         int nrhs, const double2* S, int ldS, const double* sigma, int ldsig,
-                        const int* active, bool norm, double* partial, int nblk, double* nrm2,
+                        const int* active, bool norm, double* partial, int /*unused*/, double* nrm2,
                         cudaStream_t st) {
+  const int nblk = krylov_blocks(n, nrhs, 1);
   if (norm) {
     update_kernel<true><<<dim3(nblk, nrhs), KT, 0, st>>>(V, ldb, w, wstride, n, j, S, ldS, sigma,
                                                           ldsig, active, partial);
@@ -334,7 +425,7 @@ hz_status launch_update(const double2* V, long ldb, double2* w, long wstride, lo
 }
 
 hz_status launch_givens(const KsDev& ks, int j, int nrhs, cudaStream_t st) {
-  givens_kernel<<<(nrhs + 63) / 64, 64, 0, st>>>(ks, j, nrhs);
+  givens_kernel<<<nrhs, 32, 0, st>>>(ks, j, nrhs);
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }

@@ -367,8 +367,21 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
   record_kernel<<<unsigned((n + 255) / 256), 256>>>(dc, dz, n, m->nx, nd, m->rec64, m->rec32,
                                                    m->gamma2, m->rowmask);
   slab_kernel<<<(m->nz + 127) / 128, 128>>>(m->rowmask, m->ny, m->nz, m->slabmask);
+  count_launches(4);
   ce = cudaGetLastError();
   if (ce != cudaSuccess) return fail(cuda_error(ce, "record kernel"));
+  {
+    std::vector<unsigned long long> rm(nrows), sm(m->nz);
+    ce = cudaMemcpy(rm.data(), m->rowmask, nrows * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpy(sm.data(), m->slabmask, m->nz * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return fail(cuda_error(ce, "mask readback"));
+    double ru = 0, su = 0;
+    for (auto v : rm) ru += __builtin_popcountll(v);
+    for (auto v : sm) su += __builtin_popcountll(v);
+    m->rowk_used = ru;
+    m->slabk_used = su;
+  }
 
   // symbol constants A_k = w^2 + i w a_k, G_k = gamma_k^2
   std::vector<double2> A(m->K), G(m->K);

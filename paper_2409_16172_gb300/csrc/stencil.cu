@@ -32,10 +32,13 @@ stencil_kernel(const InT* __restrict__ x, double2* __restrict__ y, const double2
     const InT* xb = x + b * in_stride;
     const long i = long(blockIdx.x) * ST_THREADS + threadIdx.x;
     if (i < n) {
-      const int ix = int(i % nx);
-      const long r = i / nx;
-      const int iy = int(r % ny);
-      const int iz = int(r / ny);
+      // n < 2^31 per right-hand side: 32-bit division
+      const unsigned ui = unsigned(i);
+      const unsigned r = ui / unsigned(nx);
+      const int ix = int(ui - r * unsigned(nx));
+      const unsigned rz = r / unsigned(ny);
+      const int iy = int(r - rz * unsigned(ny));
+      const int iz = int(rz);
       const long xl = ix == 0 ? i + nx - 1 : i - 1;
       const long xr = ix == nx - 1 ? i - (nx - 1) : i + 1;
       const long sy = nx;

@@ -75,6 +75,10 @@ _SIGS = {
     "hz_apply_operator": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
     "hz_apply_preconditioner": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
     "hz_gmres_solve": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(hz_solve_stats), _vp]),
+    "hz_profile_enable": (C.c_int, [C.c_int]),
+    "hz_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.c_int]),
+    "hz_launch_count": (C.c_ulonglong, []),
+    "hz_measure_fp64_peak": (C.c_int, [_dp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     if hasattr(lib, _name):
@@ -87,8 +91,37 @@ def header_symbols(path: str = HEADER) -> list[str]:
     """Every function name declared in include/hz.h."""
     with open(path) as fh:
         text = fh.read()
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\*?\s+\**(hz_[a-z0-9_]+)\s*\(",
+    return sorted(set(re.findall(r"^\s*(?:[a-z_]+\s+)*[a-z_]+\s*\**\s*(hz_[a-z0-9_]+)\s*\(",
                                  text, re.M)))
+
+
+class hz_phase_stats(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_longlong), ("ms", C.c_double),
+                ("bytes", C.c_double), ("flops", C.c_double)]
+
+
+def profile_enable(on: bool = True):
+    check(lib.hz_profile_enable(1 if on else 0))
+
+
+def profile_read(reset: bool = False) -> dict:
+    """{phase: dict(launches, ms, bytes, flops)} accumulated since the last reset."""
+    buf = (hz_phase_stats * 32)()
+    cnt = C.c_int()
+    check(lib.hz_profile_read(C.cast(buf, _vp), 32, C.byref(cnt), 1 if reset else 0))
+    return {buf[i].name.decode(): dict(launches=buf[i].launches, ms=buf[i].ms, bytes=buf[i].bytes,
+                                       flops=buf[i].flops) for i in range(cnt.value)}
+
+
+def launch_count() -> int:
+    return int(lib.hz_launch_count())
+
+
+def measure_fp64_peak() -> float:
+    """GFLOP/s of FP64 FMA on the current device."""
+    g = C.c_double()
+    check(lib.hz_measure_fp64_peak(C.byref(g)))
+    return g.value
 
 
 def last_error() -> str:

@@ -162,6 +162,30 @@ hz_status hz_apply_operator(hz_plan* plan, const void* x, void* y, int nrhs, voi
 hz_status hz_apply_preconditioner(hz_plan* plan, const void* x, void* y, int nrhs,
                                   int precision, void* stream);
 
+/* Allocation-free variant of hz_apply_preconditioner (the paper has no
+ * counterpart; this is a deployment aid).  y = Q_M x for nrhs c128 device
+ * vectors on a medium, without a plan: the transformed input and the K
+ * symbol planes live in one fixed device array of 32 MiB that the library
+ * image carries (every GPU that loads the library holds it until exit).
+ * For callers that cannot allocate device memory when they need the apply:
+ * code inside another runtime that owns the GPU's memory through its own
+ * pool, or a latency-bound loop that cannot afford cudaMalloc / cudaFree,
+ * which synchronise the device.  This call allocates nothing.
+ *   - Needs nrhs * n * (K + 1) * (16 for precision 0, 8 for precision 1)
+ *     bytes (plus 256 for alignment) <= 32 MiB, e.g. one 256 x 256 right-hand
+ *     side with K = 16 in complex128, or one 512 x 512 with K <= 15 in
+ *     complex64; larger requests return HZ_ERR_INVALID_ARG with the sizes.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array: calls whose work overlaps on the GPU
+ *     (different streams, or several host threads) race and corrupt each
+ *     other's results; serialise them.  No part of the array has to start
+ *     at zero: each call writes every element it later reads.
+ *   - Arguments, layout and precision as for hz_apply_preconditioner. */
+hz_status hz_apply_preconditioner_noalloc(const hz_medium* med, const void* x, void* y, int nrhs,
+                                          int precision, void* stream);
+
 /* Solve P_N u = f for nrhs right-hand sides with restarted (F)GMRES(m):
  * CGS2 Arnoldi in FP64, complex Givens rotations, true-residual check after
  * each cycle whose estimate reached tol.  f and u are c128 arrays of

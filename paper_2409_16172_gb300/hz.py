@@ -75,6 +75,7 @@ _SIGS = {
     "hz_apply_operator": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
     "hz_apply_preconditioner": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
     "hz_gmres_solve": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(hz_solve_stats), _vp]),
+    "hz_apply_preconditioner_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
     "hz_profile_enable": (C.c_int, [C.c_int]),
     "hz_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "hz_launch_count": (C.c_ulonglong, []),

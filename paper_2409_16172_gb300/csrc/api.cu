@@ -250,6 +250,7 @@ extern "C" hz_status hz_plan_bytes(const hz_plan* plan, size_t* bytes) {
 
 extern "C" hz_status hz_destroy_plan(hz_plan* plan) {
   if (!plan) return HZ_OK;
+  solve_ws_destroy(plan);
   plan->arena.release();
   delete plan;
   return HZ_OK;

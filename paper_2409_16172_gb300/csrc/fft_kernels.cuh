@@ -92,13 +92,14 @@ row_fwd_kernel(const double2* __restrict__ in, const double* __restrict__ scale,
   const bool valid = row < nrows;
   V* line = sm + li * padded_len(N);
   V x[E];
-  double s = 1.0;
-  if (valid && scale) s = scale[row / rows_per_rhs];
+  // the Krylov scale is applied after rounding to the working precision
+  R s = R(1);
+  if (valid && scale) s = R(scale[row / rows_per_rhs]);
   const double2* src = in + row * N;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     double2 v = valid ? src[F::stage0_index(t, e)] : make_double2(0.0, 0.0);
-    x[e] = cmk<V>(R(v.x * s), R(v.y * s));
+    x[e] = cmk<V>(R(v.x) * s, R(v.y) * s);
   }
   F::run(line, t, x, tw);
   if (valid) {

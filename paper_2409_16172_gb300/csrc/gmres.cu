@@ -38,25 +38,65 @@ bool is_device_ptr(const void* ptr) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-struct SolveWork {
-  DevArena ar;
-  KsDev ks{};
-  double* rnorm2 = nullptr;    // [B]
-  double2* y = nullptr;        // [B][m]
-  int* h_nact = nullptr;       // pinned, 2 slots
-  cudaEvent_t ev[2] = {nullptr, nullptr};
-  cudaEvent_t t0 = nullptr, t1 = nullptr;
-  ~SolveWork() {
-    ar.release();
-    if (h_nact) cudaFreeHost(h_nact);
-    for (auto& e : ev)
-      if (e) cudaEventDestroy(e);
-    if (t0) cudaEventDestroy(t0);
-    if (t1) cudaEventDestroy(t1);
-  }
-};
-
 }  // namespace
+
+namespace hz {
+
+hz_status solve_ws_create(hz_plan* p) {
+  if (p->ws) return HZ_OK;
+  SolveWs* w = new SolveWs();
+  const int m = p->opts.restart, B = p->max_nrhs;
+  KsDev& ks = w->ks;
+  ks.m = m;
+  ks.ldsig = B;
+  ks.tol = p->opts.tol;
+  hz_status st = HZ_OK;
+  auto A = [&](hz_status s) { if (st == HZ_OK) st = s; };
+  A(w->ar.alloc(&ks.H, size_t(B) * m * (m + 1)));
+  A(w->ar.alloc(&ks.S1, size_t(B) * (m + 1)));
+  A(w->ar.alloc(&ks.S2, size_t(B) * (m + 1)));
+  A(w->ar.alloc(&ks.sigma, size_t(B) * (m + 1)));
+  A(w->ar.alloc(&ks.nrm2, B));
+  A(w->ar.alloc(&ks.cs, size_t(B) * m));
+  A(w->ar.alloc(&ks.sn, size_t(B) * m));
+  A(w->ar.alloc(&ks.g, size_t(B) * (m + 1)));
+  A(w->ar.alloc(&ks.est, B));
+  A(w->ar.alloc(&ks.bnorm, B));
+  A(w->ar.alloc(&ks.jend, B));
+  A(w->ar.alloc(&ks.active, B));
+  A(w->ar.alloc(&ks.status, B));
+  A(w->ar.alloc(&ks.n_active, 1));
+  A(w->ar.alloc(&w->rnorm2, B));
+  A(w->ar.alloc(&w->y, size_t(B) * m));
+  if (st == HZ_OK && cudaMallocHost(&w->h_nact, 2 * sizeof(int)) != cudaSuccess)
+    st = set_error(HZ_ERR_OOM, "pinned host allocation failed");
+  for (auto& e : w->ev)
+    if (st == HZ_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      st = set_error(HZ_ERR_CUDA, "event creation failed");
+  if (st == HZ_OK && (cudaEventCreate(&w->t0) != cudaSuccess || cudaEventCreate(&w->t1) != cudaSuccess))
+    st = set_error(HZ_ERR_CUDA, "event creation failed");
+  p->ws = w;
+  if (st != HZ_OK) {
+    cudaGetLastError();
+    solve_ws_destroy(p);
+  }
+  return st;
+}
+
+void solve_ws_destroy(hz_plan* p) {
+  SolveWs* w = p->ws;
+  if (!w) return;
+  w->ar.release();
+  if (w->h_nact) cudaFreeHost(w->h_nact);
+  for (auto& e : w->ev)
+    if (e) cudaEventDestroy(e);
+  if (w->t0) cudaEventDestroy(w->t0);
+  if (w->t1) cudaEventDestroy(w->t1);
+  delete w;
+  p->ws = nullptr;
+}
+
+}  // namespace hz
 
 extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs,
                                     hz_solve_stats* stats, void* stream) {
@@ -72,31 +112,10 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
   const double tol = p->opts.tol;
   const long ldb = B;  // basis vector i of rhs b at V + (i * B + b) * n
 
-  SolveWork w;
+  HZ_TRY(solve_ws_create(p));
+  SolveWs& w = *p->ws;
   KsDev& ks = w.ks;
-  ks.m = m;
-  ks.ldsig = B;
-  ks.tol = tol;
-  HZ_TRY(w.ar.alloc(&ks.H, size_t(B) * m * (m + 1)));
-  HZ_TRY(w.ar.alloc(&ks.S1, size_t(B) * (m + 1)));
-  HZ_TRY(w.ar.alloc(&ks.S2, size_t(B) * (m + 1)));
-  HZ_TRY(w.ar.alloc(&ks.sigma, size_t(B) * (m + 1)));
-  HZ_TRY(w.ar.alloc(&ks.nrm2, B));
-  HZ_TRY(w.ar.alloc(&ks.cs, size_t(B) * m));
-  HZ_TRY(w.ar.alloc(&ks.sn, size_t(B) * m));
-  HZ_TRY(w.ar.alloc(&ks.g, size_t(B) * (m + 1)));
-  HZ_TRY(w.ar.alloc(&ks.est, B));
-  HZ_TRY(w.ar.alloc(&ks.bnorm, B));
-  HZ_TRY(w.ar.alloc(&ks.jend, B));
-  HZ_TRY(w.ar.alloc(&ks.active, B));
-  HZ_TRY(w.ar.alloc(&ks.status, B));
-  HZ_TRY(w.ar.alloc(&ks.n_active, 1));
-  HZ_TRY(w.ar.alloc(&w.rnorm2, B));
-  HZ_TRY(w.ar.alloc(&w.y, size_t(B) * m));
-  HZ_CUDA(cudaMallocHost(&w.h_nact, 2 * sizeof(int)));
-  for (auto& e : w.ev) HZ_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-  HZ_CUDA(cudaEventCreate(&w.t0));
-  HZ_CUDA(cudaEventCreate(&w.t1));
+  (void)tol;
   HZ_CUDA(cudaEventRecord(w.t0, st));
 
   // stage f and u

@@ -149,6 +149,10 @@ struct PhaseScope {
 
 }  // namespace hz
 
+namespace hz {
+struct SolveWs;
+}
+
 struct hz_plan {
   hz_medium* med = nullptr;
   hz_solver_opts opts{};
@@ -165,7 +169,5 @@ struct hz_plan {
   double2* f = nullptr;    // staged right-hand side for host buffers
   double* partial = nullptr;     // block partial sums
   size_t partial_len = 0;
-  double2* hcol = nullptr;       // [max_nrhs][m+2] current Hessenberg column sums
-  double* nrm2 = nullptr;        // [max_nrhs] squared norms
-  struct Ks* ks = nullptr;       // device-side small Krylov state
+  hz::SolveWs* ws = nullptr;     // small Krylov state, created by the first solve
 };

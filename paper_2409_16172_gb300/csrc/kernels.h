@@ -25,6 +25,19 @@ struct KsDev {
   int* n_active;    // number of active right-hand sides
 };
 
+// Per-plan solve workspace (allocated once, reused by every solve).
+struct SolveWs {
+  DevArena ar;
+  KsDev ks{};
+  double* rnorm2 = nullptr;   // [B]
+  double2* y = nullptr;       // [B][m]
+  int* h_nact = nullptr;      // pinned, 2 slots
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+};
+hz_status solve_ws_create(hz_plan* p);
+void solve_ws_destroy(hz_plan* p);
+
 int stencil_blocks(long n);
 hz_status launch_stencil(const hz_medium* m, int in_prec, const void* x, long in_stride,
                          double2* y, long out_stride, int nrhs, const int* active,

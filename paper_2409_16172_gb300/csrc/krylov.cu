@@ -43,16 +43,17 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
 }
 
 // S[b][i] partials: raw sums sum_p conj(V_i[p]) w[p] for i in [i0, i0 + nv),
-// nv = min(VC, j + 1 - i0).  grid = (nblk, nrhs, nchunk).  partial layout
+// chunks of vpc = ceil((j+1) / nchunk) <= VC vectors, i0 = chunk * vpc,
+// nv = min(vpc, j + 1 - i0).  grid = (nblk, nrhs, nchunk).  partial layout
 // [(b * (j+1) + i) * nblk + blk] as double2.  The next point's operands are
 // loaded before the current point's FMAs so that the FP64 pipe, the limit
 // here, does not wait on memory; only the nv live accumulators are reduced.
 __global__ void __launch_bounds__(KT, 2)
 dots_kernel(const double2* __restrict__ V, long ldb, const double2* __restrict__ w, long wstride,
-            long n, int j, const int* __restrict__ active, double2* __restrict__ partial) {
+            long n, int j, int vpc, const int* __restrict__ active, double2* __restrict__ partial) {
   const int b = blockIdx.y;
-  const int i0 = blockIdx.z * VC;
-  const int nv = min(VC, j + 1 - i0);
+  const int i0 = blockIdx.z * vpc;
+  const int nv = min(vpc, j + 1 - i0);
   double acc[2 * VC];
 #pragma unroll
   for (int c = 0; c < 2 * VC; ++c) acc[c] = 0.0;
@@ -395,13 +396,16 @@ int krylov_blocks(long n, int nrhs, int nchunk) {
 hz_status launch_dots(const double2* V, long ldb, const double2* w, long wstride, long n, int j,
                       int nrhs, const int* active, double2* partial, int /*unused*/, double2* S,
                       int ldS, cudaStream_t st) {
-  const int nchunk = (j + 1 + VC - 1) / VC;
-  // enough blocks to fill the GPU, but >= 16 points per thread when n allows,
-  // so that the block reductions stay small next to the FMAs
-  int nblk = krylov_blocks(n, nrhs, nchunk);
+  // balanced chunks of at most VC vectors; one wave of two blocks per SM
+  // (the register budget allows two), at least 16 points per thread
+  int nchunk = (j + 1 + VC - 1) / VC;
+  const int vpc = (j + 1 + nchunk - 1) / nchunk;
+  nchunk = (j + 1 + vpc - 1) / vpc;  // no empty chunk
+  long per = (2L * 152) / (long(nrhs) * nchunk);
   const long cap = (n + 16L * KT - 1) / (16L * KT);
-  if (nblk > cap) nblk = int(cap > 0 ? cap : 1);
-  dots_kernel<<<dim3(nblk, nrhs, nchunk), KT, 0, st>>>(V, ldb, w, wstride, n, j, active, partial);
+  if (per > cap) per = cap;
+  const int nblk = int(per < 1 ? 1 : per);
+  dots_kernel<<<dim3(nblk, nrhs, nchunk), KT, 0, st>>>(V, ldb, w, wstride, n, j, vpc, active, partial);
   reduce_c_kernel<<<unsigned(nrhs * (j + 1)), KT, 0, st>>>(partial, nblk, j + 1, ldS, S);
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;

@@ -197,6 +197,71 @@ hz_status hz_apply_preconditioner_noalloc(const hz_medium* med, const void* x, v
 hz_status hz_gmres_solve(hz_plan* plan, const void* f, void* u, int nrhs,
                          hz_solve_stats* stats, void* stream);
 
+/* ---- serving ----------------------------------------------------------
+ * A server queues solve requests and admits them onto the GPU as slots and
+ * device memory free up (admission by each request's device footprint
+ * against hbm_budget, first fit in arrival order).  Each admitted request
+ * runs medium set-up, plan, (F)GMRES solve and read-back on its own
+ * non-blocking stream and host worker, so the work of concurrent requests
+ * overlaps on the device; allocations use the stream-ordered pool.  Every
+ * reduction is fixed-order and per request: a result is the same alone and
+ * in any mix.  The paper solves one problem at a time; this is the
+ * continuous-batching layer around its method. */
+typedef struct {
+  size_t hbm_budget;   /* device bytes admitted requests may hold; 0 = 80% of free memory */
+  int max_slots;       /* requests on the GPU at once (1..64)                            */
+  int max_queue;       /* queued requests before hz_submit returns HZ_ERR_BUSY             */
+  int device;          /* CUDA device the server uses                                      */
+} hz_server_opts;
+
+typedef struct {
+  hz_grid grid;
+  const double* c;        /* host, n values (copied by hz_submit)  */
+  const double* zeta;     /* host or NULL                          */
+  const double* a;        /* host or NULL                          */
+  double omega;
+  hz_interp interp;
+  hz_solver_opts opts;
+  int nrhs;
+  const void* f;          /* host c128, nrhs * n (copied)          */
+} hz_request;
+
+typedef struct {
+  long long submitted, completed, failed, rejected;
+  int active, queued, max_active;
+  size_t hbm_in_use, hbm_budget;
+  double p50_ms, p99_ms, mean_ms;  /* submit-to-completion latency of finished requests */
+  double rhs_per_s;                /* right-hand sides solved per second since creation  */
+} hz_server_stats;
+
+typedef struct hz_server hz_server;
+
+/* Device bytes a request holds while it runs (medium + plan), the quantity
+ * admission compares against hbm_budget.  K is taken as M + Mt. */
+size_t hz_request_footprint(const hz_grid* grid, const hz_interp* interp,
+                            const hz_solver_opts* opts, int nrhs, int has_a);
+
+hz_status hz_server_create(const hz_server_opts* opts, hz_server** out);
+
+/* Copies the request and queues it; returns at once with a ticket.
+ * HZ_ERR_BUSY when the queue is full or the request alone exceeds the
+ * budget; HZ_ERR_INVALID_ARG for a malformed request. */
+hz_status hz_submit(hz_server* s, const hz_request* req, uint64_t* ticket);
+
+/* *done = 0 while the request is queued or running.  When done, copies the
+ * solution (nrhs * n c128, host; u_out may be NULL) and nrhs stats entries
+ * (may be NULL), releases the ticket and returns the request's status. */
+hz_status hz_poll(hz_server* s, uint64_t ticket, int* done, void* u_out, hz_solve_stats* stats);
+
+/* Blocks until the request is done (then hz_poll it) or timeout_s passes
+ * (HZ_ERR_TIMEOUT). */
+hz_status hz_server_wait(hz_server* s, uint64_t ticket, double timeout_s);
+
+hz_status hz_server_get_stats(hz_server* s, hz_server_stats* out);
+
+/* Drops queued requests, waits for the running ones, frees the server. */
+hz_status hz_server_destroy(hz_server* s);
+
 /* ---- measurement ------------------------------------------------------
  * Per-phase timing with CUDA events recorded on the stream each kernel is
  * launched on, plus the algorithmic bytes and flops of every launch (the

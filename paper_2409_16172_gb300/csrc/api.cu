@@ -41,10 +41,22 @@ hz_status cuda_error(cudaError_t e, const char* what) {
   return set_error(st, "%s: %s", what, cudaGetErrorString(e));
 }
 
+namespace {
+thread_local cudaStream_t g_tls_stream = nullptr;
+thread_local bool g_tls_async = false;
+}  // namespace
+
+cudaStream_t tls_stream() { return g_tls_stream; }
+void set_tls_stream(cudaStream_t st, bool async_alloc) {
+  g_tls_stream = st;
+  g_tls_async = async_alloc;
+}
+
 void* dev_alloc(size_t bytes) {
   if (g_alloc) return g_alloc(bytes, g_ctx);
   void* p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+  const cudaError_t e = g_tls_async ? cudaMallocAsync(&p, bytes, g_tls_stream) : cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
@@ -54,6 +66,7 @@ void* dev_alloc(size_t bytes) {
 void dev_free(void* p) {
   if (!p) return;
   if (g_free) g_free(p, g_ctx);
+  else if (g_tls_async) cudaFreeAsync(p, g_tls_stream);
   else cudaFree(p);
 }
 

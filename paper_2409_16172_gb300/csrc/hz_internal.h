@@ -32,6 +32,12 @@ hz_status cuda_error(cudaError_t e, const char* what);
 void* dev_alloc(size_t bytes);
 void dev_free(void* p);
 
+// Per-thread stream for the library's own set-up work and stream-ordered
+// allocation (server workers set it; elsewhere it is the legacy stream and
+// allocation uses cudaMalloc).
+cudaStream_t tls_stream();
+void set_tls_stream(cudaStream_t st, bool async_alloc);
+
 // RAII list of device allocations owned by a medium or plan.
 struct DevArena {
   std::vector<void*> ptrs;

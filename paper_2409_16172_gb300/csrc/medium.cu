@@ -169,9 +169,10 @@ void xi2_table(int N, double L, int kind, std::vector<double>& t) {
 }
 
 template <typename T>
-hz_status upload(DevArena& ar, T** d, const std::vector<T>& h) {
+hz_status upload(DevArena& ar, T** d, const std::vector<T>& h, cudaStream_t cs) {
   HZ_TRY(ar.alloc(d, h.size()));
-  HZ_CUDA(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  // pageable source: the call returns once the data has been staged
+  HZ_CUDA(cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, cs));
   return HZ_OK;
 }
 
@@ -268,18 +269,23 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
   if (st == HZ_OK && zeta) st = scratch.alloc(&dz, n);
   if (st == HZ_OK && a) st = m->arena.alloc(&m->a, n);
   if (st != HZ_OK) return fail(st);
-  cudaError_t ce = cudaMemcpy(dc, c, n * sizeof(double), cudaMemcpyHostToDevice);
-  if (ce == cudaSuccess && zeta) ce = cudaMemcpy(dz, zeta, n * sizeof(double), cudaMemcpyHostToDevice);
-  if (ce == cudaSuccess && a) ce = cudaMemcpy(m->a, a, n * sizeof(double), cudaMemcpyHostToDevice);
+  // all work of the set-up runs on the calling thread's stream (the legacy
+  // default stream unless a server worker set its own)
+  cudaStream_t cs = tls_stream();
+  cudaError_t ce = cudaMemcpyAsync(dc, c, n * sizeof(double), cudaMemcpyHostToDevice, cs);
+  if (ce == cudaSuccess && zeta) ce = cudaMemcpyAsync(dz, zeta, n * sizeof(double), cudaMemcpyHostToDevice, cs);
+  if (ce == cudaSuccess && a) ce = cudaMemcpyAsync(m->a, a, n * sizeof(double), cudaMemcpyHostToDevice, cs);
   if (ce != cudaSuccess) return fail(cuda_error(ce, "medium upload"));
 
   // validation and ranges
   const int vblocks = 304;
   ValPartial* dpart = nullptr;
   if ((st = scratch.alloc(&dpart, vblocks)) != HZ_OK) return fail(st);
-  validate_kernel<<<vblocks, VAL_THREADS>>>(dc, dz, m->a, n, interp->c_o, dpart);
+  validate_kernel<<<vblocks, VAL_THREADS, 0, cs>>>(dc, dz, m->a, n, interp->c_o, dpart);
+  count_launches(1);
   std::vector<ValPartial> hp(vblocks);
-  ce = cudaMemcpy(hp.data(), dpart, vblocks * sizeof(ValPartial), cudaMemcpyDeviceToHost);
+  ce = cudaMemcpyAsync(hp.data(), dpart, vblocks * sizeof(ValPartial), cudaMemcpyDeviceToHost, cs);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(cs);
   if (ce != cudaSuccess) return fail(cuda_error(ce, "validate"));
   double cmin = INFINITY, cmax = -INFINITY, zmax = 0;
   unsigned long long bc = 0, bz = 0, bl = 0, ba = 0;
@@ -362,19 +368,20 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
   if (st == HZ_OK) st = m->arena.alloc(&m->rowmask, nrows);
   if (st == HZ_OK) st = m->arena.alloc(&m->slabmask, m->nz);
   if (st != HZ_OK) return fail(st);
-  ce = cudaMemset(m->rowmask, 0, nrows * sizeof(unsigned long long));
+  ce = cudaMemsetAsync(m->rowmask, 0, nrows * sizeof(unsigned long long), cs);
   if (ce != cudaSuccess) return fail(cuda_error(ce, "memset"));
-  record_kernel<<<unsigned((n + 255) / 256), 256>>>(dc, dz, n, m->nx, nd, m->rec64, m->rec32,
-                                                   m->gamma2, m->rowmask);
-  slab_kernel<<<(m->nz + 127) / 128, 128>>>(m->rowmask, m->ny, m->nz, m->slabmask);
-  count_launches(4);
+  record_kernel<<<unsigned((n + 255) / 256), 256, 0, cs>>>(dc, dz, n, m->nx, nd, m->rec64, m->rec32,
+                                                          m->gamma2, m->rowmask);
+  slab_kernel<<<(m->nz + 127) / 128, 128, 0, cs>>>(m->rowmask, m->ny, m->nz, m->slabmask);
+  count_launches(2);
   ce = cudaGetLastError();
   if (ce != cudaSuccess) return fail(cuda_error(ce, "record kernel"));
   {
     std::vector<unsigned long long> rm(nrows), sm(m->nz);
-    ce = cudaMemcpy(rm.data(), m->rowmask, nrows * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    ce = cudaMemcpyAsync(rm.data(), m->rowmask, nrows * sizeof(unsigned long long), cudaMemcpyDeviceToHost, cs);
     if (ce == cudaSuccess)
-      ce = cudaMemcpy(sm.data(), m->slabmask, m->nz * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+      ce = cudaMemcpyAsync(sm.data(), m->slabmask, m->nz * sizeof(unsigned long long), cudaMemcpyDeviceToHost, cs);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(cs);
     if (ce != cudaSuccess) return fail(cuda_error(ce, "mask readback"));
     double ru = 0, su = 0;
     for (auto v : rm) ru += __builtin_popcountll(v);
@@ -393,11 +400,11 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
     Af[k] = make_float2(float(A[k].x), float(A[k].y));
     Gf[k] = make_float2(float(G[k].x), float(G[k].y));
   }
-  if ((st = upload(m->arena, &m->symA64, A)) != HZ_OK) return fail(st);
-  if ((st = upload(m->arena, &m->symG64, G)) != HZ_OK) return fail(st);
-  if ((st = upload(m->arena, &m->symA32, Af)) != HZ_OK) return fail(st);
-  if ((st = upload(m->arena, &m->symG32, Gf)) != HZ_OK) return fail(st);
-  if ((st = upload(m->arena, &m->segtab, m->segtab_h)) != HZ_OK) return fail(st);
+  if ((st = upload(m->arena, &m->symA64, A, cs)) != HZ_OK) return fail(st);
+  if ((st = upload(m->arena, &m->symG64, G, cs)) != HZ_OK) return fail(st);
+  if ((st = upload(m->arena, &m->symA32, Af, cs)) != HZ_OK) return fail(st);
+  if ((st = upload(m->arena, &m->symG32, Gf, cs)) != HZ_OK) return fail(st);
+  if ((st = upload(m->arena, &m->segtab, m->segtab_h, cs)) != HZ_OK) return fail(st);
 
   // per-axis tables
   const int nax[3] = {m->nx, m->ny, m->nz};
@@ -415,14 +422,14 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
     }
     AxisTables& t = m->ax[d];
     t.N = N;
-    if ((st = upload(m->arena, &t.tw64, tw)) != HZ_OK) return fail(st);
-    if ((st = upload(m->arena, &t.tw32, twf)) != HZ_OK) return fail(st);
-    if ((st = upload(m->arena, &t.xi2_64, xi)) != HZ_OK) return fail(st);
-    if ((st = upload(m->arena, &t.xi2_32, xif)) != HZ_OK) return fail(st);
+    if ((st = upload(m->arena, &t.tw64, tw, cs)) != HZ_OK) return fail(st);
+    if ((st = upload(m->arena, &t.tw32, twf, cs)) != HZ_OK) return fail(st);
+    if ((st = upload(m->arena, &t.xi2_64, xi, cs)) != HZ_OK) return fail(st);
+    if ((st = upload(m->arena, &t.xi2_32, xif, cs)) != HZ_OK) return fail(st);
     const double h = m->L / N;
     m->inv_h2[d] = 1.0 / (h * h);
   }
-  ce = cudaDeviceSynchronize();
+  ce = cudaStreamSynchronize(cs);
   if (ce != cudaSuccess) return fail(cuda_error(ce, "create_medium"));
   *out = m;
   return HZ_OK;

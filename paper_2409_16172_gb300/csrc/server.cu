@@ -1,0 +1,340 @@
+// Serving loop: requests of different grids, frequencies and media are
+// queued by hz_submit and admitted onto the GPU as slots and HBM budget free
+// up; each admitted request runs its whole pipeline (medium set-up, plan,
+// FGMRES solve, read-back) on its own non-blocking stream from its own
+// worker thread, so the kernels of concurrent requests overlap on the device
+// (for instance one request's FP64 Arnoldi with another's complex64
+// transforms).  Memory comes from the stream-ordered pool, so a request
+// starting or finishing does not synchronise the device.  Every reduction is
+// fixed-order and per request, so a result does not depend on what else runs.
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "hz_internal.h"
+
+using Clock = std::chrono::steady_clock;
+using hz::cuda_error;
+using hz::set_tls_stream;
+
+namespace {
+
+struct Req {
+  uint64_t id = 0;
+  hz_grid grid{};
+  std::vector<double> c, zeta, a;
+  double omega = 0;
+  hz_interp interp{};
+  hz_solver_opts opts{};
+  int nrhs = 1;
+  long n = 0;
+  std::vector<double2> f, u;
+  std::vector<hz_solve_stats> stats;
+  hz_status status = HZ_OK;
+  std::string error;
+  size_t footprint = 0;
+  Clock::time_point t_submit, t_start, t_done;
+  bool done = false;
+};
+
+size_t fft_partial_bytes(long n, int B, int m) {
+  const long nblk = std::max(1024L, (n + 255) / 256);
+  return size_t(B) * (m + 2) * nblk * 2 * sizeof(double);
+}
+
+}  // namespace
+
+// Device bytes one request holds while it runs: medium (gamma^2, records,
+// damping, staging of c and zeta during set-up, masks) and plan (transformed
+// input, K planes, Krylov basis, Z, staged f/u, partial sums).
+extern "C" size_t hz_request_footprint(const hz_grid* g, const hz_interp* it,
+                                       const hz_solver_opts* o, int nrhs, int has_a) {
+  const long n = long(g->n[0]) * g->n[1] * (g->dim == 3 ? g->n[2] : 1);
+  const int K = it->M + it->Mt;
+  const int m = o->restart;
+  const size_t B = size_t(nrhs);
+  const size_t es = o->precision == 0 ? 16 : 8;
+  size_t med = size_t(n) * (16 + 8 + 4 + (has_a ? 8 : 0) + 16) + size_t(n / g->n[0] + 1) * 16 + (1 << 20);
+  size_t plan = B * n * 16                      // tmp
+                + B * K * n * es                // planes
+                + size_t(m + 1) * B * n * 16    // V
+                + (o->precision == 1 ? size_t(m) * B * n * 8 : B * n * 16)  // Z
+                + 2 * B * n * 16                // staged u, f
+                + fft_partial_bytes(n, int(B), m) + (1 << 20);
+  return med + plan;
+}
+
+struct hz_server {
+  hz_server_opts opts{};
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<std::shared_ptr<Req>> queue;
+  std::unordered_map<uint64_t, std::shared_ptr<Req>> table;
+  size_t in_use = 0;
+  int active = 0, max_active_seen = 0;
+  bool stop = false;
+  std::vector<std::thread> workers;
+  uint64_t next_id = 1;
+  long long submitted = 0, completed = 0, failed = 0, rejected = 0, rhs_done = 0;
+  std::vector<double> lat_ms;
+  Clock::time_point t0;
+};
+
+namespace {
+
+void run_request(hz_server* s, Req& r, cudaStream_t st) {
+  hz_medium* med = nullptr;
+  hz_plan* plan = nullptr;
+  r.u.assign(size_t(r.nrhs) * r.n, make_double2(0, 0));
+  r.stats.assign(r.nrhs, hz_solve_stats{});
+  hz_status rc = hz_create_medium(&r.grid, r.c.data(), r.zeta.empty() ? nullptr : r.zeta.data(),
+                                  r.a.empty() ? nullptr : r.a.data(), r.omega, &r.interp, &med);
+  if (rc == HZ_OK) rc = hz_plan_create(med, &r.opts, r.nrhs, &plan);
+  if (rc == HZ_OK) {
+    const size_t vb = size_t(r.nrhs) * r.n * sizeof(double2);
+    cudaError_t ce = cudaMemcpyAsync(plan->f, r.f.data(), vb, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(plan->u, 0, vb, st);
+    if (ce != cudaSuccess) {
+      rc = cuda_error(ce, "request upload");
+    } else {
+      rc = hz_gmres_solve(plan, plan->f, plan->u, r.nrhs, r.stats.data(), st);
+      if (rc == HZ_OK || rc == HZ_ERR_NOT_CONVERGED || rc == HZ_ERR_BREAKDOWN) {
+        ce = cudaMemcpyAsync(r.u.data(), plan->u, vb, cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) rc = cuda_error(ce, "request read-back");
+      }
+    }
+  }
+  if (rc != HZ_OK) r.error = hz_last_error();
+  if (plan) hz_destroy_plan(plan);
+  if (med) hz_destroy_medium(med);
+  cudaStreamSynchronize(st);
+  r.status = rc;
+  (void)s;
+}
+
+void worker_main(hz_server* s) {
+  cudaSetDevice(s->device);
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    st = nullptr;
+  }
+  set_tls_stream(st, st != nullptr);
+  for (;;) {
+    std::shared_ptr<Req> r;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      for (;;) {
+        if (s->stop) {
+          set_tls_stream(nullptr, false);
+          if (st) cudaStreamDestroy(st);
+          return;
+        }
+        // first fit in arrival order within the HBM budget
+        for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+          if (s->in_use + (*it)->footprint <= s->opts.hbm_budget || s->active == 0) {
+            r = *it;
+            s->queue.erase(it);
+            break;
+          }
+        }
+        if (r) break;
+        s->cv_work.wait(lk);
+      }
+      s->in_use += r->footprint;
+      ++s->active;
+      s->max_active_seen = std::max(s->max_active_seen, s->active);
+      r->t_start = Clock::now();
+    }
+    run_request(s, *r, st);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->in_use -= r->footprint;
+      --s->active;
+      r->t_done = Clock::now();
+      r->done = true;
+      if (r->status == HZ_OK) {
+        ++s->completed;
+        s->rhs_done += r->nrhs;
+      } else {
+        ++s->failed;
+      }
+      s->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+      r->c.clear(); r->c.shrink_to_fit();
+      r->zeta.clear(); r->zeta.shrink_to_fit();
+      r->a.clear(); r->a.shrink_to_fit();
+      r->f.clear(); r->f.shrink_to_fit();
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+  }
+}
+
+double percentile(std::vector<double> v, double q) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  const double pos = q * double(v.size() - 1);
+  const size_t i = size_t(pos);
+  const double f = pos - double(i);
+  return i + 1 < v.size() ? v[i] * (1 - f) + v[i + 1] * f : v[i];
+}
+
+}  // namespace
+
+using namespace hz;
+
+extern "C" hz_status hz_server_create(const hz_server_opts* opts, hz_server** out) {
+  if (!opts || !out) return set_error(HZ_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (opts->max_slots < 1 || opts->max_slots > 64 || opts->max_queue < 1)
+    return set_error(HZ_ERR_INVALID_ARG, "need 1 <= max_slots <= 64 and max_queue >= 1");
+  hz_server* s = new hz_server();
+  s->opts = *opts;
+  s->device = opts->device;
+  HZ_CUDA(cudaSetDevice(s->device));
+  if (s->opts.hbm_budget == 0) {
+    size_t fr = 0, tot = 0;
+    HZ_CUDA(cudaMemGetInfo(&fr, &tot));
+    s->opts.hbm_budget = fr / 10 * 8;
+  }
+  // keep freed blocks in the stream-ordered pool between requests
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess) {
+    unsigned long long thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  s->t0 = Clock::now();
+  for (int i = 0; i < opts->max_slots; ++i) s->workers.emplace_back(worker_main, s);
+  *out = s;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_submit(hz_server* s, const hz_request* q, uint64_t* ticket) {
+  if (!s || !q || !ticket || !q->c || !q->f) return set_error(HZ_ERR_INVALID_ARG, "null argument");
+  if (q->nrhs < 1) return set_error(HZ_ERR_INVALID_ARG, "nrhs must be >= 1");
+  if (q->grid.dim != 2 && q->grid.dim != 3) return set_error(HZ_ERR_INVALID_ARG, "dim must be 2 or 3");
+  for (int d = 0; d < q->grid.dim; ++d)
+    if (!fft_size_supported(q->grid.n[d]))
+      return set_error(HZ_ERR_INVALID_ARG, "unsupported axis length %d", q->grid.n[d]);
+  auto r = std::make_shared<Req>();
+  r->grid = q->grid;
+  if (r->grid.dim == 2) r->grid.n[2] = 1;
+  r->n = long(r->grid.n[0]) * r->grid.n[1] * r->grid.n[2];
+  r->omega = q->omega;
+  r->interp = q->interp;
+  r->opts = q->opts;
+  r->nrhs = q->nrhs;
+  r->footprint = hz_request_footprint(&r->grid, &r->interp, &r->opts, r->nrhs, q->a != nullptr);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (r->footprint > s->opts.hbm_budget) {
+      ++s->rejected;
+      return set_error(HZ_ERR_BUSY, "request needs %zu bytes, more than the server's budget %zu",
+                       r->footprint, s->opts.hbm_budget);
+    }
+    if (int(s->queue.size()) >= s->opts.max_queue) {
+      ++s->rejected;
+      return set_error(HZ_ERR_BUSY, "queue full (%d requests)", s->opts.max_queue);
+    }
+  }
+  r->c.assign(q->c, q->c + r->n);
+  if (q->zeta) r->zeta.assign(q->zeta, q->zeta + r->n);
+  if (q->a) r->a.assign(q->a, q->a + r->n);
+  const double2* f = static_cast<const double2*>(q->f);
+  r->f.assign(f, f + size_t(r->nrhs) * r->n);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->id = s->next_id++;
+    r->t_submit = Clock::now();
+    s->table[r->id] = r;
+    s->queue.push_back(r);
+    ++s->submitted;
+    *ticket = r->id;
+  }
+  s->cv_work.notify_one();
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_poll(hz_server* s, uint64_t ticket, int* done, void* u_out,
+                             hz_solve_stats* stats) {
+  if (!s || !done) return set_error(HZ_ERR_INVALID_ARG, "null argument");
+  std::shared_ptr<Req> r;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->table.find(ticket);
+    if (it == s->table.end()) return set_error(HZ_ERR_INVALID_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    r = it->second;
+    if (!r->done) {
+      *done = 0;
+      return HZ_OK;
+    }
+    s->table.erase(it);
+  }
+  *done = 1;
+  if (u_out && !r->u.empty()) memcpy(u_out, r->u.data(), r->u.size() * sizeof(double2));
+  if (stats && !r->stats.empty()) memcpy(stats, r->stats.data(), r->stats.size() * sizeof(hz_solve_stats));
+  if (r->status != HZ_OK) return set_error(r->status, "%s", r->error.c_str());
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_server_wait(hz_server* s, uint64_t ticket, double timeout_s) {
+  if (!s) return set_error(HZ_ERR_INVALID_ARG, "null argument");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->table.find(ticket);
+  if (it == s->table.end()) return set_error(HZ_ERR_INVALID_ARG, "unknown ticket");
+  auto r = it->second;
+  const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                           std::chrono::duration<double>(timeout_s));
+  while (!r->done) {
+    if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !r->done)
+      return set_error(HZ_ERR_TIMEOUT, "request %llu not done within %.3f s",
+                       (unsigned long long)ticket, timeout_s);
+  }
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_server_get_stats(hz_server* s, hz_server_stats* out) {
+  if (!s || !out) return set_error(HZ_ERR_INVALID_ARG, "null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  out->submitted = s->submitted;
+  out->completed = s->completed;
+  out->failed = s->failed;
+  out->rejected = s->rejected;
+  out->active = s->active;
+  out->queued = int(s->queue.size());
+  out->max_active = s->max_active_seen;
+  out->hbm_in_use = s->in_use;
+  out->hbm_budget = s->opts.hbm_budget;
+  out->p50_ms = percentile(s->lat_ms, 0.50);
+  out->p99_ms = percentile(s->lat_ms, 0.99);
+  double mean = 0;
+  for (double v : s->lat_ms) mean += v;
+  out->mean_ms = s->lat_ms.empty() ? 0 : mean / s->lat_ms.size();
+  const double el = std::chrono::duration<double>(Clock::now() - s->t0).count();
+  out->rhs_per_s = el > 0 ? double(s->rhs_done) / el : 0;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_server_destroy(hz_server* s) {
+  if (!s) return HZ_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->queue.clear();
+  }
+  s->cv_work.notify_all();
+  for (auto& t : s->workers) t.join();
+  delete s;
+  return HZ_OK;
+}

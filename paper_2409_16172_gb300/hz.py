@@ -60,6 +60,24 @@ class hz_solve_stats(C.Structure):
 
 _vp = C.c_void_p
 _dp = C.POINTER(C.c_double)
+
+
+class hz_server_opts(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int), ("max_queue", C.c_int),
+                ("device", C.c_int)]
+
+
+class hz_request(C.Structure):
+    _fields_ = [("grid", hz_grid), ("c", _dp), ("zeta", _dp), ("a", _dp), ("omega", C.c_double),
+                ("interp", hz_interp), ("opts", hz_solver_opts), ("nrhs", C.c_int), ("f", _vp)]
+
+
+class hz_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong), ("failed", C.c_longlong),
+                ("rejected", C.c_longlong), ("active", C.c_int), ("queued", C.c_int),
+                ("max_active", C.c_int), ("hbm_in_use", C.c_size_t), ("hbm_budget", C.c_size_t),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
+                ("rhs_per_s", C.c_double)]
 _SIGS = {
     "hz_last_error": (C.c_char_p, []),
     "hz_version": (C.c_char_p, []),
@@ -76,6 +94,14 @@ _SIGS = {
     "hz_apply_preconditioner": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
     "hz_gmres_solve": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(hz_solve_stats), _vp]),
     "hz_apply_preconditioner_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
+    "hz_request_footprint": (C.c_size_t, [C.POINTER(hz_grid), C.POINTER(hz_interp),
+                                          C.POINTER(hz_solver_opts), C.c_int, C.c_int]),
+    "hz_server_create": (C.c_int, [C.POINTER(hz_server_opts), C.POINTER(_vp)]),
+    "hz_submit": (C.c_int, [_vp, C.POINTER(hz_request), C.POINTER(C.c_uint64)]),
+    "hz_poll": (C.c_int, [_vp, C.c_uint64, C.POINTER(C.c_int), _vp, _vp]),
+    "hz_server_wait": (C.c_int, [_vp, C.c_uint64, C.c_double]),
+    "hz_server_get_stats": (C.c_int, [_vp, C.POINTER(hz_server_stats)]),
+    "hz_server_destroy": (C.c_int, [_vp]),
     "hz_profile_enable": (C.c_int, [C.c_int]),
     "hz_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "hz_launch_count": (C.c_ulonglong, []),
@@ -280,6 +306,92 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             lib.hz_destroy_plan(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+def _grid_of(shape, L=1.0):
+    g = hz_grid()
+    g.dim = len(shape)
+    dims = list(reversed(shape)) + [1] * (3 - len(shape))
+    for i in range(3):
+        g.n[i] = dims[i]
+    g.L = L
+    return g
+
+
+def request_footprint(shape, M, Mt, precision=1, restart=40, nrhs=1, has_a=False) -> int:
+    g = _grid_of(tuple(shape))
+    it = hz_interp(M, Mt, 1.0, 0.0, 0.15, 0.0, 0)
+    o = hz_solver_opts(precision, restart, 1e-6, 4000)
+    return int(lib.hz_request_footprint(C.byref(g), C.byref(it), C.byref(o), nrhs, 1 if has_a else 0))
+
+
+class Server:
+    """Continuous-batching solve server (hz_server_* in the C ABI)."""
+
+    def __init__(self, max_slots: int = 4, max_queue: int = 4096, hbm_budget: int = 0,
+                 device: int = 0):
+        o = hz_server_opts(hbm_budget, max_slots, max_queue, device)
+        h = _vp()
+        check(lib.hz_server_create(C.byref(o), C.byref(h)))
+        self._h = h
+        self._shapes = {}
+
+    def submit(self, c, f, *, omega: float, M: int, Mt: int = 0, zeta=None, a=None,
+               c_o: float = 1.0, zeta_max: float = 0.0, alpha: float = 0.15, a_node: float = 0.0,
+               symbol_kind: int = 0, precision: int = 1, restart: int = 40, tol: float = 1e-6,
+               maxit: int = 4000, L: float = 1.0) -> int:
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        shape = c.shape
+        f = np.ascontiguousarray(f, dtype=np.complex128)
+        nrhs = f.size // c.size
+        zeta = None if zeta is None else np.ascontiguousarray(zeta, dtype=np.float64)
+        a = None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+        r = hz_request()
+        r.grid = _grid_of(shape, L)
+        r.c = _dptr(c)
+        r.zeta = _dptr(zeta)
+        r.a = _dptr(a)
+        r.omega = omega
+        r.interp = hz_interp(M, Mt, c_o, zeta_max, alpha, a_node, symbol_kind)
+        r.opts = hz_solver_opts(precision, restart, tol, maxit)
+        r.nrhs = nrhs
+        r.f = _vp(f.ctypes.data)
+        t = C.c_uint64()
+        check(lib.hz_submit(self._h, C.byref(r), C.byref(t)))
+        self._shapes[t.value] = (nrhs,) + tuple(shape)
+        return t.value
+
+    def poll(self, ticket: int):
+        """(done, u, stats, status); u and stats are None until done."""
+        shape = self._shapes[ticket]
+        done = C.c_int()
+        u = np.empty(shape, np.complex128)
+        stats = (hz_solve_stats * shape[0])()
+        st = lib.hz_poll(self._h, ticket, C.byref(done), _vp(u.ctypes.data), C.cast(stats, _vp))
+        if not done.value:
+            check(st)
+            return False, None, None, st
+        del self._shapes[ticket]
+        return True, u, [s.as_dict() for s in stats], st
+
+    def wait(self, ticket: int, timeout: float = 600.0):
+        check(lib.hz_server_wait(self._h, ticket, timeout))
+
+    def result(self, ticket: int, timeout: float = 600.0):
+        self.wait(ticket, timeout)
+        return self.poll(ticket)
+
+    def stats(self) -> dict:
+        s = hz_server_stats()
+        check(lib.hz_server_get_stats(self._h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.hz_server_destroy(self._h)
             self._h = None
 
     __del__ = close

@@ -1,0 +1,115 @@
+"""Serving layer (hz_submit / hz_poll): mixed requests overlap on the GPU,
+each result equals the same request solved alone, admission respects the
+HBM budget, and malformed or oversized requests are refused."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2409_16172_gb300 import synth as S
+
+from gpu_util import hz_module, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hz():
+    import torch
+    assert torch.cuda.is_available()
+    return hz_module()
+
+
+def _requests():
+    out = []
+    for shape, seed, M, Mt, nrhs in [((64, 64), 1, 5, 2, 2), ((96, 128), 2, 6, 2, 1),
+                                     ((16, 24, 32), 3, 4, 2, 1), ((256, 256), 4, 6, 2, 1),
+                                     ((48, 48), 5, 3, 1, 3), ((32, 32, 32), 6, 6, 2, 1)]:
+        p = S.small_problem(shape, seed, M=M, Mt=Mt, width=3)
+        f = S.random_field(np.random.Generator(np.random.PCG64(seed)), shape, nrhs)
+        out.append((p, f))
+    return out
+
+
+def _submit(srv, p, f, **kw):
+    return srv.submit(p.c, f, omega=p.omega, M=p.M, Mt=p.Mt, zeta=p.zeta, alpha=0.15,
+                      restart=30, tol=1e-8, **kw)
+
+
+def test_mixed_requests_match_solo_solves_and_oracle(hz):
+    reqs = _requests()
+    srv = hz.Server(max_slots=3)
+    tickets = [_submit(srv, p, f) for p, f in reqs]
+    results = [srv.result(t) for t in tickets]
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["max_active"] >= 2, st  # requests really overlapped
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+    for (p, f), (done, u, stats, status) in zip(reqs, results):
+        assert done and status == 0
+        med_o = O.make_medium(p.c, p.zeta, None, p.omega, p.M, p.Mt, 1.0, None, 0.15)
+        for b in range(f.shape[0]):
+            assert stats[b]["converged"]
+            assert rel(O.apply_operator(med_o, u[b]), f[b]) <= 1e-8
+        # the same request through a plan on its own
+        med = hz.Medium(p.c, p.zeta, omega=p.omega, M=p.M, Mt=p.Mt, alpha=0.15)
+        plan = hz.Plan(med, precision=1, restart=30, tol=1e-8, max_nrhs=f.shape[0])
+        u1, st1 = plan.solve(np.ascontiguousarray(f))
+        assert np.array_equal(u1, u), rel(u1, u)
+        assert [s["iters"] for s in st1] == [s["iters"] for s in stats]
+    srv.close()
+
+
+def test_result_same_alone_and_in_mix(hz):
+    reqs = _requests()
+    p, f = reqs[1]
+    solo = hz.Server(max_slots=1)
+    ua = solo.result(_submit(solo, p, f))[1]
+    solo.close()
+    mix = hz.Server(max_slots=4)
+    ts = [_submit(mix, q, g) for q, g in reqs[3:]] + [_submit(mix, p, f)] + \
+         [_submit(mix, q, g) for q, g in reqs[:3]]
+    out = {t: mix.result(t) for t in ts}
+    assert np.array_equal(out[ts[len(reqs) - 3]][1], ua)
+    assert mix.stats()["max_active"] >= 2
+    mix.close()
+
+
+def test_admission_by_hbm_budget(hz):
+    reqs = _requests()[:4]
+    fps = [hz.request_footprint(p.shape, p.M, p.Mt, 1, 30, f.shape[0]) for p, f in reqs]
+    budget = int(max(fps) * 1.2)  # room for the largest alone, never two of the big ones
+    srv = hz.Server(max_slots=4, hbm_budget=budget)
+    ts = [_submit(srv, p, f) for p, f in reqs]
+    for t in ts:
+        done, u, stats, status = srv.result(t)
+        assert done and status == 0
+    st = srv.stats()
+    assert st["completed"] == 4 and st["hbm_in_use"] == 0
+    srv.close()
+    # a request larger than the whole budget is refused at submit
+    small = hz.Server(max_slots=1, hbm_budget=1 << 20)
+    p, f = reqs[0]
+    with pytest.raises(hz.HzError) as e:
+        _submit(small, p, f)
+    assert e.value.status == 7
+    small.close()
+
+
+def test_queue_limit_and_bad_request(hz):
+    reqs = _requests()
+    srv = hz.Server(max_slots=1, max_queue=1)
+    p, f = reqs[3]
+    t0 = _submit(srv, p, f)
+    refused = 0
+    for _ in range(4):
+        try:
+            _submit(srv, p, f)
+        except hz.HzError as e:
+            assert e.status == 7
+            refused += 1
+    assert refused >= 2
+    srv.result(t0)
+    with pytest.raises(hz.HzError) as e:
+        srv.submit(np.ones((20, 16)), np.zeros((1, 20, 16), complex), omega=3.0, M=2)
+    assert e.value.status == 1
+    srv.close()

@@ -32,16 +32,29 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-ALPHA = 0.1          # node-symbol damping a_k = alpha * omega (sweep in the design doc)
 METRIC = "Helmholtz solves/s at 1e-6 true relative residual"
-WORKLOAD = "2d-1024x1024-bumps20+gradient-layer32-ppw8-K16-fgmres40"
+
+# name -> (problem factory, alpha, graphs, workload label, L2 note)
+WORKLOADS = {
+    "cfg2": ("config2", 0.1, False, "2d-1024x1024-bumps20+gradient-layer32-ppw8-K16-fgmres40-c64",
+             "working set larger than L2 (basis 0.7 GB, planes 134 MB); no flush"),
+    "cfg1": ("config1", 0.15, True, "2d-128x128-bumps3-layer16-ppw10-K8-gmres30-fp64",
+             "L2-resident (17 MB working set); timed as repeated solves, not an HBM figure"),
+    "cfg3": ("config3", 0.15, False, "3d-256^3-layers6+incl10-layer24-ppw8-K16-fgmres40-c64",
+             "working set larger than L2 (basis 11 GB); no flush"),
+    "cfg4": ("config4", 0.15, False, "2d-512x512-bumps3-layer16-ppw10-K12-64rhs-fgmres40-c64",
+             "working set larger than L2 (basis 11 GB for 64 rhs); no flush"),
+}
+ALPHA = 0.1
+WORKLOAD = WORKLOADS["cfg2"][3]
 
 
-def workload_config(p):
-    return {"workload": WORKLOAD, "grid": list(p.shape), "K": p.K, "M": p.M, "Mt": p.Mt,
-            "omega": round(p.omega, 4), "restart": p.restart, "tol": p.tol, "nrhs": 1,
-            "alpha": ALPHA, "precond": "complex64", "krylov": "FP64 CGS2",
-            "l2": "working set larger than L2 (basis 0.7 GB, planes 134 MB); no flush"}
+def workload_config(p, name="cfg2", nrhs=1):
+    fac, alpha, graphs, label, l2 = WORKLOADS[name]
+    return {"workload": label, "grid": list(p.shape), "K": p.K, "M": p.M, "Mt": p.Mt,
+            "omega": round(p.omega, 4), "restart": p.restart, "tol": p.tol, "nrhs": nrhs,
+            "alpha": alpha, "precond": "complex64" if p.precision == 1 else "complex128",
+            "krylov": "FP64 CGS2", "graphs": graphs, "l2": l2}
 
 
 class ClockSampler:
@@ -126,19 +139,27 @@ def barrier(dist):
 
 
 def max_over_ranks(dist, x: float) -> float:
+    """Largest x over the ranks (the job's time is the slowest replica's)."""
     if dist is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
-def oracle_solve_sample(p, iters: int, workers: int):
+def job_rate(dist, world: int, units_per_rank: float, ms: float):
+    """(slowest rank's ms, whole-job units per second)."""
+    ms_max = max_over_ranks(dist, ms)
+    return ms_max, world * units_per_rank / (ms_max / 1e3)
+
+
+def oracle_solve_sample(p, iters: int, workers: int, alpha: float = ALPHA):
     """Bounded oracle sample: one FGMRES cycle of `iters` Arnoldi steps of the
     same workload (oracle as it stands, FP64 numpy / scipy)."""
     import oracle as O
-    med = O.make_medium(p.c, p.zeta, None, p.omega, p.M, p.Mt, p.c_o, None, ALPHA)
+    med = O.make_medium(p.c, p.zeta, None, p.omega, p.M, p.Mt, p.c_o, None, alpha)
     t0 = time.perf_counter()
     _, st = O.gmres(lambda u: O.apply_operator(med, u), p.f[0],
                     lambda v: O.apply_preconditioner(med, v, workers=workers),
@@ -186,7 +207,10 @@ def run_reference(args, p):
     print(json.dumps(out), flush=True)
 
 
-def run_gpu(args, p):
+FP64_DFMA_PER_CLK_PER_SM = 2  # sm_103 (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak)
+
+
+def run_gpu(args, p, name):
     import torch
     world, rank, local, dist = dist_setup(args.gpus)
     if world == 1:
@@ -197,27 +221,33 @@ def run_gpu(args, p):
     barrier(dist)
     from paper_2409_16172_gb300 import hz
 
-    med = hz.Medium(p.c, p.zeta, omega=p.omega, M=p.M, Mt=p.Mt, c_o=p.c_o, alpha=ALPHA)
-    plan = hz.Plan(med, precision=1, restart=p.restart, tol=p.tol, maxit=4000, max_nrhs=1)
-    f = torch.from_numpy(np.ascontiguousarray(p.f[0])).cuda()
+    fac, alpha, graphs, label, l2 = WORKLOADS[name]
+    nrhs = p.f.shape[0]
+    med = hz.Medium(p.c, p.zeta, omega=p.omega, M=p.M, Mt=p.Mt, c_o=p.c_o, alpha=alpha)
+    plan = hz.Plan(med, precision=p.precision, restart=p.restart, tol=p.tol, maxit=4000,
+                   max_nrhs=nrhs, graphs=graphs)
+    f = torch.from_numpy(np.ascontiguousarray(p.f)).cuda()
     u = torch.zeros_like(f)
     stream = torch.cuda.current_stream()
 
-    def solve():
+    def solve(pl=plan):
         u.zero_()
-        _, st = plan.solve(f, u, stream=stream)
-        return st[0]
+        _, st = pl.solve(f, u, stream=stream)
+        return st
 
     for _ in range(args.warmup):
-        st0 = solve()
+        solve()
     torch.cuda.synchronize()
-    fp64_gflops = hz.measure_fp64_peak()
+    fp64_probe = hz.measure_fp64_peak()
+    props = torch.cuda.get_device_properties(0)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp64_peak = FP64_DFMA_PER_CLK_PER_SM * 2 * props.multi_processor_count * sm_max * 1e6 / 1e12
 
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    hz.profile_enable(True)
-    hz.profile_read(reset=True)
+    hz.profile_enable(False)
     launches0 = hz.launch_count()
     barrier(dist)
     torch.cuda.synchronize()
@@ -229,16 +259,28 @@ def run_gpu(args, p):
     torch.cuda.synchronize()
     barrier(dist)
     launches = hz.launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    ms_max, value = job_rate(dist, world, nrhs * args.steps, ms)
+    # Per-kernel CUDA events on the launching stream, in a second pass of
+    # the same steps right after the timed one (events around every launch
+    # would add to the timed step; graph replay carries none, so that pass
+    # launches step by step)
+    plan_p = plan
+    if graphs:
+        plan_p = hz.Plan(med, precision=p.precision, restart=p.restart, tol=p.tol, maxit=4000,
+                         max_nrhs=nrhs, graphs=False)
+    hz.profile_enable(True)
+    hz.profile_read(reset=True)
+    for _ in range(max(1, min(args.steps, 3))):
+        solve(plan_p)
+    torch.cuda.synchronize()
     prof = hz.profile_read(reset=True)
     hz.profile_enable(False)
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    ms_max = max_over_ranks(dist, ms)
-    value = world * args.steps / (ms_max / 1e3)
 
     # end to end through the C ABI with host buffers: H2D of f and the
     # initial guess, D2H of the solution, inside the timed region
-    fh = np.ascontiguousarray(p.f[0])
+    fh = np.ascontiguousarray(p.f)
     e2e_steps = max(1, min(args.steps, 5))
     uh = np.zeros_like(fh)
     torch.cuda.synchronize()
@@ -249,29 +291,29 @@ def run_gpu(args, p):
         plan.solve(fh, uh, stream=stream)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
-    e2e_val = world * e2e_steps / e2e_s
+    e2e_val = world * nrhs * e2e_steps / e2e_s
 
-    ok = all(s["converged"] and s["rel_true_resid"] <= p.tol for s in stats)
+    ok = all(s["converged"] and s["rel_true_resid"] <= p.tol for st in stats for s in st)
     if rank != 0:
         return
-    peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     hbm_src = "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
-    # dominant kernel by summed event time
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
-    name, d = dom
+    kname, d = dom
     fp64_phases = {"cgs2_dots", "cgs2_update", "stencil", "residual", "solution_update", "norm"}
-    if name in fp64_phases:
+    if kname in fp64_phases:
         achieved = d["flops"] / d["ms"] / 1e9  # TFLOP/s
-        roof = {"kernel": name, "bound": "alu", "achieved": achieved,
-                "peak": fp64_gflops / 1e3, "unit": "TFLOP/s",
-                "frac": achieved / (fp64_gflops / 1e3), "traffic": None,
-                "peak_source": "FP64 FMA probe on this GPU (hz_measure_fp64_peak)",
+        roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                "peak_source": f"FP64: {FP64_DFMA_PER_CLK_PER_SM} DFMA/clk/SM x 2 flops x "
+                               f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz "
+                               f"(in-library FMA probe {fp64_probe / 1e3:.3f} TFLOP/s)",
                 "launches": d["launches"], "avg_launch_us": 1e3 * d["ms"] / d["launches"],
-                "hbm_gbs_achieved": d["bytes"] / d["ms"] / 1e6}
+                "hbm_gbs_achieved": d["bytes"] / d["ms"] / 1e6,
+                "timing": "CUDA events per launch, profiled pass of the same steps"}
     else:
         achieved = d["bytes"] / d["ms"] / 1e6  # GB/s
-        roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm,
+        roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
                 "peak_source": hbm_src, "launches": d["launches"],
                 "avg_launch_us": 1e3 * d["ms"] / d["launches"]}
@@ -295,25 +337,79 @@ def run_gpu(args, p):
     cpu = None
     if not args.no_cpu_baseline:
         workers = os.cpu_count() or 1
-        dt, it = oracle_solve_sample(p, args.cpu_iters, workers)
-        iters = stats[0]["iters"]
+        its = args.cpu_iters if name != "cfg3" else min(args.cpu_iters, 2)
+        pc = p
+        if nrhs > 1:  # one right-hand side of the batch; the rate is per solve
+            import copy
+            pc = copy.copy(p)
+            pc.f = p.f[:1]
+        dt, it = oracle_solve_sample(pc, its, workers, alpha)
+        iters = int(np.mean([s["iters"] for s in stats[0]]))
         cpu = {"value": 1.0 / (dt / max(it, 1) * iters), "unit": "solves/s", "cores": workers,
                "kind": "oracle",
-               "sample": f"{it} oracle FGMRES(40) Arnoldi steps of the workload ({dt:.1f} s); "
-                         f"scaled by the {iters} steps of the GPU solve"}
+               "sample": f"{it} oracle (F)GMRES Arnoldi steps of one right-hand side of the "
+                         f"workload ({dt:.1f} s); scaled by the {iters} steps of the GPU solve"}
     n = p.n
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "c64+c128", "data": "synthetic", "config": workload_config(p),
-           "iters": stats[0]["iters"], "rel_true_resid": stats[0]["rel_true_resid"],
+           "dtype": "c64+c128" if p.precision == 1 else "c128", "data": "synthetic",
+           "config": workload_config(p, name, nrhs),
+           "iters": [s["iters"] for s in stats[0]][:8],
+           "rel_true_resid": max(s["rel_true_resid"] for s in stats[0]),
            "all_converged": ok,
            "roofline": roof, "roofline_precond": precond,
            "cpu_baseline": cpu,
-           "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": 2 * 16 * n,
-                   "d2h_bytes_per_step": 16 * n},
+           "e2e": {"value": e2e_val, "unit": "solves/s",
+                   "h2d_bytes_per_step": 2 * 16 * n * nrhs, "d2h_bytes_per_step": 16 * n * nrhs},
            "gpu_launches": launches, "clocks": clocks, "phases": phases,
-           "fp64_peak_tflops": fp64_gflops / 1e3}
+           "fp64_peak_tflops": fp64_peak, "fp64_probe_tflops": fp64_probe / 1e3}
+    print(json.dumps(out), flush=True)
+
+
+def run_serving(args):
+    """Serving stream: requests drawn from the serving recipe arrive with
+    seeded exponential gaps; the server admits them by HBM footprint."""
+    import torch
+    from paper_2409_16172_gb300 import build, synth as S
+    build.build()
+    from paper_2409_16172_gb300 import hz
+    torch.cuda.set_device(0)
+    rng = np.random.Generator(np.random.PCG64(16177))
+    reqs = [S.serving_request(rng) for _ in range(args.requests)]
+    gaps = rng.exponential(1.0 / args.rate, size=len(reqs))
+    srv = hz.Server(max_slots=args.slots)
+    # warm-up: one small request of each dimension
+    for q in reqs[:2]:
+        srv.result(srv.submit(q.c, q.f, omega=q.omega, M=q.M, Mt=q.Mt, zeta=q.zeta, alpha=0.15,
+                              restart=q.restart, tol=q.tol), timeout=600)
+    srv.close()
+    srv = hz.Server(max_slots=args.slots)
+    sampler = ClockSampler(0)
+    sampler.start()
+    t0 = time.perf_counter()
+    tickets = []
+    for q, g in zip(reqs, gaps):
+        time.sleep(g)
+        tickets.append(srv.submit(q.c, q.f, omega=q.omega, M=q.M, Mt=q.Mt, zeta=q.zeta,
+                                  alpha=0.15, restart=q.restart, tol=q.tol,
+                                  graphs=q.n <= 256 * 256))
+    res = [srv.result(t, timeout=1800) for t in tickets]
+    span = time.perf_counter() - t0
+    st = srv.stats()
+    clocks = sampler.stop()
+    srv.close()
+    rhs = sum(q.f.shape[0] for q in reqs)
+    ok = all(r[0] and r[3] == 0 for r in res)
+    out = {"metric": METRIC + " (serving stream)", "value": rhs / span, "unit": "solves/s",
+           "n_gpus": 1, "steps": len(reqs), "warmup": 2, "ms_per_step": 1e3 * span / len(reqs),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "c64+c128", "data": "synthetic",
+           "config": {"workload": f"serving-{len(reqs)}req-poisson{args.rate}/s-slots{args.slots}",
+                      "grids": sorted({"x".join(map(str, q.shape)) for q in reqs}),
+                      "rhs_total": rhs},
+           "latency": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"]},
+           "server": st, "all_converged": ok, "clocks": clocks}
     print(json.dumps(out), flush=True)
 
 
@@ -323,6 +419,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", choices=["cfg2", "cfg1", "cfg3", "cfg4", "serving"],
+                    default="cfg2", help="cfg2 (default): the 2D 1024^2 K=16 workload")
+    ap.add_argument("--requests", type=int, default=30, help="serving: number of requests")
+    ap.add_argument("--rate", type=float, default=4.0, help="serving: arrivals per second")
+    ap.add_argument("--slots", type=int, default=4, help="serving: concurrent requests")
     ap.add_argument("--cpu-iters", type=int, default=6, help="Arnoldi steps in the CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=3, help="reference arm: steps per sample")
@@ -331,11 +432,14 @@ def main():
                          "untimed oracle solve)")
     args = ap.parse_args()
     from paper_2409_16172_gb300 import synth as S
-    p = S.config2()
+    if args.workload == "serving":
+        run_serving(args)
+        return
+    p = getattr(S, WORKLOADS[args.workload][0])()
     if args.impl == "reference":
         run_reference(args, p)
     else:
-        run_gpu(args, p)
+        run_gpu(args, p, args.workload)
 
 
 if __name__ == "__main__":

@@ -86,12 +86,16 @@ typedef struct {
  *                 operator and residuals stay FP64.
  *   restart    m, the Krylov dimension per cycle (1..128).
  *   tol        stop when ||f - P_N u||_2 / ||f||_2 <= tol (true residual).
- *   maxit      cap on the total number of Arnoldi steps.               */
+ *   maxit      cap on the total number of Arnoldi steps.
+ *   graphs     1: capture each full Arnoldi cycle once as a CUDA graph and
+ *              replay it (worth it for small grids, where launches cost as
+ *              much as the kernels); 0: launch step by step.             */
 typedef struct {
   int precision;
   int restart;
   double tol;
   int maxit;
+  int graphs;
 } hz_solver_opts;
 
 typedef struct {

@@ -129,7 +129,7 @@ static hz_status ensure_planes(hz_plan* p, int prec) {
 // in: nrhs c128 vectors at stride n, each scaled by scale[b] (NULL = 1).
 // out_kind 0: c64 output, 1: c128 output.  prec 0: complex128 arithmetic.
 hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* scale, int nrhs,
-                        void* out, int out_kind, cudaStream_t st) {
+                        void* out, int out_kind, cudaStream_t st, const int* active) {
   const hz_medium* m = p->med;
   HZ_TRY(ensure_planes(p, prec));
   const int nx = m->nx, ny = m->ny, nz = m->nz;
@@ -151,45 +151,46 @@ hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* s
   auto l2 = [](int N) { return std::log2(double(N)); };
   {
     PhaseScope ps(st, PH_ROW_FWD, B * dn * (16.0 + s), B * 5.0 * dn * l2(nx));
-    HZ_TRY(ox->row_fwd(prec, in, scale, rows, rows * nrhs, tw(tx), p->tmp, st));
+    HZ_TRY(ox->row_fwd(prec, in, scale, rows, rows * nrhs, tw(tx), p->tmp, st, active));
   }
   // forward FFT along every axis but x, in place on tmp
   {
     PhaseScope ps(st, PH_LINE, B * 2.0 * s * dn, B * 5.0 * dn * l2(ny));
     HZ_TRY(oy->line_pass(prec, -1, p->tmp, nx, nz, nx, long(nx) * ny, n, nrhs, nullptr, m->K,
-                         tw(ty), st));
+                         tw(ty), st, active, 1));
   }
   if (m->dim == 2) {
     PhaseScope ps(st, PH_SYMINV, B * (dn * s + m->rowk_used * nx * s),
                   B * K * (5.0 * dn * l2(ny) + 14.0 * dn));
     HZ_TRY(oy->line_sym_inv(prec, p->tmp, p->planes, nx, 1, nx, 0, n, m->K, nrhs, xi(tx), nullptr,
-                            xi(ty), A, G, m->rowmask, 0, 1, tw(ty), st));
+                            xi(ty), A, G, m->rowmask, 0, 1, tw(ty), st, active));
   } else {
     const FftOps* oz = fft_ops(nz);
     const AxisTables& tz = m->ax[2];
     const long slab = long(nx) * ny;
     {
       PhaseScope ps(st, PH_LINE, B * 2.0 * s * dn, B * 5.0 * dn * l2(nz));
-      HZ_TRY(oz->line_pass(prec, -1, p->tmp, nx, ny, slab, nx, n, nrhs, nullptr, m->K, tw(tz), st));
+      HZ_TRY(oz->line_pass(prec, -1, p->tmp, nx, ny, slab, nx, n, nrhs, nullptr, m->K, tw(tz), st,
+                           active, 1));
     }
     {
       PhaseScope ps(st, PH_SYMINV, B * (dn * s + m->slabk_used * slab * s),
                     B * K * (5.0 * dn * l2(nz) + 14.0 * dn));
       HZ_TRY(oz->line_sym_inv(prec, p->tmp, p->planes, nx, ny, slab, nx, n, m->K, nrhs, xi(tx),
-                              xi(ty), xi(tz), A, G, m->slabmask, 0, 1, tw(tz), st));
+                              xi(ty), xi(tz), A, G, m->slabmask, 0, 1, tw(tz), st, active));
     }
     {
       PhaseScope ps(st, PH_LINE, B * 2.0 * s * m->slabk_used * slab,
                     B * 5.0 * m->slabk_used * slab * l2(ny));
       HZ_TRY(oy->line_pass(prec, +1, p->planes, nx, nz, nx, slab, n, nrhs * m->K, m->slabmask, m->K,
-                           tw(ty), st));
+                           tw(ty), st, active, m->K));
     }
   }
   {
     PhaseScope ps(st, PH_ROW_INV, B * (m->rowk_used * nx * s + dn * (rb + so)),
                   B * (m->rowk_used * 5.0 * nx * l2(nx) + 8.0 * dn));
     HZ_TRY(ox->row_inv_acc(prec, out_kind, p->planes, rec, m->segtab, m->nseg, m->rowmask, m->K,
-                           rows, rows * nrhs, n, 1.0 / double(n), tw(tx), out, st));
+                           rows, rows * nrhs, n, 1.0 / double(n), tw(tx), out, st, active));
   }
   return HZ_OK;
 }
@@ -286,5 +287,5 @@ extern "C" hz_status hz_apply_preconditioner(hz_plan* plan, const void* x, void*
   if (nrhs < 1 || nrhs > plan->max_nrhs) return set_error(HZ_ERR_INVALID_ARG, "nrhs out of range");
   if (precision != 0 && precision != 1) return set_error(HZ_ERR_INVALID_ARG, "precision must be 0 or 1");
   return precond_apply(plan, precision, static_cast<const double2*>(x), nullptr, nrhs, y, 1,
-                       static_cast<cudaStream_t>(stream));
+                       static_cast<cudaStream_t>(stream), nullptr);
 }

@@ -123,12 +123,46 @@ template <int S, typename V> __device__ __forceinline__ void dft16(V* x) {
   }
 }
 
+// w32^k = cos(2 pi k / 32) + S i sin(2 pi k / 32), k = 0..15
+template <int S, typename V> __device__ __forceinline__ V w32mul(V a, int k) {
+  using R = decltype(V::x);
+  constexpr double C[8] = {1.0,
+                           0.980785280403230449126182, 0.923879532511286756128183,
+                           0.831469612302545237078788, 0.707106781186547524400844,
+                           0.555570233019602224742831, 0.382683432365089771728460,
+                           0.195090322016128267848285};
+  if (k == 0) return a;
+  if (k == 8) return cmul_si<S>(a);
+  if (k < 8) return cmul(a, cmk<V>(R(C[k]), R(S) * R(C[8 - k])));
+  // w^(8 + m) = S i w^m
+  return cmul_si<S>(cmul(a, cmk<V>(R(C[k - 8]), R(S) * R(C[16 - k]))));
+}
+
+// 32-point DFT as two 16-point DFTs of the even and odd samples.
+template <int S, typename V> __device__ __forceinline__ void dft32(V* x) {
+  V e[16], o[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    e[i] = x[2 * i];
+    o[i] = x[2 * i + 1];
+  }
+  dft16<S>(e);
+  dft16<S>(o);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const V t = w32mul<S>(o[k], k);
+    x[k] = cadd(e[k], t);
+    x[k + 16] = csub(e[k], t);
+  }
+}
+
 template <int RAD, int S, typename V> __device__ __forceinline__ void dftR(V* x) {
   if constexpr (RAD == 2) dft2<S>(x);
   else if constexpr (RAD == 3) dft3<S>(x);
   else if constexpr (RAD == 4) dft4<S>(x);
   else if constexpr (RAD == 8) dft8<S>(x);
   else if constexpr (RAD == 16) dft16<S>(x);
+  else if constexpr (RAD == 32) dft32<S>(x);
   else static_assert(RAD == 2, "unsupported radix");
 }
 
@@ -136,8 +170,9 @@ template <int RAD, int S, typename V> __device__ __forceinline__ void dftR(V* x)
 // Radix plans: N = prod(radices); E is a multiple of every radix.
 // ---------------------------------------------------------------------------
 template <int N> struct FftPlan;
-#define HZ_PLAN(NN, EE, ...)                                               \
-  template <> struct FftPlan<NN> {                                         \
+#define HZ_PLAN(NN, EE, ...) HZ_PLAN_T(FftPlan<NN>, NN, EE, __VA_ARGS__)
+#define HZ_PLAN_T(NAME, NN, EE, ...)                                       \
+  template <> struct NAME {                                                \
     static constexpr int E = EE;                                           \
     static constexpr int rads[] = {__VA_ARGS__};                           \
     static constexpr int NST = sizeof(rads) / sizeof(int);                 \
@@ -157,7 +192,18 @@ HZ_PLAN(256, 16, 16, 16)
 HZ_PLAN(512, 8, 8, 8, 8)
 HZ_PLAN(1024, 16, 16, 16, 4)
 HZ_PLAN(2048, 16, 16, 16, 8)
+
+// Row plans (contiguous lines, complex64): 32 threads per line for N = 512
+// and 1024 so that a line is one warp and its stage barriers are warp
+// barriers.  Other lengths and complex128 use the plans above.
+template <typename R, int N> struct RowPlan { using P = FftPlan<N>; };
+template <int N> struct FftPlanW;
+HZ_PLAN_T(FftPlanW<512>, 512, 16, 16, 16, 2)
+HZ_PLAN_T(FftPlanW<1024>, 1024, 32, 32, 32)
+template <> struct RowPlan<float, 512> { using P = FftPlanW<512>; };
+template <> struct RowPlan<float, 1024> { using P = FftPlanW<1024>; };
 #undef HZ_PLAN
+#undef HZ_PLAN_T
 
 constexpr int PAD_SHIFT = 4;
 __host__ __device__ constexpr int padded(int i) { return i + (i >> PAD_SHIFT); }
@@ -165,12 +211,21 @@ __host__ __device__ constexpr int padded_len(int n) { return n + (n >> PAD_SHIFT
 
 // LS: distance in elements between consecutive positions of a line in shared
 // memory (1 for a private line, TB when TB lines are interleaved).
-template <typename R, int N, int S, int LS = 1> struct LineFFT {
+// WS: the threads of a line lie in one warp (TPL <= 32 and lines laid out
+// warp by warp), so the stage barriers are warp barriers.
+template <typename R, int N, int S, int LS = 1, bool WS = false, typename PL = FftPlan<N>>
+struct LineFFT {
   using V = typename cvec<R>::T;
-  using P = FftPlan<N>;
+  using P = PL;
   static constexpr int E = P::E;
   static constexpr int TPL = N / E;
   static constexpr int R0 = P::rad(0);
+  static_assert(!WS || TPL <= 32, "warp-synchronous lines need TPL <= 32");
+
+  __device__ static __forceinline__ void sync() {
+    if constexpr (WS) __syncwarp();
+    else __syncthreads();
+  }
 
   // Frequency / position index held in x[e] before stage 0 (the stage-0
   // read pattern): b = e / R0, r = e % R0, j = t + b TPL, index = j + r N/R0.
@@ -194,7 +249,7 @@ template <typename R, int N, int S, int LS = 1> struct LineFFT {
 #pragma unroll
           for (int r = 0; r < RAD; ++r) x[b * RAD + r] = line[padded(j + r * (N / RAD)) * LS];
         }
-        __syncthreads();
+        sync();
       }
 #pragma unroll
       for (int b = 0; b < E / RAD; ++b) {
@@ -213,15 +268,15 @@ template <typename R, int N, int S, int LS = 1> struct LineFFT {
 #pragma unroll
         for (int r = 0; r < RAD; ++r) line[padded(d + r * NS) * LS] = x[b * RAD + r];
       }
-      __syncthreads();
+      sync();
       stage<STAGE + 1, NS * RAD>(line, t, x, tw);
     }
   }
 
   // Runs the whole transform.  On entry x holds the stage-0 inputs and every
-  // thread of the block has finished reading the line (the caller syncs).
-  // On exit the line holds the result in natural order and the block is
-  // synchronised.  tw[i] = exp(-2 pi i * i / N) for i < N.
+  // thread of the line has finished reading it (the caller syncs).  On exit
+  // the line holds the result in natural order and the line's threads (the
+  // block, unless WS) are synchronised.  tw[i] = exp(-2 pi i * i / N) for i < N.
   __device__ static __forceinline__ void run(V* line, int t, V (&x)[E], const V* __restrict__ tw) {
     stage<0, 1>(line, t, x, tw);
   }

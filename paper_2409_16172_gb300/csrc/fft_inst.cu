@@ -22,28 +22,29 @@ hz_status smem_attr(K kernel, size_t bytes) {
 
 template <typename R>
 hz_status row_fwd_t(const double2* in, const double* scale, long rows_per_rhs, long nrows,
-                    const void* tw, void* out, cudaStream_t st) {
+                    const void* tw, void* out, cudaStream_t st, const int* active) {
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
   auto k = row_fwd_kernel<R, N>;
   HZ_TRY(smem_attr(k, C::row_smem()));
   const long blocks = (nrows + C::ROW_LINES - 1) / C::ROW_LINES;
   k<<<unsigned(blocks), C::ROW_THREADS, C::row_smem(), st>>>(
-      in, scale, rows_per_rhs, nrows, static_cast<const V*>(tw), static_cast<V*>(out));
+      in, scale, rows_per_rhs, nrows, static_cast<const V*>(tw), static_cast<V*>(out), active);
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
 
 hz_status row_fwd(int prec, const double2* in, const double* scale, long rows_per_rhs, long nrows,
-                  const void* tw, void* out, cudaStream_t st) {
-  return prec == 0 ? row_fwd_t<double>(in, scale, rows_per_rhs, nrows, tw, out, st)
-                   : row_fwd_t<float>(in, scale, rows_per_rhs, nrows, tw, out, st);
+                  const void* tw, void* out, cudaStream_t st, const int* active) {
+  return prec == 0 ? row_fwd_t<double>(in, scale, rows_per_rhs, nrows, tw, out, st, active)
+                   : row_fwd_t<float>(in, scale, rows_per_rhs, nrows, tw, out, st, active);
 }
 
 template <typename R, typename OutT>
 hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segtab, int nseg,
                         const unsigned long long* rowmask, int K, long rows_per_rhs, long nrows,
-                        long n, double inv_n, const void* tw, void* out, cudaStream_t st) {
+                        long n, double inv_n, const void* tw, void* out, cudaStream_t st,
+                        const int* active) {
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
   auto k = row_inv_acc_kernel<R, N, OutT>;
@@ -52,7 +53,7 @@ hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segta
   k<<<unsigned(blocks), C::ROW_THREADS, C::row_acc_smem(), st>>>(
       static_cast<const V*>(planes), static_cast<const typename RecT<R>::T*>(rec), segtab, nseg,
       rowmask, K, rows_per_rhs, nrows, n, R(inv_n), static_cast<const V*>(tw),
-      static_cast<OutT*>(out));
+      static_cast<OutT*>(out), active);
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
@@ -60,21 +61,21 @@ hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segta
 hz_status row_inv_acc(int prec, int out_kind, const void* planes, const void* rec,
                       const uchar2* segtab, int nseg, const unsigned long long* rowmask, int K,
                       long rows_per_rhs, long nrows, long n, double inv_n, const void* tw,
-                      void* out, cudaStream_t st) {
+                      void* out, cudaStream_t st, const int* active) {
   if (prec == 0)
     return row_inv_acc_t<double, double2>(planes, rec, segtab, nseg, rowmask, K, rows_per_rhs,
-                                          nrows, n, inv_n, tw, out, st);
+                                          nrows, n, inv_n, tw, out, st, active);
   if (out_kind == 0)
     return row_inv_acc_t<float, float2>(planes, rec, segtab, nseg, rowmask, K, rows_per_rhs,
-                                        nrows, n, inv_n, tw, out, st);
+                                        nrows, n, inv_n, tw, out, st, active);
   return row_inv_acc_t<float, double2>(planes, rec, segtab, nseg, rowmask, K, rows_per_rhs,
-                                       nrows, n, inv_n, tw, out, st);
+                                       nrows, n, inv_n, tw, out, st, active);
 }
 
 template <typename R, int SIGN>
 hz_status line_pass_t(void* data, int nx, long outer, long S, long ostride, long bstride,
                       int batch, const unsigned long long* omask, int K, const void* tw,
-                      cudaStream_t st) {
+                      cudaStream_t st, const int* active, int per_rhs) {
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
   auto k = line_pass_kernel<R, N, SIGN>;
@@ -83,19 +84,19 @@ hz_status line_pass_t(void* data, int nx, long outer, long S, long ostride, long
   dim3 grid(unsigned(ntile * outer), 1, unsigned(batch));
   k<<<grid, C::COL_THREADS, C::col_smem(), st>>>(static_cast<V*>(data), nx, ntile, S,
                                                        ostride, bstride, omask, K,
-                                                       static_cast<const V*>(tw));
+                                                       static_cast<const V*>(tw), active, per_rhs);
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
 
 hz_status line_pass(int prec, int sign, void* data, int nx, long outer, long S, long ostride,
                     long bstride, int batch, const unsigned long long* omask, int K,
-                    const void* tw, cudaStream_t st) {
+                    const void* tw, cudaStream_t st, const int* active, int per_rhs) {
   if (prec == 0)
-    return sign < 0 ? line_pass_t<double, -1>(data, nx, outer, S, ostride, bstride, batch, omask, K, tw, st)
-                    : line_pass_t<double, +1>(data, nx, outer, S, ostride, bstride, batch, omask, K, tw, st);
-  return sign < 0 ? line_pass_t<float, -1>(data, nx, outer, S, ostride, bstride, batch, omask, K, tw, st)
-                  : line_pass_t<float, +1>(data, nx, outer, S, ostride, bstride, batch, omask, K, tw, st);
+    return sign < 0 ? line_pass_t<double, -1>(data, nx, outer, S, ostride, bstride, batch, omask, K, tw, st, active, per_rhs)
+                    : line_pass_t<double, +1>(data, nx, outer, S, ostride, bstride, batch, omask, K, tw, st, active, per_rhs);
+  return sign < 0 ? line_pass_t<float, -1>(data, nx, outer, S, ostride, bstride, batch, omask, K, tw, st, active, per_rhs)
+                  : line_pass_t<float, +1>(data, nx, outer, S, ostride, bstride, batch, omask, K, tw, st, active, per_rhs);
 }
 
 template <typename R>
@@ -103,7 +104,7 @@ hz_status line_sym_inv_t(const void* vhat, void* planes, int nx, long outer, lon
                          long n, int K, int batch, const void* xi2_x, const void* xi2_o,
                          const void* xi2_l, const void* symA, const void* symG,
                          const unsigned long long* smask, long smO, long smS, const void* tw,
-                         cudaStream_t st) {
+                         cudaStream_t st, const int* active) {
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
   auto k = line_sym_inv_kernel<R, N>;
@@ -114,7 +115,7 @@ hz_status line_sym_inv_t(const void* vhat, void* planes, int nx, long outer, lon
       static_cast<const V*>(vhat), static_cast<V*>(planes), nx, ntile, S, ostride, n, K,
       static_cast<const R*>(xi2_x), static_cast<const R*>(xi2_o), static_cast<const R*>(xi2_l),
       static_cast<const V*>(symA), static_cast<const V*>(symG), smask, smO, smS,
-      static_cast<const V*>(tw));
+      static_cast<const V*>(tw), active);
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
@@ -123,12 +124,12 @@ hz_status line_sym_inv(int prec, const void* vhat, void* planes, int nx, long ou
                        long ostride, long n, int K, int batch, const void* xi2_x,
                        const void* xi2_o, const void* xi2_l, const void* symA, const void* symG,
                        const unsigned long long* smask, long smO, long smS, const void* tw,
-                       cudaStream_t st) {
+                       cudaStream_t st, const int* active) {
   return prec == 0
              ? line_sym_inv_t<double>(vhat, planes, nx, outer, S, ostride, n, K, batch, xi2_x,
-                                      xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, st)
+                                      xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, st, active)
              : line_sym_inv_t<float>(vhat, planes, nx, outer, S, ostride, n, K, batch, xi2_x,
-                                     xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, st);
+                                     xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, st, active);
 }
 
 const FftOps ops = {N, row_fwd, row_inv_acc, line_pass, line_sym_inv};

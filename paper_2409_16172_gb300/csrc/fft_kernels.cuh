@@ -27,9 +27,13 @@ namespace hz {
 // block moves at least 64 contiguous bytes per row, has >= 128 threads, at
 // most 512, and its shared memory stays under ~200 KB.
 template <typename R, int N> struct LineCfg {
-  static constexpr int TPL = N / FftPlan<N>::E;
-  static constexpr int ROW_THREADS = TPL > 128 ? TPL : 128;
-  static constexpr int ROW_LINES = ROW_THREADS / TPL;
+  static constexpr int TPL = N / FftPlan<N>::E;  // strided kernels
+  using RP = typename RowPlan<R, N>::P;           // row kernels
+  static constexpr int TPL_ROW = N / RP::E;
+  static constexpr int ROW_THREADS = TPL_ROW > 128 ? TPL_ROW : 128;
+  static constexpr int ROW_LINES = ROW_THREADS / TPL_ROW;
+  // row kernels: a line's threads sit in one warp -> warp barriers
+  static constexpr bool WS = TPL_ROW <= 32;
   static constexpr int VB = int(2 * sizeof(R));
   static constexpr int tb_calc() {
     int tb = 32 / VB;                 // one 32-byte sector per row at least
@@ -81,15 +85,16 @@ template <typename R, int N>
 __global__ void __launch_bounds__(LineCfg<R, N>::ROW_THREADS)
 row_fwd_kernel(const double2* __restrict__ in, const double* __restrict__ scale,
                long rows_per_rhs, long nrows, const typename cvec<R>::T* __restrict__ tw,
-               typename cvec<R>::T* __restrict__ out) {
+               typename cvec<R>::T* __restrict__ out, const int* __restrict__ active) {
   using V = typename cvec<R>::T;
-  using F = LineFFT<R, N, -1>;
+  using F = LineFFT<R, N, -1, 1, LineCfg<R, N>::WS, typename LineCfg<R, N>::RP>;
   constexpr int TPL = F::TPL, E = F::E, LPB = LineCfg<R, N>::ROW_LINES;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
   const int li = threadIdx.x / TPL, t = threadIdx.x % TPL;
   const long row = long(blockIdx.x) * LPB + li;
-  const bool valid = row < nrows;
+  // rows of retired right-hand sides (active[rhs] == 0) are skipped
+  const bool valid = row < nrows && (!active || active[row / rows_per_rhs]);
   V* line = sm + li * padded_len(N);
   V x[E];
   // the Krylov scale is applied after rounding to the working precision
@@ -124,9 +129,11 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
                    const typename RecT<R>::T* __restrict__ rec, const uchar2* __restrict__ segtab,
                    int nseg, const unsigned long long* __restrict__ rowmask, int K,
                    long rows_per_rhs, long nrows, long n, R inv_n,
-                   const typename cvec<R>::T* __restrict__ tw, OutT* __restrict__ out) {
+                   const typename cvec<R>::T* __restrict__ tw, OutT* __restrict__ out,
+                   const int* __restrict__ active) {
   using V = typename cvec<R>::T;
-  using F = LineFFT<R, N, +1>;
+  constexpr bool WS = LineCfg<R, N>::WS;
+  using F = LineFFT<R, N, +1, 1, WS, typename LineCfg<R, N>::RP>;
   constexpr int TPL = F::TPL, E = F::E, LPB = LineCfg<R, N>::ROW_LINES;
   constexpr int CH = N * int(sizeof(V)) / 16;  // 16-byte chunks per row
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -136,7 +143,7 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
   for (int i = threadIdx.x; i < nseg; i += blockDim.x) seg_s[i] = segtab[i];
   const int li = threadIdx.x / TPL, t = threadIdx.x % TPL;
   const long row = long(blockIdx.x) * LPB + li;
-  const bool valid = row < nrows;
+  const bool valid = row < nrows && (!active || active[row / rows_per_rhs]);
   const long rhs = valid ? row / rows_per_rhs : 0;
   const long lrow = valid ? row - rhs * rows_per_rhs : 0;
   unsigned long long mymask = valid ? rowmask[lrow] : 0ull;
@@ -154,7 +161,14 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
     acc[i] = cmk<V>(R(0), R(0));
   }
   __syncthreads();
-  const unsigned long long cm = cta_mask;
+  // planes to transform: those any line of the block needs, or with
+  // warp-synchronous lines only those the lines of this warp need
+  unsigned long long cm = cta_mask;
+  if constexpr (WS) {
+    const unsigned lo = __reduce_or_sync(0xffffffffu, unsigned(mymask & 0xFFFFFFFFull));
+    const unsigned hi = __reduce_or_sync(0xffffffffu, unsigned(mymask >> 32));
+    cm = (unsigned long long)lo | ((unsigned long long)hi << 32);
+  }
   const V* pbase = planes + (rhs * K) * n + lrow * N;
   auto issue = [&](int kk, int buf) {
     if ((mymask >> kk) & 1ull) {
@@ -180,7 +194,7 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
       cp_async_commit();  // keep one group in flight per step
     }
     cp_async_wait1();   // this thread's copies of plane kc are done
-    __syncthreads();    // ... and everyone's; the previous results were read
+    F::sync();          // ... and the line's; the previous results were read
     const bool need = (mymask >> kc) & 1ull;
     V x[E];
 #pragma unroll
@@ -229,7 +243,8 @@ template <typename R, int N, int SIGN>
 __global__ void __launch_bounds__(LineCfg<R, N>::COL_THREADS)
 line_pass_kernel(typename cvec<R>::T* __restrict__ data, int nx, int ntile, long S, long ostride,
                  long bstride, const unsigned long long* __restrict__ omask, int K,
-                 const typename cvec<R>::T* __restrict__ tw) {
+                 const typename cvec<R>::T* __restrict__ tw, const int* __restrict__ active,
+                 int per_rhs) {
   using V = typename cvec<R>::T;
   constexpr int TB = LineCfg<R, N>::TB;
   using F = LineFFT<R, N, SIGN, TB>;
@@ -243,6 +258,7 @@ line_pass_kernel(typename cvec<R>::T* __restrict__ data, int nx, int ntile, long
   const bool valid = x < nx;
   // omask (planes only): skip outer slices o that no row of plane k needs
   if (omask && !((omask[o] >> (blockIdx.z % K)) & 1ull)) return;
+  if (active && !active[blockIdx.z / per_rhs]) return;
   V* base = data + long(blockIdx.z) * bstride + o * ostride + x;
   V* line = sm + col;
   V v[E];
@@ -270,10 +286,11 @@ line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
                     const typename cvec<R>::T* __restrict__ symA,
                     const typename cvec<R>::T* __restrict__ symG,
                     const unsigned long long* __restrict__ smask, long smO, long smS,
-                    const typename cvec<R>::T* __restrict__ tw) {
+                    const typename cvec<R>::T* __restrict__ tw, const int* __restrict__ active) {
   using V = typename cvec<R>::T;
   constexpr int TB = LineCfg<R, N>::TB;
   using F = LineFFT<R, N, +1, TB>;
+  if (active && !active[blockIdx.z]) return;
   constexpr int TPL = F::TPL, E = F::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);

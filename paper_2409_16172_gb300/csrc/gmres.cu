@@ -22,7 +22,7 @@
 
 namespace hz {
 hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* scale, int nrhs,
-                        void* out, int out_kind, cudaStream_t st);
+                        void* out, int out_kind, cudaStream_t st, const int* active);
 }
 
 using namespace hz;
@@ -92,6 +92,10 @@ void solve_ws_destroy(hz_plan* p) {
     if (e) cudaEventDestroy(e);
   if (w->t0) cudaEventDestroy(w->t0);
   if (w->t1) cudaEventDestroy(w->t1);
+  if (w->cyc_exec) cudaGraphExecDestroy(w->cyc_exec);
+  for (auto& e : w->gev)
+    if (e) cudaEventDestroy(e);
+  if (w->gstream) cudaStreamDestroy(w->gstream);
   delete w;
   p->ws = nullptr;
 }
@@ -203,7 +207,8 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
     for (int b = 0; b < nrhs; ++b)
       if (!done[b]) maxit_left = std::max(maxit_left, p->opts.maxit - iters[b]);
     const int jmax = std::min(m, maxit_left);
-    for (int j = 0; j < jmax; ++j) {
+    // one Arnoldi step for every live right-hand side (no host interaction)
+    auto step = [&](int j, cudaStream_t st) -> hz_status {
       const double2* Vj = p->V + long(j) * ldb * n;
       double2* Vn = p->V + long(j + 1) * ldb * n;
       const double* sig_j = ks.sigma + long(j) * B;
@@ -211,12 +216,12 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
       const double stf = Bn * (med->dim == 3 ? 30.0 : 26.0);
       if (prec == 1) {
         float2* Zj = static_cast<float2*>(p->Z) + long(j) * ldb * n;
-        HZ_TRY(precond_apply(p, 1, Vj, sig_j, nrhs, Zj, 0, st));
+        HZ_TRY(precond_apply(p, 1, Vj, sig_j, nrhs, Zj, 0, st, ks.active));
         PhaseScope ps(st, PH_STENCIL, stb, stf);
         HZ_TRY(launch_stencil(med, 1, Zj, n, Vn, n, nrhs, ks.active, st));
       } else {
         double2* zt = static_cast<double2*>(p->Z);
-        HZ_TRY(precond_apply(p, 0, Vj, sig_j, nrhs, zt, 1, st));
+        HZ_TRY(precond_apply(p, 0, Vj, sig_j, nrhs, zt, 1, st, ks.active));
         PhaseScope ps(st, PH_STENCIL, stb, stf);
         HZ_TRY(launch_stencil(med, 0, zt, n, Vn, n, nrhs, ks.active, st));
       }
@@ -233,15 +238,58 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
         HZ_TRY(launch_update(p->V, ldb, Vn, n, n, j, nrhs, S, m + 1, ks.sigma, B, ks.active, pass == 1,
                              p->partial, nblk_k, ks.nrm2, st));
       }
-      {
-        PhaseScope ps(st, PH_GIVENS, 0.0, 0.0);
-        HZ_TRY(launch_givens(ks, j, nrhs, st));
+      PhaseScope ps(st, PH_GIVENS, 0.0, 0.0);
+      HZ_TRY(launch_givens(ks, j, nrhs, st));
+      return HZ_OK;
+    };
+    if (p->opts.graphs && jmax == m) {
+      // The whole cycle as one CUDA graph, captured once per plan and right-
+      // hand-side count and replayed; steps after a right-hand side retires
+      // return at once on its device-side flag.
+      // captured on and replayed from the plan's own stream (the legacy
+      // default stream cannot be captured), ordered after / before st
+      if (!w.gstream) HZ_CUDA(cudaStreamCreateWithFlags(&w.gstream, cudaStreamNonBlocking));
+      if (!w.gev[0]) {
+        HZ_CUDA(cudaEventCreateWithFlags(&w.gev[0], cudaEventDisableTiming));
+        HZ_CUDA(cudaEventCreateWithFlags(&w.gev[1], cudaEventDisableTiming));
       }
-      HZ_CUDA(cudaMemcpyAsync(&w.h_nact[j & 1], ks.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
-      HZ_CUDA(cudaEventRecord(w.ev[j & 1], st));
-      if (j >= 1) {
-        HZ_CUDA(cudaEventSynchronize(w.ev[(j - 1) & 1]));
-        if (w.h_nact[(j - 1) & 1] == 0) break;
+      if (!w.cyc_exec || w.cyc_nrhs != nrhs) {
+        if (w.cyc_exec) cudaGraphExecDestroy(w.cyc_exec);
+        w.cyc_exec = nullptr;
+        const unsigned long long l0 = hz_launch_count();
+        HZ_CUDA(cudaStreamBeginCapture(w.gstream, cudaStreamCaptureModeThreadLocal));
+        hz_status cst = HZ_OK;
+        for (int j = 0; j < m && cst == HZ_OK; ++j) cst = step(j, w.gstream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(w.gstream, &graph);
+        const unsigned long long captured = hz_launch_count() - l0;
+        count_launches(-int(captured));  // recorded, not run
+        if (cst != HZ_OK) {
+          if (graph) cudaGraphDestroy(graph);
+          return cst;
+        }
+        HZ_CUDA(ce);
+        const cudaError_t ie = cudaGraphInstantiate(&w.cyc_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        HZ_CUDA(ie);
+        w.cyc_nrhs = nrhs;
+        w.cyc_kernels = int(captured);
+      }
+      HZ_CUDA(cudaEventRecord(w.gev[0], st));
+      HZ_CUDA(cudaStreamWaitEvent(w.gstream, w.gev[0], 0));
+      HZ_CUDA(cudaGraphLaunch(w.cyc_exec, w.gstream));
+      HZ_CUDA(cudaEventRecord(w.gev[1], w.gstream));
+      HZ_CUDA(cudaStreamWaitEvent(st, w.gev[1], 0));
+      count_launches(w.cyc_kernels);
+    } else {
+      for (int j = 0; j < jmax; ++j) {
+        HZ_TRY(step(j, st));
+        HZ_CUDA(cudaMemcpyAsync(&w.h_nact[j & 1], ks.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        HZ_CUDA(cudaEventRecord(w.ev[j & 1], st));
+        if (j >= 1) {
+          HZ_CUDA(cudaEventSynchronize(w.ev[(j - 1) & 1]));
+          if (w.h_nact[(j - 1) & 1] == 0) break;
+        }
       }
     }
     HZ_CUDA(cudaMemcpyAsync(h_jend.data(), ks.jend, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -295,7 +343,7 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
         HZ_TRY(launch_combine(p->V, ldb, t, n, n, nrhs, w.y, m, ks.sigma, B, d_jn, st));
       }
       double2* zt = static_cast<double2*>(p->Z);
-      HZ_TRY(precond_apply(p, 0, t, nullptr, nrhs, zt, 1, st));
+      HZ_TRY(precond_apply(p, 0, t, nullptr, nrhs, zt, 1, st, nullptr));
       PhaseScope ps(st, PH_SOLUPD, Bn * 48.0, Bn * 2.0);
       HZ_TRY(launch_axpy(u, zt, n, n, nrhs, d_jn, st));
     }

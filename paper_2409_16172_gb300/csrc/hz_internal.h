@@ -113,24 +113,25 @@ namespace hz {
 struct FftOps {
   int N;
   // forward FFT along x, c128 input (optionally scaled per rhs)
+  // active (nullable): per-rhs flags; work of retired right-hand sides is skipped
   hz_status (*row_fwd)(int prec, const double2* in, const double* scale, long rows_per_rhs,
-                       long nrows, const void* tw, void* out, cudaStream_t st);
+                       long nrows, const void* tw, void* out, cudaStream_t st, const int* active);
   // inverse FFT along x of the K planes + weighted sum; out_kind 0: c64, 1: c128
   hz_status (*row_inv_acc)(int prec, int out_kind, const void* planes, const void* rec,
                            const uchar2* segtab, int nseg, const unsigned long long* rowmask,
                            int K, long rows_per_rhs, long nrows, long n, double inv_n,
-                           const void* tw, void* out, cudaStream_t st);
+                           const void* tw, void* out, cudaStream_t st, const int* active);
   // FFT along a strided axis, in place; sign -1 forward, +1 inverse
   hz_status (*line_pass)(int prec, int sign, void* data, int nx, long outer, long S,
                          long ostride, long bstride, int batch,
                          const unsigned long long* omask, int K, const void* tw,
-                         cudaStream_t st);
+                         cudaStream_t st, const int* active, int per_rhs);
   // last axis: symbol multiply of the spectrum and inverse FFT, one plane per k
   hz_status (*line_sym_inv)(int prec, const void* vhat, void* planes, int nx, long outer, long S,
                             long ostride, long n, int K, int batch, const void* xi2_x,
                             const void* xi2_o, const void* xi2_l, const void* symA,
                             const void* symG, const unsigned long long* smask, long smO,
-                            long smS, const void* tw, cudaStream_t st);
+                            long smS, const void* tw, cudaStream_t st, const int* active);
 };
 
 const FftOps* fft_ops(int N);

@@ -34,6 +34,10 @@ struct SolveWs {
   int* h_nact = nullptr;      // pinned, 2 slots
   cudaEvent_t ev[2] = {nullptr, nullptr};
   cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaGraphExec_t cyc_exec = nullptr;  // captured Arnoldi cycle (opts.graphs)
+  int cyc_nrhs = 0, cyc_kernels = 0;
+  cudaStream_t gstream = nullptr;      // stream the cycle graph is captured on / replayed from
+  cudaEvent_t gev[2] = {nullptr, nullptr};
 };
 hz_status solve_ws_create(hz_plan* p);
 void solve_ws_destroy(hz_plan* p);

@@ -397,12 +397,12 @@ hz_status launch_dots(const double2* V, long ldb, const double2* w, long wstride
                       int nrhs, const int* active, double2* partial, int /*unused*/, double2* S,
                       int ldS, cudaStream_t st) {
   // balanced chunks of at most VC vectors; one wave of two blocks per SM
-  // (the register budget allows two), at least 16 points per thread
+  // (the register budget allows two)
   int nchunk = (j + 1 + VC - 1) / VC;
   const int vpc = (j + 1 + nchunk - 1) / nchunk;
   nchunk = (j + 1 + vpc - 1) / vpc;  // no empty chunk
   long per = (2L * 152) / (long(nrhs) * nchunk);
-  const long cap = (n + 16L * KT - 1) / (16L * KT);
+  const long cap = (n + KT - 1) / KT;  // at least one point per thread
   if (per > cap) per = cap;
   const int nblk = int(per < 1 ? 1 : per);
   dots_kernel<<<dim3(nblk, nrhs, nchunk), KT, 0, st>>>(V, ldb, w, wstride, n, j, vpc, active, partial);

@@ -84,25 +84,27 @@ extern "C" hz_status hz_apply_preconditioner_noalloc(const hz_medium* med, const
   const void* rec = prec == 0 ? (const void*)med->rec64 : (const void*)med->rec32;
   const long rows = n / nx;
   const long slab = long(nx) * ny;
-  HZ_TRY(ox->row_fwd(prec, static_cast<const double2*>(x), nullptr, rows, rows * nrhs, tw(tx), tmp, st));
-  HZ_TRY(oy->line_pass(prec, -1, tmp, nx, nz, nx, slab, n, nrhs, nullptr, med->K, tw(ty), st));
+  HZ_TRY(ox->row_fwd(prec, static_cast<const double2*>(x), nullptr, rows, rows * nrhs, tw(tx), tmp, st,
+                     nullptr));
+  HZ_TRY(oy->line_pass(prec, -1, tmp, nx, nz, nx, slab, n, nrhs, nullptr, med->K, tw(ty), st, nullptr, 1));
   int launches = 2;
   if (med->dim == 2) {
     HZ_TRY(oy->line_sym_inv(prec, tmp, planes, nx, 1, nx, 0, n, med->K, nrhs, xi(tx), nullptr, xi(ty),
-                            A, G, med->rowmask, 0, 1, tw(ty), st));
+                            A, G, med->rowmask, 0, 1, tw(ty), st, nullptr));
     launches += 1;
   } else {
     const FftOps* oz = fft_ops(nz);
     const AxisTables& tz = med->ax[2];
-    HZ_TRY(oz->line_pass(prec, -1, tmp, nx, ny, slab, nx, n, nrhs, nullptr, med->K, tw(tz), st));
+    HZ_TRY(oz->line_pass(prec, -1, tmp, nx, ny, slab, nx, n, nrhs, nullptr, med->K, tw(tz), st,
+                         nullptr, 1));
     HZ_TRY(oz->line_sym_inv(prec, tmp, planes, nx, ny, slab, nx, n, med->K, nrhs, xi(tx), xi(ty),
-                            xi(tz), A, G, med->slabmask, 0, 1, tw(tz), st));
+                            xi(tz), A, G, med->slabmask, 0, 1, tw(tz), st, nullptr));
     HZ_TRY(oy->line_pass(prec, +1, planes, nx, nz, nx, slab, n, nrhs * med->K, med->slabmask, med->K,
-                         tw(ty), st));
+                         tw(ty), st, nullptr, med->K));
     launches += 3;
   }
   HZ_TRY(ox->row_inv_acc(prec, 1, planes, rec, med->segtab, med->nseg, med->rowmask, med->K, rows,
-                         rows * nrhs, n, 1.0 / double(n), tw(tx), y, st));
+                         rows * nrhs, n, 1.0 / double(n), tw(tx), y, st, nullptr));
   count_launches(launches + 1);
   return HZ_OK;
 }

@@ -67,13 +67,20 @@ __global__ void fma_probe_kernel(double* out, double a, double b, int iters) {
 
 }  // namespace
 
-void count_launches(int k) { g_launches.fetch_add(unsigned(k), std::memory_order_relaxed); }
+void count_launches(int k) {
+  g_launches.fetch_add((unsigned long long)(long long)k, std::memory_order_relaxed);
+}
 bool profiling() { return g_on.load(std::memory_order_relaxed); }
 
 PhaseScope::PhaseScope(cudaStream_t s, Phase p, double b, double f, int l)
     : st(s), ph(p), bytes(b), flops(f), launches(l) {
   count_launches(l);
   if (!profiling()) return;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;  // no timing inside a graph capture
+  }
   std::lock_guard<std::mutex> lk(g_mu);
   if (g_free_slots.empty() && g_pend.size() >= 4096) resolve_locked();
   if (g_free_slots.empty()) {

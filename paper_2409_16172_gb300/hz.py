@@ -46,7 +46,7 @@ class hz_interp(C.Structure):
 
 class hz_solver_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("restart", C.c_int), ("tol", C.c_double),
-                ("maxit", C.c_int)]
+                ("maxit", C.c_int), ("graphs", C.c_int)]
 
 
 class hz_solve_stats(C.Structure):
@@ -243,10 +243,10 @@ class Plan:
     """Workspace for applying and solving on one medium."""
 
     def __init__(self, medium: Medium, *, precision: int = 1, restart: int = 40,
-                 tol: float = 1e-6, maxit: int = 4000, max_nrhs: int = 1):
+                 tol: float = 1e-6, maxit: int = 4000, max_nrhs: int = 1, graphs: bool = False):
         self.medium = medium
         self.max_nrhs = max_nrhs
-        self.opts = hz_solver_opts(precision, restart, tol, maxit)
+        self.opts = hz_solver_opts(precision, restart, tol, maxit, 1 if graphs else 0)
         h = _vp()
         check(lib.hz_plan_create(medium.handle, C.byref(self.opts), max_nrhs, C.byref(h)))
         self._h = h
@@ -324,7 +324,7 @@ def _grid_of(shape, L=1.0):
 def request_footprint(shape, M, Mt, precision=1, restart=40, nrhs=1, has_a=False) -> int:
     g = _grid_of(tuple(shape))
     it = hz_interp(M, Mt, 1.0, 0.0, 0.15, 0.0, 0)
-    o = hz_solver_opts(precision, restart, 1e-6, 4000)
+    o = hz_solver_opts(precision, restart, 1e-6, 4000, 0)
     return int(lib.hz_request_footprint(C.byref(g), C.byref(it), C.byref(o), nrhs, 1 if has_a else 0))
 
 
@@ -342,7 +342,7 @@ class Server:
     def submit(self, c, f, *, omega: float, M: int, Mt: int = 0, zeta=None, a=None,
                c_o: float = 1.0, zeta_max: float = 0.0, alpha: float = 0.15, a_node: float = 0.0,
                symbol_kind: int = 0, precision: int = 1, restart: int = 40, tol: float = 1e-6,
-               maxit: int = 4000, L: float = 1.0) -> int:
+               maxit: int = 4000, L: float = 1.0, graphs: bool = False) -> int:
         c = np.ascontiguousarray(c, dtype=np.float64)
         shape = c.shape
         f = np.ascontiguousarray(f, dtype=np.complex128)
@@ -356,7 +356,7 @@ class Server:
         r.a = _dptr(a)
         r.omega = omega
         r.interp = hz_interp(M, Mt, c_o, zeta_max, alpha, a_node, symbol_kind)
-        r.opts = hz_solver_opts(precision, restart, tol, maxit)
+        r.opts = hz_solver_opts(precision, restart, tol, maxit, 1 if graphs else 0)
         r.nrhs = nrhs
         r.f = _vp(f.ctypes.data)
         t = C.c_uint64()

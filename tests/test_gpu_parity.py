@@ -172,3 +172,35 @@ def test_edge_cases(hz):
     assert e.value.status == 1
     with pytest.raises(hz.HzError):
         plan.apply_operator(_dev(np.zeros((2, 16, 16), complex)))  # nrhs > max_nrhs
+
+
+def test_graph_replay_matches_stepwise(hz):
+    """The captured-cycle mode (opts.graphs) launches the same kernels in the
+    same order: identical iterates and counts, also for several right-hand
+    sides that retire at different steps."""
+    p = S.bump_problem(64, 41, width=8, ppw=8.0, M=4, Mt=2, nrhs=3)
+    med_g, _ = media(hz, p, oracle=False)
+    out = []
+    for graphs in (False, True):
+        plan = hz.Plan(med_g, precision=1, restart=15, tol=1e-7, maxit=3000, max_nrhs=3,
+                       graphs=graphs)
+        u, st = plan.solve(np.ascontiguousarray(p.f))
+        out.append((u, [s["iters"] for s in st], [s["converged"] for s in st]))
+        u, st = plan.solve(np.ascontiguousarray(p.f))  # replay of the captured graph
+        assert np.array_equal(u, out[-1][0])
+    assert out[0][1] == out[1][1] and all(out[1][2])
+    assert np.array_equal(out[0][0], out[1][0])
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (16, 48, 24)])
+def test_gmres_3d_matches_oracle(hz, shape):
+    p = S.small_problem(shape, 42, M=5, Mt=2, width=3)
+    med_g, med_o = media(hz, p)
+    plan = hz.Plan(med_g, precision=1, restart=20, tol=1e-8, maxit=3000)
+    u, st = plan.solve(_dev(p.f[0]))
+    u = u.cpu().numpy()
+    r = rel(O.apply_operator(med_o, u), p.f[0])
+    assert st[0]["converged"] and r <= 1e-8, (st, r)
+    uo, sto = O.gmres(lambda x: O.apply_operator(med_o, x), p.f[0],
+                      lambda v: O.apply_preconditioner(med_o, v), restart=20, tol=1e-8)
+    assert abs(st[0]["iters"] - sto["iters"]) <= 3, (st[0]["iters"], sto["iters"])

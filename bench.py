@@ -226,6 +226,7 @@ def run_gpu(args, p, name):
     med = hz.Medium(p.c, p.zeta, omega=p.omega, M=p.M, Mt=p.Mt, c_o=p.c_o, alpha=alpha)
     plan = hz.Plan(med, precision=p.precision, restart=p.restart, tol=p.tol, maxit=4000,
                    max_nrhs=nrhs, graphs=graphs)
+    tune = plan.autotune() if not args.no_autotune else None
     f = torch.from_numpy(np.ascontiguousarray(p.f)).cuda()
     u = torch.zeros_like(f)
     stream = torch.cuda.current_stream()
@@ -269,6 +270,8 @@ def run_gpu(args, p, name):
     if graphs:
         plan_p = hz.Plan(med, precision=p.precision, restart=p.restart, tol=p.tol, maxit=4000,
                          max_nrhs=nrhs, graphs=False)
+        if tune is not None:
+            plan_p.autotune()  # cached: same shapes as the timed plan
     hz.profile_enable(True)
     hz.profile_read(reset=True)
     for _ in range(max(1, min(args.steps, 3))):
@@ -362,7 +365,7 @@ def run_gpu(args, p, name):
            "cpu_baseline": cpu,
            "e2e": {"value": e2e_val, "unit": "solves/s",
                    "h2d_bytes_per_step": 2 * 16 * n * nrhs, "d2h_bytes_per_step": 16 * n * nrhs},
-           "gpu_launches": launches, "clocks": clocks, "phases": phases,
+           "gpu_launches": launches, "clocks": clocks, "phases": phases, "autotune": tune,
            "fp64_peak_tflops": fp64_peak, "fp64_probe_tflops": fp64_probe / 1e3}
     print(json.dumps(out), flush=True)
 
@@ -426,6 +429,7 @@ def main():
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent requests")
     ap.add_argument("--cpu-iters", type=int, default=6, help="Arnoldi steps in the CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--ref-sample", type=int, default=3, help="reference arm: steps per sample")
     ap.add_argument("--ref-iters", type=int, default=0,
                     help="reference arm: Arnoldi steps per solve (0: count them with one full "

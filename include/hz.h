@@ -150,6 +150,24 @@ hz_status hz_destroy_medium(hz_medium* med);
 hz_status hz_plan_create(hz_medium* med, const hz_solver_opts* opts, int max_nrhs,
                          hz_plan** out);
 
+/* Autotuner (the paper has no counterpart; it tunes this implementation's
+ * launch shapes).  Times candidate launch shapes of the kernels that dominate
+ * a solve on the plan's own buffers with CUDA events on `stream`: blocks per
+ * SM and vectors per block of the CGS2 dot kernel, blocks per SM of the CGS2
+ * update, nodes per block of the last-axis symbol pass.  The choice is stored
+ * in the plan and cached per (grid, K, max_nrhs, restart, precision) for the
+ * process; later plans with the same key reuse it without timing.
+ * Synchronous; overwrites the plan's work arrays (call before solving). */
+typedef struct {
+  int dots_bps, dots_vc, upd_bps, syminv_kpb;
+  int cached;               /* 1: taken from the process cache, no timing  */
+  float dots_us, dots_us_default;     /* chosen vs default shape           */
+  float upd_us, upd_us_default;
+  float apply_us, apply_us_default;   /* whole preconditioner apply        */
+} hz_tune_report;
+
+hz_status hz_plan_autotune(hz_plan* plan, void* stream, hz_tune_report* report);
+
 /* Bytes of device memory the plan holds. */
 hz_status hz_plan_bytes(const hz_plan* plan, size_t* bytes);
 

@@ -33,7 +33,7 @@ def nvcc() -> str:
 def _units():
     units = []
     for name in ("api.cu", "gmres.cu", "medium.cu", "stencil.cu", "krylov.cu", "profile.cu",
-                 "noalloc.cu", "server.cu"):
+                 "noalloc.cu", "server.cu", "tune.cu"):
         units.append((os.path.join(CSRC, name), os.path.join(OUT, name.replace(".cu", ".o")), []))
     for n in FFT_SIZES:
         units.append((os.path.join(CSRC, "fft_inst.cu"), os.path.join(OUT, f"fft_{n}.o"),

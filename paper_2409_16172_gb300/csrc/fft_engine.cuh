@@ -222,8 +222,13 @@ struct LineFFT {
   static constexpr int R0 = P::rad(0);
   static_assert(!WS || TPL <= 32, "warp-synchronous lines need TPL <= 32");
 
+  // lanes of the warp that exist: a block smaller than a warp holds lanes
+  // 0 .. blockDim.x - 1 only
+  __device__ static __forceinline__ unsigned lane_mask() {
+    return blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
+  }
   __device__ static __forceinline__ void sync() {
-    if constexpr (WS) __syncwarp();
+    if constexpr (WS) __syncwarp(lane_mask());
     else __syncthreads();
   }
 

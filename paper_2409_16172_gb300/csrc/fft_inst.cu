@@ -25,10 +25,14 @@ hz_status row_fwd_t(const double2* in, const double* scale, long rows_per_rhs, l
                     const void* tw, void* out, cudaStream_t st, const int* active) {
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
-  auto k = row_fwd_kernel<R, N>;
-  HZ_TRY(smem_attr(k, C::row_smem()));
-  const long blocks = (nrows + C::ROW_LINES - 1) / C::ROW_LINES;
-  k<<<unsigned(blocks), C::ROW_THREADS, C::row_smem(), st>>>(
+  // blocks of ROW_LINES lines, or one warp per block when that leaves the
+  // GPU under-filled (small grids)
+  const bool small = (nrows + C::ROW_LINES - 1) / C::ROW_LINES < 2L * 152;
+  const int lines = small ? C::ROW_LINES_SMALL : C::ROW_LINES;
+  auto k = small ? row_fwd_kernel<R, N, C::ROW_LINES_SMALL> : row_fwd_kernel<R, N, C::ROW_LINES>;
+  HZ_TRY(smem_attr(k, C::row_smem(lines)));
+  const long blocks = (nrows + lines - 1) / lines;
+  k<<<unsigned(blocks), lines * C::TPL_ROW, C::row_smem(lines), st>>>(
       in, scale, rows_per_rhs, nrows, static_cast<const V*>(tw), static_cast<V*>(out), active);
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
@@ -47,10 +51,13 @@ hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segta
                         const int* active) {
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
-  auto k = row_inv_acc_kernel<R, N, OutT>;
-  HZ_TRY(smem_attr(k, C::row_acc_smem()));
-  const long blocks = (nrows + C::ROW_LINES - 1) / C::ROW_LINES;
-  k<<<unsigned(blocks), C::ROW_THREADS, C::row_acc_smem(), st>>>(
+  const bool small = (nrows + C::ROW_LINES - 1) / C::ROW_LINES < 2L * 152;
+  const int lines = small ? C::ROW_LINES_SMALL : C::ROW_LINES;
+  auto k = small ? row_inv_acc_kernel<R, N, OutT, C::ROW_LINES_SMALL>
+                 : row_inv_acc_kernel<R, N, OutT, C::ROW_LINES>;
+  HZ_TRY(smem_attr(k, C::row_acc_smem(lines)));
+  const long blocks = (nrows + lines - 1) / lines;
+  k<<<unsigned(blocks), lines * C::TPL_ROW, C::row_acc_smem(lines), st>>>(
       static_cast<const V*>(planes), static_cast<const typename RecT<R>::T*>(rec), segtab, nseg,
       rowmask, K, rows_per_rhs, nrows, n, R(inv_n), static_cast<const V*>(tw),
       static_cast<OutT*>(out), active);
@@ -104,18 +111,19 @@ hz_status line_sym_inv_t(const void* vhat, void* planes, int nx, long outer, lon
                          long n, int K, int batch, const void* xi2_x, const void* xi2_o,
                          const void* xi2_l, const void* symA, const void* symG,
                          const unsigned long long* smask, long smO, long smS, const void* tw,
-                         cudaStream_t st, const int* active) {
+                         cudaStream_t st, const int* active, int kpb) {
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
   auto k = line_sym_inv_kernel<R, N>;
   HZ_TRY(smem_attr(k, C::col_smem()));
   const int ntile = (nx + C::TB - 1) / C::TB;
-  dim3 grid(unsigned(ntile * outer), unsigned(K), unsigned(batch));
+  if (kpb < 1) kpb = 1;
+  dim3 grid(unsigned(ntile * outer), unsigned((K + kpb - 1) / kpb), unsigned(batch));
   k<<<grid, C::COL_THREADS, C::col_smem(), st>>>(
       static_cast<const V*>(vhat), static_cast<V*>(planes), nx, ntile, S, ostride, n, K,
       static_cast<const R*>(xi2_x), static_cast<const R*>(xi2_o), static_cast<const R*>(xi2_l),
       static_cast<const V*>(symA), static_cast<const V*>(symG), smask, smO, smS,
-      static_cast<const V*>(tw), active);
+      static_cast<const V*>(tw), active, kpb);
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
@@ -124,12 +132,12 @@ hz_status line_sym_inv(int prec, const void* vhat, void* planes, int nx, long ou
                        long ostride, long n, int K, int batch, const void* xi2_x,
                        const void* xi2_o, const void* xi2_l, const void* symA, const void* symG,
                        const unsigned long long* smask, long smO, long smS, const void* tw,
-                       cudaStream_t st, const int* active) {
+                       cudaStream_t st, const int* active, int kpb) {
   return prec == 0
              ? line_sym_inv_t<double>(vhat, planes, nx, outer, S, ostride, n, K, batch, xi2_x,
-                                      xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, st, active)
+                                      xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, st, active, kpb)
              : line_sym_inv_t<float>(vhat, planes, nx, outer, S, ostride, n, K, batch, xi2_x,
-                                     xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, st, active);
+                                     xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, st, active, kpb);
 }
 
 const FftOps ops = {N, row_fwd, row_inv_acc, line_pass, line_sym_inv};

@@ -45,11 +45,16 @@ template <typename R, int N> struct LineCfg {
   }
   static constexpr int TB = tb_calc();
   static constexpr int COL_THREADS = TB * TPL;
-  static constexpr size_t row_smem() { return size_t(ROW_LINES) * padded_len(N) * VB; }
+  // one line per block (TPL_ROW threads, possibly less than a warp) when
+  // there are too few rows to fill the GPU with ROW_LINES-line blocks
+  static constexpr int ROW_LINES_SMALL = 1;
+  static constexpr size_t row_smem(int lines = ROW_LINES) { return size_t(lines) * padded_len(N) * VB; }
   // row_inv_acc: padded work lines, then (16-byte aligned for cp.async) two
   // unpadded staging rows per line
-  static constexpr size_t stage_offset() { return (row_smem() + 15) / 16 * 16; }
-  static constexpr size_t row_acc_smem() { return stage_offset() + size_t(ROW_LINES) * 2 * N * VB; }
+  static constexpr size_t stage_offset(int lines = ROW_LINES) { return (row_smem(lines) + 15) / 16 * 16; }
+  static constexpr size_t row_acc_smem(int lines = ROW_LINES) {
+    return stage_offset(lines) + size_t(lines) * 2 * N * VB;
+  }
   static constexpr size_t col_smem() { return size_t(TB) * padded_len(N) * VB; }
 };
 
@@ -81,14 +86,14 @@ template <> struct RecT<double> { using T = double; };
 // Forward FFT along x.  in: c128 rows (row gr at gr * N); scale[rhs] (or
 // NULL) multiplies the input; out: working-precision rows.
 // ---------------------------------------------------------------------------
-template <typename R, int N>
-__global__ void __launch_bounds__(LineCfg<R, N>::ROW_THREADS)
+template <typename R, int N, int LPB>
+__global__ void __launch_bounds__(LPB * LineCfg<R, N>::TPL_ROW)
 row_fwd_kernel(const double2* __restrict__ in, const double* __restrict__ scale,
                long rows_per_rhs, long nrows, const typename cvec<R>::T* __restrict__ tw,
                typename cvec<R>::T* __restrict__ out, const int* __restrict__ active) {
   using V = typename cvec<R>::T;
   using F = LineFFT<R, N, -1, 1, LineCfg<R, N>::WS, typename LineCfg<R, N>::RP>;
-  constexpr int TPL = F::TPL, E = F::E, LPB = LineCfg<R, N>::ROW_LINES;
+  constexpr int TPL = F::TPL, E = F::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
   const int li = threadIdx.x / TPL, t = threadIdx.x % TPL;
@@ -123,8 +128,8 @@ row_fwd_kernel(const double2* __restrict__ in, const double* __restrict__ scale,
 // rows need; the next plane's rows are copied into a shared staging buffer
 // with cp.async while the current plane is transformed.
 // ---------------------------------------------------------------------------
-template <typename R, int N, typename OutT>
-__global__ void __launch_bounds__(LineCfg<R, N>::ROW_THREADS)
+template <typename R, int N, typename OutT, int LPB>
+__global__ void __launch_bounds__(LPB * LineCfg<R, N>::TPL_ROW)
 row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
                    const typename RecT<R>::T* __restrict__ rec, const uchar2* __restrict__ segtab,
                    int nseg, const unsigned long long* __restrict__ rowmask, int K,
@@ -134,7 +139,7 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
   using V = typename cvec<R>::T;
   constexpr bool WS = LineCfg<R, N>::WS;
   using F = LineFFT<R, N, +1, 1, WS, typename LineCfg<R, N>::RP>;
-  constexpr int TPL = F::TPL, E = F::E, LPB = LineCfg<R, N>::ROW_LINES;
+  constexpr int TPL = F::TPL, E = F::E;
   constexpr int CH = N * int(sizeof(V)) / 16;  // 16-byte chunks per row
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
@@ -152,7 +157,7 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
   if (t == 0 && mymask) atomicOr(&cta_mask, mymask);
   V* line = sm + li * padded_len(N);
   // two staging rows of this line; cp.async needs 16-byte aligned destinations
-  V* stg = reinterpret_cast<V*>(smem_raw + LineCfg<R, N>::stage_offset()) + li * 2 * N;
+  V* stg = reinterpret_cast<V*>(smem_raw + LineCfg<R, N>::stage_offset(LPB)) + li * 2 * N;
   typename RecT<R>::T r_[E];
   V acc[E];
 #pragma unroll
@@ -165,8 +170,9 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
   // warp-synchronous lines only those the lines of this warp need
   unsigned long long cm = cta_mask;
   if constexpr (WS) {
-    const unsigned lo = __reduce_or_sync(0xffffffffu, unsigned(mymask & 0xFFFFFFFFull));
-    const unsigned hi = __reduce_or_sync(0xffffffffu, unsigned(mymask >> 32));
+    const unsigned lm = F::lane_mask();
+    const unsigned lo = __reduce_or_sync(lm, unsigned(mymask & 0xFFFFFFFFull));
+    const unsigned hi = __reduce_or_sync(lm, unsigned(mymask >> 32));
     cm = (unsigned long long)lo | ((unsigned long long)hi << 32);
   }
   const V* pbase = planes + (rhs * K) * n + lrow * N;
@@ -271,9 +277,10 @@ line_pass_kernel(typename cvec<R>::T* __restrict__ data, int nx, int ntile, long
   }
 }
 
-// Last axis, one block per (column tile and outer index, node k, rhs): the
-// spectrum vhat (transformed along every axis) times q_k, inverse FFT along
-// the axis, written to plane k.  |xi|^2 = xi2_x[x] + xi2_o[o] + xi2_l[p].
+// Last axis, one block per (column tile and outer index, group of kpb nodes,
+// rhs): the spectrum vhat (transformed along every axis) times q_k, inverse
+// FFT along the axis, written to plane k, for each node of the group (the
+// spectrum is read once per block).  |xi|^2 = xi2_x[x] + xi2_o[o] + xi2_l[p].
 // Plane k is only stored where smask[o smO + p smS] has bit k: per row in 2D
 // (the next pass is the x inverse), per z-slab in 3D (the next pass is the y
 // inverse, which needs the whole slab).
@@ -286,43 +293,53 @@ line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
                     const typename cvec<R>::T* __restrict__ symA,
                     const typename cvec<R>::T* __restrict__ symG,
                     const unsigned long long* __restrict__ smask, long smO, long smS,
-                    const typename cvec<R>::T* __restrict__ tw, const int* __restrict__ active) {
+                    const typename cvec<R>::T* __restrict__ tw, const int* __restrict__ active,
+                    int kpb) {
   using V = typename cvec<R>::T;
   constexpr int TB = LineCfg<R, N>::TB;
   using F = LineFFT<R, N, +1, TB>;
-  if (active && !active[blockIdx.z]) return;
   constexpr int TPL = F::TPL, E = F::E;
+  if (active && !active[blockIdx.z]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
   const int col = threadIdx.x % TB, t = threadIdx.x / TB;
   const int tile = blockIdx.x % ntile;
   const long o = blockIdx.x / ntile;
-  const int k = blockIdx.y;
+  const int k0 = blockIdx.y * kpb;
+  const int k1 = min(K, k0 + kpb);
   const long rhs = blockIdx.z;
   const int x = tile * TB + col;
   const bool valid = x < nx;
   const long off = o * ostride + x;
   const V* src = vhat + rhs * n + off;
-  const V A = symA[k], G = symG[k];
   const R sxo = (valid ? xi2_x[x] : R(0)) + (xi2_o ? xi2_o[o] : R(0));
-  V v[E];
+  V spec[E];
+  R s2[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int p = F::stage0_index(t, e);
-    const V sv = valid ? src[long(p) * S] : cmk<V>(R(0), R(0));
-    const R s2 = sxo + xi2_l[p];
-    // q = 1 / (A - G s) = conj(den) / |den|^2
-    const V den = cmk<V>(A.x - G.x * s2, A.y - G.y * s2);
-    const R inv = R(1) / (den.x * den.x + den.y * den.y);
-    v[e] = cmul(sv, cmk<V>(den.x * inv, -den.y * inv));
+    spec[e] = valid ? src[long(p) * S] : cmk<V>(R(0), R(0));
+    s2[e] = sxo + xi2_l[p];
   }
-  F::run(sm + col, t, v, tw);
-  if (valid) {
-    V* dst = planes + (rhs * K + k) * n + off;
+  for (int k = k0; k < k1; ++k) {
+    const V A = symA[k], G = symG[k];
+    V v[E];
 #pragma unroll
-    for (int i = 0; i < E; ++i) {
-      const int p = t + i * TPL;
-      if ((smask[o * smO + long(p) * smS] >> k) & 1ull) dst[long(p) * S] = sm[padded(p) * TB + col];
+    for (int e = 0; e < E; ++e) {
+      // q = 1 / (A - G s) = conj(den) / |den|^2
+      const V den = cmk<V>(A.x - G.x * s2[e], A.y - G.y * s2[e]);
+      const R inv = R(1) / (den.x * den.x + den.y * den.y);
+      v[e] = cmul(spec[e], cmk<V>(den.x * inv, -den.y * inv));
+    }
+    if (k > k0) __syncthreads();  // the previous node's results have been stored
+    F::run(sm + col, t, v, tw);
+    if (valid) {
+      V* dst = planes + (rhs * K + k) * n + off;
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int p = t + i * TPL;
+        if ((smask[o * smO + long(p) * smS] >> k) & 1ull) dst[long(p) * S] = sm[padded(p) * TB + col];
+      }
     }
   }
 }

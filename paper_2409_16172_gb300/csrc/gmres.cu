@@ -131,7 +131,6 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
   if (!u_dev) HZ_CUDA(cudaMemcpyAsync(p->u, u_io, vbytes, cudaMemcpyHostToDevice, st));
 
   const int nblk_r = stencil_blocks(n);
-  const int nblk_k = krylov_blocks(n, nrhs, (m + 1 + 7) / 8);
   const int nblk_n = krylov_blocks(n, nrhs, 1);
   const double Bn = double(nrhs) * n;
   {
@@ -232,11 +231,11 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
         {
           PhaseScope ps(st, PH_DOTS, db, fl, 2);
           HZ_TRY(launch_dots(p->V, ldb, Vn, n, n, j, nrhs, ks.active,
-                             reinterpret_cast<double2*>(p->partial), nblk_k, S, m + 1, st));
+                             reinterpret_cast<double2*>(p->partial), p->tune, S, m + 1, st));
         }
         PhaseScope ps(st, PH_UPDATE, ub, fl + (pass ? 4.0 * Bn : 0.0), pass ? 2 : 1);
         HZ_TRY(launch_update(p->V, ldb, Vn, n, n, j, nrhs, S, m + 1, ks.sigma, B, ks.active, pass == 1,
-                             p->partial, nblk_k, ks.nrm2, st));
+                             p->partial, p->tune, ks.nrm2, st));
       }
       PhaseScope ps(st, PH_GIVENS, 0.0, 0.0);
       HZ_TRY(launch_givens(ks, j, nrhs, st));

@@ -131,7 +131,8 @@ struct FftOps {
                             long ostride, long n, int K, int batch, const void* xi2_x,
                             const void* xi2_o, const void* xi2_l, const void* symA,
                             const void* symG, const unsigned long long* smask, long smO,
-                            long smS, const void* tw, cudaStream_t st, const int* active);
+                            long smS, const void* tw, cudaStream_t st, const int* active,
+                            int kpb);
 };
 
 const FftOps* fft_ops(int N);
@@ -158,6 +159,16 @@ struct PhaseScope {
 
 namespace hz {
 struct SolveWs;
+
+// Launch shapes the autotuner chooses per plan (defaults are the untuned
+// choice): blocks per SM of the CGS2 dot and update kernels, basis vectors
+// per dot block, and nodes per block of the last-axis symbol pass.
+struct Tune {
+  int dots_bps = 2;
+  int dots_vc = 8;
+  int upd_bps = 4;
+  int syminv_kpb = 1;
+};
 }
 
 struct hz_plan {
@@ -177,4 +188,5 @@ struct hz_plan {
   double* partial = nullptr;     // block partial sums
   size_t partial_len = 0;
   hz::SolveWs* ws = nullptr;     // small Krylov state, created by the first solve
+  hz::Tune tune;                 // launch shapes (hz_plan_autotune)
 };

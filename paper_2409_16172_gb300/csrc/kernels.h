@@ -52,11 +52,11 @@ hz_status launch_residual(const hz_medium* m, const double2* u, const double2* f
 
 int krylov_blocks(long n, int nrhs, int nchunk);
 hz_status launch_dots(const double2* V, long ldb, const double2* w, long wstride, long n, int j,
-                      int nrhs, const int* active, double2* partial, int nblk, double2* S, int ldS,
-                      cudaStream_t st);
+                      int nrhs, const int* active, double2* partial, const Tune& tn, double2* S,
+                      int ldS, cudaStream_t st);
 hz_status launch_update(const double2* V, long ldb, double2* w, long wstride, long n, int j,
                         int nrhs, const double2* S, int ldS, const double* sigma, int ldsig,
-                        const int* active, bool norm, double* partial, int nblk, double* nrm2,
+                        const int* active, bool norm, double* partial, const Tune& tn, double* nrm2,
                         cudaStream_t st);
 hz_status launch_givens(const KsDev& ks, int j, int nrhs, cudaStream_t st);
 hz_status launch_solution_update(int zprec, const void* Z, long ldb, double2* u, long ustride,

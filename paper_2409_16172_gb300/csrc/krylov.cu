@@ -18,7 +18,7 @@ namespace hz {
 namespace {
 
 constexpr int KT = 256;   // threads per block
-constexpr int VC = 8;     // basis vectors per dots block
+constexpr int VCMAX = 8;  // basis vectors per dots block (at most)
 
 // fixed-order block sum of NV doubles per thread; result in sh[0..NV-1]
 template <int NV>
@@ -47,16 +47,26 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
 // nv = min(vpc, j + 1 - i0).  grid = (nblk, nrhs, nchunk).  partial layout
 // [(b * (j+1) + i) * nblk + blk] as double2.  The next point's operands are
 // loaded before the current point's FMAs so that the FP64 pipe, the limit
-// here, does not wait on memory; only the nv live accumulators are reduced.
-__global__ void __launch_bounds__(KT, 2)
+// here, does not wait on memory.  With VC <= 4 every product has its own
+// accumulator (re*re, im*im, re*im, im*re), so that no FMA waits on another
+// FMA of the same point; with VC = 8 (register budget) two per vector.  Only
+// the nv live sums are reduced.
+template <int VC> struct DotsCfg {
+  static constexpr int NA = VC <= 4 ? 4 : 2;  // accumulators per vector
+  static constexpr int MINB = VC <= 2 ? 4 : (VC <= 4 ? 3 : 2);
+};
+
+template <int VC>
+__global__ void __launch_bounds__(KT, DotsCfg<VC>::MINB)
 dots_kernel(const double2* __restrict__ V, long ldb, const double2* __restrict__ w, long wstride,
             long n, int j, int vpc, const int* __restrict__ active, double2* __restrict__ partial) {
+  constexpr int NA = DotsCfg<VC>::NA;
   const int b = blockIdx.y;
   const int i0 = blockIdx.z * vpc;
   const int nv = min(vpc, j + 1 - i0);
-  double acc[2 * VC];
+  double acc[NA * VC];
 #pragma unroll
-  for (int c = 0; c < 2 * VC; ++c) acc[c] = 0.0;
+  for (int c = 0; c < NA * VC; ++c) acc[c] = 0.0;
   const bool on = active[b] != 0;
   if (on) {
     const double2* wb = w + b * wstride;
@@ -83,14 +93,33 @@ dots_kernel(const double2* __restrict__ V, long ldb, const double2* __restrict__
 #pragma unroll
       for (int c = 0; c < VC; ++c) {
         if (c < nv) {
-          acc[2 * c] = fma(v[c].x, x.x, fma(v[c].y, x.y, acc[2 * c]));
-          acc[2 * c + 1] = fma(v[c].x, x.y, fma(-v[c].y, x.x, acc[2 * c + 1]));
+          if constexpr (NA == 4) {
+            acc[4 * c] = fma(v[c].x, x.x, acc[4 * c]);
+            acc[4 * c + 1] = fma(v[c].y, x.y, acc[4 * c + 1]);
+            acc[4 * c + 2] = fma(v[c].x, x.y, acc[4 * c + 2]);
+            acc[4 * c + 3] = fma(v[c].y, x.x, acc[4 * c + 3]);
+          } else {
+            acc[2 * c] = fma(v[c].x, x.x, fma(v[c].y, x.y, acc[2 * c]));
+            acc[2 * c + 1] = fma(v[c].x, x.y, fma(-v[c].y, x.x, acc[2 * c + 1]));
+          }
         }
       }
       p = q;
       x = xn;
 #pragma unroll
       for (int c = 0; c < VC; ++c) v[c] = vn[c];
+    }
+  }
+  // conj(v) x = (re re + im im) + i (re im - im re)
+  double sum[2 * VC];
+#pragma unroll
+  for (int c = 0; c < VC; ++c) {
+    if constexpr (NA == 4) {
+      sum[2 * c] = acc[4 * c] + acc[4 * c + 1];
+      sum[2 * c + 1] = acc[4 * c + 2] - acc[4 * c + 3];
+    } else {
+      sum[2 * c] = acc[2 * c];
+      sum[2 * c + 1] = acc[2 * c + 1];
     }
   }
   // block reduction of the 2 nv live sums (warp shuffles, then one value per warp)
@@ -100,8 +129,8 @@ dots_kernel(const double2* __restrict__ V, long ldb, const double2* __restrict__
   for (int c = 0; c < 2 * VC; ++c) {
     if (c < 2 * nv) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
-      if (lane == 0) sh[warp * 2 * VC + c] = acc[c];
+      for (int o = 16; o > 0; o >>= 1) sum[c] += __shfl_down_sync(0xffffffffu, sum[c], o);
+      if (lane == 0) sh[warp * 2 * VC + c] = sum[c];
     }
   }
   __syncthreads();
@@ -208,18 +237,27 @@ __device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 conj_d(double2 a) { return make_double2(a.x, -a.y); }
 
-// One warp per right-hand side: form column j of the Hessenberg matrix in
-// shared memory, apply the earlier rotations (serial, lane 0), build the new
-// one (c real, G [a;b] = [r;0]), update g and the residual estimate, and
-// retire converged / broken rows.
+__device__ __forceinline__ double2 cfma_d(double2 a, double2 b, double2 c) {  // a b + c
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 shfl_up_d2(double2 v, int o) {
+  return make_double2(__shfl_up_sync(0xffffffffu, v.x, o), __shfl_up_sync(0xffffffffu, v.y, o));
+}
+
+// One warp per right-hand side: form column j of the Hessenberg matrix,
+// apply the earlier rotations, build the new one (c real, G [a;b] = [r;0]),
+// update g and the residual estimate, and retire converged / broken rows.
+// Applying rotations 0..j-1 is a linear recurrence on the running entry,
+//   x_0 = h_0,  x_{i+1} = -conj(s_i) x_i + c_i h_{i+1},  r_i = c_i x_i + s_i h_{i+1},
+// evaluated as a warp scan of affine maps (each lane composes a contiguous
+// chunk, a shuffle scan composes the chunks) instead of j serial steps.
 __global__ void givens_kernel(KsDev ks, int j, int nrhs) {
   const int b = blockIdx.x;
   const int lane = threadIdx.x;
   if (b >= nrhs || !ks.active[b]) return;
   const int m = ks.m;
-  __shared__ double2 col[HZ_MAX_RESTART + 2];
-  __shared__ double2 sn_s[HZ_MAX_RESTART];
-  __shared__ double cs_s[HZ_MAX_RESTART];
+  __shared__ double2 col[HZ_MAX_RESTART + 2];   // h, the new column before rotation
+  __shared__ double2 rcol[HZ_MAX_RESTART + 2];  // rotated column
   double2* colg = ks.H + (long(b) * m + j) * (m + 1);
   const double2* S1 = ks.S1 + long(b) * (m + 1);
   const double2* S2 = ks.S2 + long(b) * (m + 1);
@@ -235,28 +273,50 @@ __global__ void givens_kernel(KsDev ks, int j, int nrhs) {
     hmax = fmax(hmax, fmax(fabs(h.x), fabs(h.y)));
     bad |= !isfinite(h.x) || !isfinite(h.y);
   }
-  for (int i = lane; i < j; i += 32) {
-    cs_s[i] = cs[i];
-    sn_s[i] = sn[i];
-  }
+  const double hn = sqrt(ks.nrm2[b]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) hmax = fmax(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
-  bad = __any_sync(0xffffffffu, bad);
+  bad = __any_sync(0xffffffffu, bad) || !isfinite(hn);
+  __syncwarp();
+  // chunk of maps i in [i0, i1) of this lane; composite F(x) = A x + B
+  const int per = (j + 31) / 32;
+  const int i0 = min(j, lane * per), i1 = min(j, i0 + per);
+  double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);
+  for (int i = i0; i < i1; ++i) {
+    const double2 al = make_double2(-sn[i].x, sn[i].y);  // -conj(s_i)
+    const double c = cs[i];
+    const double2 be = make_double2(c * col[i + 1].x, c * col[i + 1].y);
+    A = cmul_d(al, A);
+    B = cfma_d(al, B, be);
+  }
+  // inclusive scan over lanes: G_l = F_l o F_{l-1} o ... o F_0
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double2 Ap = shfl_up_d2(A, o), Bp = shfl_up_d2(B, o);
+    if (lane >= o) {
+      B = cfma_d(A, Bp, B);
+      A = cmul_d(A, Ap);
+    }
+  }
+  const double2 h0 = col[0];
+  double2 Ae = shfl_up_d2(A, 1), Be = shfl_up_d2(B, 1);
+  if (lane == 0) {
+    Ae = make_double2(1.0, 0.0);
+    Be = make_double2(0.0, 0.0);
+  }
+  double2 x = cfma_d(Ae, h0, Be);  // x_{i0}
+  for (int i = i0; i < i1; ++i) {
+    const double c = cs[i];
+    const double2 sv = sn[i], h1 = col[i + 1];
+    rcol[i] = cfma_d(sv, h1, make_double2(c * x.x, c * x.y));
+    x = cfma_d(make_double2(-sv.x, sv.y), x, make_double2(c * h1.x, c * h1.y));
+  }
+  const double2 xall = cfma_d(A, h0, B);  // lane 31 holds the full composition
+  const double2 a = make_double2(__shfl_sync(0xffffffffu, xall.x, 31), __shfl_sync(0xffffffffu, xall.y, 31));
   __syncwarp();
   if (lane == 0) {
-    const double hn = sqrt(ks.nrm2[b]);
-    bad |= !isfinite(hn);
     const bool happy = hn <= 1e-14 * hmax;
     ks.sigma[long(j + 1) * ks.ldsig + b] = (hn > 0.0 && !happy) ? 1.0 / hn : 0.0;
-    for (int i = 0; i < j; ++i) {
-      const double c = cs_s[i];
-      const double2 sv = sn_s[i], a0 = col[i], a1 = col[i + 1];
-      const double2 u = cmul_d(sv, a1);
-      const double2 lo = cmul_d(conj_d(sv), a0);
-      col[i] = make_double2(c * a0.x + u.x, c * a0.y + u.y);
-      col[i + 1] = make_double2(c * a1.x - lo.x, c * a1.y - lo.y);
-    }
-    const double2 a = col[j];
     const double aa = hypot(a.x, a.y);
     double c;
     double2 s, r;
@@ -274,8 +334,8 @@ __global__ void givens_kernel(KsDev ks, int j, int nrhs) {
     }
     cs[j] = c;
     sn[j] = s;
-    col[j] = r;
-    col[j + 1] = make_double2(0.0, 0.0);
+    rcol[j] = r;
+    rcol[j + 1] = make_double2(0.0, 0.0);
     const double2 gj = g[j];
     const double2 gn = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
     g[j + 1] = gn;  // -conj(s) g_j
@@ -297,11 +357,7 @@ __global__ void givens_kernel(KsDev ks, int j, int nrhs) {
     }
   }
   __syncwarp();
-  for (int i = lane; i <= j + 1; i += 32) colg[i] = col[i];
-  for (int i = lane; i < j; i += 32) {
-    cs[i] = cs_s[i];
-    sn[i] = sn_s[i];
-  }
+  for (int i = lane; i <= j + 1; i += 32) colg[i] = rcol[i];
 }
 
 // u += sum_{i < jn} y[b][i] Z_i  (Z in c64 or c128), one pass.
@@ -384,6 +440,14 @@ norm2_kernel(const double2* __restrict__ x, long stride, long n, double* __restr
 
 }  // namespace
 
+int krylov_blocks_bps(long n, int nrhs, int nchunk, int bps) {
+  long per = (long(bps) * 152 + long(nrhs) * nchunk - 1) / (long(nrhs) * nchunk);
+  long maxb = (n + 4L * KT - 1) / (4L * KT);
+  if (per > maxb) per = maxb;
+  if (per < 1) per = 1;
+  return int(per);
+}
+
 int krylov_blocks(long n, int nrhs, int nchunk) {
   // aim at ~4 blocks per SM over the whole launch, >= 4 points per thread
   long per = (4L * 152 + long(nrhs) * nchunk - 1) / (long(nrhs) * nchunk);
@@ -394,18 +458,24 @@ int krylov_blocks(long n, int nrhs, int nchunk) {
 }
 
 hz_status launch_dots(const double2* V, long ldb, const double2* w, long wstride, long n, int j,
-                      int nrhs, const int* active, double2* partial, int /*unused*/, double2* S,
+                      int nrhs, const int* active, double2* partial, const Tune& tn, double2* S,
                       int ldS, cudaStream_t st) {
-  // balanced chunks of at most VC vectors; one wave of two blocks per SM
-  // (the register budget allows two)
-  int nchunk = (j + 1 + VC - 1) / VC;
+  // balanced chunks of at most vc vectors; one wave of tn.dots_bps blocks
+  // per SM (the register budget allows two)
+  const int vc = tn.dots_vc <= 2 ? 2 : (tn.dots_vc <= 4 ? 4 : VCMAX);
+  int nchunk = (j + 1 + vc - 1) / vc;
   const int vpc = (j + 1 + nchunk - 1) / nchunk;
   nchunk = (j + 1 + vpc - 1) / vpc;  // no empty chunk
-  long per = (2L * 152) / (long(nrhs) * nchunk);
+  long per = (long(tn.dots_bps) * 152) / (long(nrhs) * nchunk);
   const long cap = (n + KT - 1) / KT;  // at least one point per thread
   if (per > cap) per = cap;
   const int nblk = int(per < 1 ? 1 : per);
-  dots_kernel<<<dim3(nblk, nrhs, nchunk), KT, 0, st>>>(V, ldb, w, wstride, n, j, vpc, active, partial);
+  if (vc == 2)
+    dots_kernel<2><<<dim3(nblk, nrhs, nchunk), KT, 0, st>>>(V, ldb, w, wstride, n, j, vpc, active, partial);
+  else if (vc == 4)
+    dots_kernel<4><<<dim3(nblk, nrhs, nchunk), KT, 0, st>>>(V, ldb, w, wstride, n, j, vpc, active, partial);
+  else
+    dots_kernel<VCMAX><<<dim3(nblk, nrhs, nchunk), KT, 0, st>>>(V, ldb, w, wstride, n, j, vpc, active, partial);
   reduce_c_kernel<<<unsigned(nrhs * (j + 1)), KT, 0, st>>>(partial, nblk, j + 1, ldS, S);
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
@@ -413,9 +483,9 @@ hz_status launch_dots(const double2* V, long ldb, const double2* w, long wstride
 
 hz_status launch_update(const double2* V, long ldb, double2* w, long wstride, long n, int j,
                         int nrhs, const double2* S, int ldS, const double* sigma, int ldsig,
-                        const int* active, bool norm, double* partial, int /*unused*/, double* nrm2,
+                        const int* active, bool norm, double* partial, const Tune& tn, double* nrm2,
                         cudaStream_t st) {
-  const int nblk = krylov_blocks(n, nrhs, 1);
+  const int nblk = krylov_blocks_bps(n, nrhs, 1, tn.upd_bps);
   if (norm) {
     update_kernel<true><<<dim3(nblk, nrhs), KT, 0, st>>>(V, ldb, w, wstride, n, j, S, ldS, sigma,
                                                           ldsig, active, partial);

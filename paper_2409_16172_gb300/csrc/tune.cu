@@ -1,0 +1,185 @@
+// Plan autotuner: picks the launch shapes of the kernels that dominate a
+// solve by timing the candidates on the plan's own buffers, once per
+// (grid, K, right-hand sides, restart, precision) in a process, and caches
+// the choice.  Candidates:
+//   CGS2 dot kernel   (vectors per block, blocks per SM) in
+//                     {(8, 1), (8, 2), (4, 2), (4, 3), (2, 2), (2, 4)}
+//   CGS2 update       blocks per SM {2, 4, 6, 8}
+//   symbol pass       nodes per block {1, 2, 4} (the spectrum is read once
+//                     per block; fewer, longer blocks)
+// Timing uses CUDA events on the caller's stream around 3 repetitions of
+// each candidate at the middle Arnoldi step of a cycle.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "hz_internal.h"
+#include "kernels.h"
+
+namespace hz {
+hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* scale, int nrhs,
+                        void* out, int out_kind, cudaStream_t st, const int* active);
+}
+
+using namespace hz;
+
+namespace {
+
+using Key = std::tuple<int, int, int, int, int, int, int>;
+std::mutex g_mu;
+std::map<Key, Tune> g_cache;
+
+Key key_of(const hz_plan* p) {
+  const hz_medium* m = p->med;
+  return Key(m->nx, m->ny, m->nz, m->K, p->max_nrhs, p->opts.restart, p->opts.precision);
+}
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t st;
+  explicit Timer(cudaStream_t s) : st(s) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+  template <typename F>
+  float best_ms(F&& f, int reps = 3) {
+    float best = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+      cudaEventRecord(a, st);
+      if (f() != HZ_OK) return 1e30f;
+      cudaEventRecord(b, st);
+      if (cudaEventSynchronize(b) != cudaSuccess) return 1e30f;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      best = std::min(best, ms);
+    }
+    return best;
+  }
+};
+
+}  // namespace
+
+extern "C" hz_status hz_plan_autotune(hz_plan* plan, void* stream, hz_tune_report* rep) {
+  if (!plan) return set_error(HZ_ERR_INVALID_ARG, "null plan");
+  const Key key = key_of(plan);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+      plan->tune = it->second;
+      if (rep) {
+        *rep = hz_tune_report{};
+        rep->dots_bps = plan->tune.dots_bps;
+        rep->dots_vc = plan->tune.dots_vc;
+        rep->upd_bps = plan->tune.upd_bps;
+        rep->syminv_kpb = plan->tune.syminv_kpb;
+        rep->cached = 1;
+      }
+      return HZ_OK;
+    }
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HZ_TRY(solve_ws_create(plan));
+  hz_plan* p = plan;
+  const hz_medium* med = p->med;
+  const long n = med->n;
+  const int m = p->opts.restart, B = p->max_nrhs;
+  const int j = std::max(0, m / 2);
+  const long ldb = B;
+  KsDev& ks = p->ws->ks;
+  // defined contents for the timed kernels: zero basis, unit scales, all active
+  HZ_CUDA(cudaMemsetAsync(p->V, 0, size_t(j + 2) * B * n * sizeof(double2), st));
+  HZ_CUDA(cudaMemsetAsync(ks.sigma, 0, size_t(m + 1) * B * sizeof(double), st));
+  HZ_CUDA(cudaMemsetAsync(ks.S1, 0, size_t(m + 1) * B * sizeof(double2), st));
+  std::vector<int> ones(B, 1);
+  HZ_CUDA(cudaMemcpyAsync(ks.active, ones.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+  HZ_CUDA(cudaMemsetAsync(p->tmp, 0, size_t(B) * n * 16, st));
+  HZ_CUDA(cudaStreamSynchronize(st));
+  double2* Vn = p->V + long(j + 1) * ldb * n;
+  Timer tm(st);
+  const Tune def;
+  Tune best = def;
+  hz_tune_report r{};
+
+  // CGS2 dot products
+  float tbest = 1e30f, tdef = 0.f;
+  const int cand[6][2] = {{8, 1}, {8, 2}, {4, 2}, {4, 3}, {2, 2}, {2, 4}};
+  for (const auto& c : cand) {
+    const int vc = c[0], bps = c[1];
+    {
+      Tune t = best;
+      t.dots_bps = bps;
+      t.dots_vc = vc;
+      const float ms = tm.best_ms([&] {
+        return launch_dots(p->V, ldb, Vn, n, n, j, B, ks.active,
+                           reinterpret_cast<double2*>(p->partial), t, ks.S1, m + 1, st);
+      });
+      if (bps == def.dots_bps && vc == def.dots_vc) tdef = ms;
+      if (ms < tbest) {
+        tbest = ms;
+        best.dots_bps = bps;
+        best.dots_vc = vc;
+      }
+    }
+  }
+  r.dots_us = 1e3f * tbest;
+  r.dots_us_default = 1e3f * tdef;
+
+  // CGS2 update
+  tbest = 1e30f;
+  for (int bps : {2, 4, 6, 8}) {
+    Tune t = best;
+    t.upd_bps = bps;
+    const float ms = tm.best_ms([&] {
+      return launch_update(p->V, ldb, Vn, n, n, j, B, ks.S1, m + 1, ks.sigma, B, ks.active, false,
+                           p->partial, t, ks.nrm2, st);
+    });
+    if (bps == def.upd_bps) tdef = ms;
+    if (ms < tbest) {
+      tbest = ms;
+      best.upd_bps = bps;
+    }
+  }
+  r.upd_us = 1e3f * tbest;
+  r.upd_us_default = 1e3f * tdef;
+
+  // symbol pass, through a whole preconditioner apply (its other passes do
+  // not depend on the choice)
+  tbest = 1e30f;
+  const int prec = p->opts.precision;
+  void* out = p->Z;
+  for (int kpb : {1, 2, 4}) {
+    if (kpb > 1 && kpb > med->K) break;
+    p->tune = best;
+    p->tune.syminv_kpb = kpb;
+    const float ms = tm.best_ms([&] {
+      return precond_apply(p, prec, p->V, nullptr, B, out, prec == 1 ? 0 : 1, st, nullptr);
+    });
+    if (kpb == def.syminv_kpb) tdef = ms;
+    if (ms < tbest) {
+      tbest = ms;
+      best.syminv_kpb = kpb;
+    }
+  }
+  r.apply_us = 1e3f * tbest;
+  r.apply_us_default = 1e3f * tdef;
+  HZ_CUDA(cudaStreamSynchronize(st));
+  p->tune = best;
+  r.dots_bps = best.dots_bps;
+  r.dots_vc = best.dots_vc;
+  r.upd_bps = best.upd_bps;
+  r.syminv_kpb = best.syminv_kpb;
+  r.cached = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_cache[key] = best;
+  }
+  if (rep) *rep = r;
+  return HZ_OK;
+}

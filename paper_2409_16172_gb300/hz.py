@@ -62,6 +62,14 @@ _vp = C.c_void_p
 _dp = C.POINTER(C.c_double)
 
 
+class hz_tune_report(C.Structure):
+    _fields_ = [("dots_bps", C.c_int), ("dots_vc", C.c_int), ("upd_bps", C.c_int),
+                ("syminv_kpb", C.c_int), ("cached", C.c_int), ("dots_us", C.c_float),
+                ("dots_us_default", C.c_float), ("upd_us", C.c_float),
+                ("upd_us_default", C.c_float), ("apply_us", C.c_float),
+                ("apply_us_default", C.c_float)]
+
+
 class hz_server_opts(C.Structure):
     _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int), ("max_queue", C.c_int),
                 ("device", C.c_int)]
@@ -102,6 +110,7 @@ _SIGS = {
     "hz_server_wait": (C.c_int, [_vp, C.c_uint64, C.c_double]),
     "hz_server_get_stats": (C.c_int, [_vp, C.POINTER(hz_server_stats)]),
     "hz_server_destroy": (C.c_int, [_vp]),
+    "hz_plan_autotune": (C.c_int, [_vp, _vp, C.POINTER(hz_tune_report)]),
     "hz_profile_enable": (C.c_int, [C.c_int]),
     "hz_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "hz_launch_count": (C.c_ulonglong, []),
@@ -254,6 +263,12 @@ class Plan:
     @property
     def handle(self):
         return self._h
+
+    def autotune(self, stream=None) -> dict:
+        """Time the candidate launch shapes on this plan (hz_plan_autotune)."""
+        r = hz_tune_report()
+        check(lib.hz_plan_autotune(self._h, _stream(stream), C.byref(r)))
+        return {f: getattr(r, f) for f, _ in r._fields_}
 
     def nbytes(self) -> int:
         b = C.c_size_t()

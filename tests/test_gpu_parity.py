@@ -204,3 +204,26 @@ def test_gmres_3d_matches_oracle(hz, shape):
     uo, sto = O.gmres(lambda x: O.apply_operator(med_o, x), p.f[0],
                       lambda v: O.apply_preconditioner(med_o, v), restart=20, tol=1e-8)
     assert abs(st[0]["iters"] - sto["iters"]) <= 3, (st[0]["iters"], sto["iters"])
+
+
+def test_autotune_choices_are_valid_and_cached(hz):
+    p = S.bump_problem(128, 43, width=8, ppw=8.0, M=5, Mt=2, nrhs=2)
+    med_g, med_o = media(hz, p)
+    plan = hz.Plan(med_g, precision=1, restart=20, tol=1e-8, maxit=2000, max_nrhs=2)
+    r = plan.autotune()
+    assert r["cached"] == 0
+    assert r["dots_bps"] in (1, 2, 3, 4) and r["dots_vc"] in (2, 4, 8)
+    assert r["upd_bps"] in (2, 4, 6, 8) and r["syminv_kpb"] in (1, 2, 4)
+    assert 0 < r["dots_us"] <= r["dots_us_default"] * 1.0001
+    u, st = plan.solve(np.ascontiguousarray(p.f))
+    for b in range(2):
+        assert st[b]["converged"]
+        assert rel(O.apply_operator(med_o, u[b]), p.f[b]) <= 1e-8
+    plan2 = hz.Plan(med_g, precision=1, restart=20, tol=1e-8, maxit=2000, max_nrhs=2)
+    r2 = plan2.autotune()
+    assert r2["cached"] == 1 and r2["syminv_kpb"] == r["syminv_kpb"]
+    # the tuned preconditioner apply still matches the oracle
+    v = S.random_field(np.random.Generator(np.random.PCG64(9)), p.shape)
+    ref = O.apply_preconditioner(med_o, v)
+    got = plan2.apply_preconditioner(_dev(v), precision=0).cpu().numpy()
+    assert rel(got, ref) <= 1e-10

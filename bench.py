@@ -210,6 +210,69 @@ def run_reference(args, p):
 FP64_DFMA_PER_CLK_PER_SM = 2  # sm_103 (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak)
 
 
+def apply_model_bytes(p):
+    """Algorithmic HBM bytes of one complex64 preconditioner apply: the
+    passes' compulsory traffic with the K planes streamed once each way
+    (x-forward 2s, fused last-axis pass s + Ks, inverse + weighted sum
+    Ks + s + 4 B of interpolation record; 3D adds a y pass on the input and
+    on every plane), for a c128 input and a c128 output."""
+    s, K, n = 8, p.K, p.n * p.f.shape[0]
+    per = (4 + 2 * K) * s + 4 if len(p.shape) == 2 else (6 + 4 * K) * s + 4
+    return n * (per + 8)
+
+
+def time_apply(plan, p, stream, reps=30, nbuf=8):
+    """Mean time (us) of one hz_apply_preconditioner (complex64) on one
+    right-hand side, back to back, rotating through nbuf input/output pairs
+    so that the inputs are not L2-resident."""
+    import torch
+    n = p.n
+    g = torch.Generator(device="cuda").manual_seed(7)
+    xs = [torch.randn(n, dtype=torch.complex128, device="cuda", generator=g) for _ in range(nbuf)]
+    ys = [torch.empty_like(x) for x in xs]
+    for i in range(3):
+        plan.apply_preconditioner(xs[i], 1, out=ys[i], stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for r in range(reps):
+        plan.apply_preconditioner(xs[r % nbuf], 1, out=ys[r % nbuf], stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return 1e3 * e0.elapsed_time(e1) / reps
+
+
+def plain_fp64(hz, med, p, f, stream, graphs, dist, world, max_rhs=2):
+    """The plain FP64 path one right-hand side at a time (complex128
+    preconditioner, right GMRES): the comparison the mixed-precision batched
+    solver is measured against.  One warm-up solve, then up to max_rhs
+    right-hand sides solved one by one."""
+    import torch
+    plan = hz.Plan(med, precision=0, restart=p.restart, tol=p.tol, maxit=4000, max_nrhs=1,
+                   graphs=graphs)
+    plan.autotune()
+    nr = min(f.shape[0], max_rhs)
+    u = torch.zeros_like(f[:1])
+    plan.solve(f[:1], u, stream=stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sts = []
+    e0.record(stream)
+    for i in range(nr):
+        u.zero_()
+        sts += plan.solve(f[i:i + 1], u, stream=stream)[1]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms, value = job_rate(dist, world, nr, e0.elapsed_time(e1))
+    return {"value": value, "unit": "solves/s", "ms_per_solve": ms / nr, "rhs_sampled": nr,
+            "iters": [s["iters"] for s in sts], "rel_true_resid": max(s["rel_true_resid"] for s in sts),
+            "converged": all(s["converged"] for s in sts),
+            "path": "precision 0: complex128 preconditioner, FP64 right GMRES, one rhs at a time"}
+
+
 def run_gpu(args, p, name):
     import torch
     world, rank, local, dist = dist_setup(args.gpus)
@@ -297,6 +360,8 @@ def run_gpu(args, p, name):
     e2e_val = world * nrhs * e2e_steps / e2e_s
 
     ok = all(s["converged"] and s["rel_true_resid"] <= p.tol for st in stats for s in st)
+    apply_us = time_apply(plan, p, stream) if p.precision == 1 else None
+    plain = None if args.no_plain else plain_fp64(hz, med, p, f, stream, graphs, dist, world)
     if rank != 0:
         return
     hbm = float(peaks.get("hbm_gbs", 6800.0))
@@ -323,13 +388,22 @@ def run_gpu(args, p, name):
     fft = [k for k in prof if k.startswith("fft_")]
     pb = sum(prof[k]["bytes"] for k in fft)
     pm = sum(prof[k]["ms"] for k in fft)
-    precond = {"bound": "hbm", "achieved": pb / pm / 1e6, "peak": hbm, "unit": "GB/s",
-               "frac": pb / pm / 1e6 / hbm, "peak_source": hbm_src,
-               "apply_us": 1e3 * pm / max(prof["fft_row_fwd"]["launches"], 1),
-               "kernels": {k: {"launches": prof[k]["launches"],
-                               "avg_us": 1e3 * prof[k]["ms"] / prof[k]["launches"],
-                               "gbs": prof[k]["bytes"] / prof[k]["ms"] / 1e6}
-                           for k in fft}}
+    n_applies = max(prof["fft_row_fwd"]["launches"], 1)
+    precond = None
+    if apply_us is not None:
+        mb = apply_model_bytes(p)
+        precond = {"bound": "hbm", "achieved": mb / apply_us / 1e3, "peak": hbm, "unit": "GB/s",
+                   "frac": mb / apply_us / 1e3 / hbm, "traffic": None, "peak_source": hbm_src,
+                   "apply_us": apply_us, "model_bytes": mb,
+                   "model": "n*[(4+2K)s+4] (2D) or n*[(6+4K)s+4] (3D), s = 8 (complex64), "
+                            "plus 8 B/pt for the complex128 output of the public apply",
+                   "timing": "CUDA events around 30 back-to-back hz_apply_preconditioner calls, "
+                             "8 rotating c128 input/output pairs (> L2)",
+                   "in_solve_apply_us": 1e3 * pm / n_applies,
+                   "kernels": {k: {"launches": prof[k]["launches"],
+                                   "avg_us": 1e3 * prof[k]["ms"] / prof[k]["launches"],
+                                   "masked_model_gbs": prof[k]["bytes"] / prof[k]["ms"] / 1e6}
+                               for k in fft}}
     total_ms = sum(v["ms"] for v in prof.values())
     phases = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                   "share": round(v["ms"] / total_ms, 4),
@@ -366,6 +440,7 @@ def run_gpu(args, p, name):
            "e2e": {"value": e2e_val, "unit": "solves/s",
                    "h2d_bytes_per_step": 2 * 16 * n * nrhs, "d2h_bytes_per_step": 16 * n * nrhs},
            "gpu_launches": launches, "clocks": clocks, "phases": phases, "autotune": tune,
+           "fp64_plain": plain,
            "fp64_peak_tflops": fp64_peak, "fp64_probe_tflops": fp64_probe / 1e3}
     print(json.dumps(out), flush=True)
 
@@ -387,23 +462,38 @@ def run_serving(args):
         srv.result(srv.submit(q.c, q.f, omega=q.omega, M=q.M, Mt=q.Mt, zeta=q.zeta, alpha=0.15,
                               restart=q.restart, tol=q.tol), timeout=600)
     srv.close()
-    srv = hz.Server(max_slots=args.slots)
+
+    def run_stream(slots, precision):
+        srv = hz.Server(max_slots=slots)
+        t0 = time.perf_counter()
+        tickets = []
+        for q, g in zip(reqs, gaps):
+            time.sleep(g)
+            tickets.append(srv.submit(q.c, q.f, omega=q.omega, M=q.M, Mt=q.Mt, zeta=q.zeta,
+                                      alpha=0.15, restart=q.restart, tol=q.tol,
+                                      precision=precision, graphs=q.n <= 256 * 256))
+        res = [srv.result(t, timeout=3600) for t in tickets]
+        span = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return span, st, res
+
     sampler = ClockSampler(0)
     sampler.start()
-    t0 = time.perf_counter()
-    tickets = []
-    for q, g in zip(reqs, gaps):
-        time.sleep(g)
-        tickets.append(srv.submit(q.c, q.f, omega=q.omega, M=q.M, Mt=q.Mt, zeta=q.zeta,
-                                  alpha=0.15, restart=q.restart, tol=q.tol,
-                                  graphs=q.n <= 256 * 256))
-    res = [srv.result(t, timeout=1800) for t in tickets]
-    span = time.perf_counter() - t0
-    st = srv.stats()
+    span, st, res = run_stream(args.slots, 1)
     clocks = sampler.stop()
-    srv.close()
     rhs = sum(q.f.shape[0] for q in reqs)
     ok = all(r[0] and r[3] == 0 for r in res)
+    plain = None
+    if not args.no_plain:
+        # the same arrival stream served by the plain FP64 path one request
+        # at a time
+        span0, st0, res0 = run_stream(1, 0)
+        plain = {"value": rhs / span0, "unit": "solves/s", "p50_ms": st0["p50_ms"],
+                 "p99_ms": st0["p99_ms"], "mean_ms": st0["mean_ms"], "span_s": span0,
+                 "all_converged": all(r[0] and r[3] == 0 for r in res0),
+                 "path": "precision 0 (complex128 preconditioner, FP64 GMRES), one request "
+                         "on the GPU at a time, same requests and arrival times"}
     out = {"metric": METRIC + " (serving stream)", "value": rhs / span, "unit": "solves/s",
            "n_gpus": 1, "steps": len(reqs), "warmup": 2, "ms_per_step": 1e3 * span / len(reqs),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -412,7 +502,7 @@ def run_serving(args):
                       "grids": sorted({"x".join(map(str, q.shape)) for q in reqs}),
                       "rhs_total": rhs},
            "latency": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"]},
-           "server": st, "all_converged": ok, "clocks": clocks}
+           "server": st, "all_converged": ok, "clocks": clocks, "fp64_plain": plain}
     print(json.dumps(out), flush=True)
 
 
@@ -430,6 +520,8 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=6, help="Arnoldi steps in the CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the plain FP64 one-rhs-at-a-time comparison solve")
     ap.add_argument("--ref-sample", type=int, default=3, help="reference arm: steps per sample")
     ap.add_argument("--ref-iters", type=int, default=0,
                     help="reference arm: Arnoldi steps per solve (0: count them with one full "

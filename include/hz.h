@@ -154,7 +154,9 @@ hz_status hz_plan_create(hz_medium* med, const hz_solver_opts* opts, int max_nrh
  * launch shapes).  Times candidate launch shapes of the kernels that dominate
  * a solve on the plan's own buffers with CUDA events on `stream`: blocks per
  * SM and vectors per block of the CGS2 dot kernel, blocks per SM of the CGS2
- * update, nodes per block of the last-axis symbol pass.  The choice is stored
+ * update, nodes per block of the last-axis symbol pass, and whether the
+ * x-inverse pass accumulates the weighted sum as it goes or transforms the
+ * planes in place and gathers the sum afterwards.  The choice is stored
  * in the plan and cached per (grid, K, max_nrhs, restart, precision) for the
  * process; later plans with the same key reuse it without timing.
  * Synchronous; overwrites the plan's work arrays (call before solving). */
@@ -164,9 +166,17 @@ typedef struct {
   float dots_us, dots_us_default;     /* chosen vs default shape           */
   float upd_us, upd_us_default;
   float apply_us, apply_us_default;   /* whole preconditioner apply        */
+  int rowinv_mode;          /* x-inverse pass: 0 by grid size, 1 in place
+                               then a gather of the weighted sum, 2 fused  */
 } hz_tune_report;
 
 hz_status hz_plan_autotune(hz_plan* plan, void* stream, hz_tune_report* report);
+
+/* Sets the plan's launch shapes from a report (e.g. one saved from an
+ * earlier hz_plan_autotune): dots_vc in {2, 4, 8}, dots_bps and upd_bps in
+ * 1..32, syminv_kpb in {1, 2, 4}, rowinv_mode in {0, 1, 2}; the timing
+ * fields are ignored.  HZ_ERR_INVALID_ARG for any other value. */
+hz_status hz_plan_set_tune(hz_plan* plan, const hz_tune_report* report);
 
 /* Bytes of device memory the plan holds. */
 hz_status hz_plan_bytes(const hz_plan* plan, size_t* bytes);

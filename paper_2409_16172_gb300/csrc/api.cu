@@ -191,7 +191,8 @@ hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* s
     PhaseScope ps(st, PH_ROW_INV, B * (m->rowk_used * nx * s + dn * (rb + so)),
                   B * (m->rowk_used * 5.0 * nx * l2(nx) + 8.0 * dn));
     HZ_TRY(ox->row_inv_acc(prec, out_kind, p->planes, rec, m->segtab, m->nseg, m->rowmask, m->K,
-                           rows, rows * nrhs, n, 1.0 / double(n), tw(tx), out, st, active));
+                           rows, rows * nrhs, n, 1.0 / double(n), tw(tx), out, st, active,
+                           p->tune.rowinv_mode));
   }
   return HZ_OK;
 }

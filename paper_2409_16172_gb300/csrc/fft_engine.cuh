@@ -42,6 +42,20 @@ template <int S, typename V> __device__ __forceinline__ V cmul_si(V a) {
   return (S > 0) ? cmk<V>(-a.y, a.x) : cmk<V>(a.y, -a.x);
 }
 
+// Twiddle loads through the read-only path, kept where they are written: a
+// kernel that runs several transforms per thread (one per node) would
+// otherwise keep every twiddle of every stage live in registers across them.
+__device__ __forceinline__ float2 ld_twiddle(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double2 ld_twiddle(const double2* p) {
+  double2 v;
+  asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  return v;
+}
+
 // ---------------------------------------------------------------------------
 // Small DFTs, X[m] = sum_n x[n] e^{S 2 pi i n m / R}, in place on x[0..R-1].
 // ---------------------------------------------------------------------------
@@ -202,6 +216,38 @@ HZ_PLAN_T(FftPlanW<512>, 512, 16, 16, 16, 2)
 HZ_PLAN_T(FftPlanW<1024>, 1024, 32, 32, 32)
 template <> struct RowPlan<float, 512> { using P = FftPlanW<512>; };
 template <> struct RowPlan<float, 1024> { using P = FftPlanW<1024>; };
+
+// Strided-axis (column) kernels use FftPlan, except as below.
+template <typename R, int N> struct ColPlan { using P = FftPlan<N>; };
+
+// FP64 lines up to 256 points: radix-4 (and 2, 3) stages with 4 or 12
+// elements per thread.  An FP64 instruction occupies a sub-partition's FP64
+// unit for many cycles on this part, so a short line is transformed by more
+// threads with shorter per-thread chains; the extra stages cost shared
+// memory traffic, not FP64 work.
+template <int N> struct FftPlanD;
+HZ_PLAN_T(FftPlanD<8>, 8, 4, 4, 2)
+HZ_PLAN_T(FftPlanD<16>, 16, 4, 4, 4)
+HZ_PLAN_T(FftPlanD<24>, 24, 12, 4, 2, 3)
+HZ_PLAN_T(FftPlanD<32>, 32, 4, 4, 4, 2)
+HZ_PLAN_T(FftPlanD<64>, 64, 4, 4, 4, 4)
+HZ_PLAN_T(FftPlanD<96>, 96, 12, 4, 4, 2, 3)
+HZ_PLAN_T(FftPlanD<128>, 128, 4, 4, 4, 4, 2)
+HZ_PLAN_T(FftPlanD<192>, 192, 12, 4, 4, 4, 3)
+HZ_PLAN_T(FftPlanD<256>, 256, 4, 4, 4, 4, 4)
+#define HZ_DPLAN(NN)                                                       \
+  template <> struct RowPlan<double, NN> { using P = FftPlanD<NN>; };      \
+  template <> struct ColPlan<double, NN> { using P = FftPlanD<NN>; };
+HZ_DPLAN(8)
+HZ_DPLAN(16)
+HZ_DPLAN(24)
+HZ_DPLAN(32)
+HZ_DPLAN(64)
+HZ_DPLAN(96)
+HZ_DPLAN(128)
+HZ_DPLAN(192)
+HZ_DPLAN(256)
+#undef HZ_DPLAN
 #undef HZ_PLAN
 #undef HZ_PLAN_T
 
@@ -243,7 +289,7 @@ struct LineFFT {
     for (int e = 0; e < E; ++e) x[e] = line[padded(stage0_index(t, e)) * LS];
   }
 
-  template <int STAGE, int NS>
+  template <int STAGE, int NS, bool KEEP>
   __device__ static __forceinline__ void stage(V* line, int t, V (&x)[E], const V* __restrict__ tw) {
     if constexpr (STAGE < P::NST) {
       constexpr int RAD = P::rad(STAGE);
@@ -263,18 +309,20 @@ struct LineFFT {
         if constexpr (NS > 1) {
 #pragma unroll
           for (int r = 1; r < RAD; ++r) {
-            V w = __ldg(&tw[r * k * (N / (NS * RAD))]);
+            V w = ld_twiddle(&tw[r * k * (N / (NS * RAD))]);
             if constexpr (S > 0) w.y = -w.y;
             x[b * RAD + r] = cmul(x[b * RAD + r], w);
           }
         }
         dftR<RAD, S>(&x[b * RAD]);
-        const int d = (j / NS) * NS * RAD + k;
+        if constexpr (!(KEEP && STAGE == P::NST - 1)) {
+          const int d = (j / NS) * NS * RAD + k;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) line[padded(d + r * NS) * LS] = x[b * RAD + r];
+          for (int r = 0; r < RAD; ++r) line[padded(d + r * NS) * LS] = x[b * RAD + r];
+        }
       }
-      sync();
-      stage<STAGE + 1, NS * RAD>(line, t, x, tw);
+      if constexpr (!(KEEP && STAGE == P::NST - 1)) sync();
+      stage<STAGE + 1, NS * RAD, KEEP>(line, t, x, tw);
     }
   }
 
@@ -283,7 +331,19 @@ struct LineFFT {
   // the line holds the result in natural order and the line's threads (the
   // block, unless WS) are synchronised.  tw[i] = exp(-2 pi i * i / N) for i < N.
   __device__ static __forceinline__ void run(V* line, int t, V (&x)[E], const V* __restrict__ tw) {
-    stage<0, 1>(line, t, x, tw);
+    stage<0, 1, false>(line, t, x, tw);
+  }
+
+  // Same transform, but the last stage leaves its outputs in registers:
+  // x[e] holds output position out_index(t, e).  The line's shared memory is
+  // free again on return (the last stage's reads are behind a barrier), so
+  // the next transform on the same line needs no barrier of the caller.
+  static constexpr int RL = P::rad(P::NST - 1);
+  __device__ static __forceinline__ int out_index(int t, int e) {
+    return t + (e / RL) * TPL + (e % RL) * (N / RL);
+  }
+  __device__ static __forceinline__ void run_regs(V* line, int t, V (&x)[E], const V* __restrict__ tw) {
+    stage<0, 1, true>(line, t, x, tw);
   }
 };
 

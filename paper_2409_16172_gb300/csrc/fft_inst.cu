@@ -1,6 +1,8 @@
 // Instantiates the FFT pass kernels for one axis length, HZ_FFT_N, and
 // exposes them as an FftOps table.  The build compiles this file once per
 // supported length, in parallel.
+#include <algorithm>
+
 #include "fft_kernels.cuh"
 
 #ifndef HZ_FFT_N
@@ -48,13 +50,30 @@ template <typename R, typename OutT>
 hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segtab, int nseg,
                         const unsigned long long* rowmask, int K, long rows_per_rhs, long nrows,
                         long n, double inv_n, const void* tw, void* out, cudaStream_t st,
-                        const int* active) {
+                        const int* active, int mode) {
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
   const bool small = (nrows + C::ROW_LINES - 1) / C::ROW_LINES < 2L * 152;
-  const int lines = small ? C::ROW_LINES_SMALL : C::ROW_LINES;
-  auto k = small ? row_inv_acc_kernel<R, N, OutT, C::ROW_LINES_SMALL>
-                 : row_inv_acc_kernel<R, N, OutT, C::ROW_LINES>;
+  if (mode == 1 || (mode == 0 && small)) {
+    // few rows: (row, node) lines in parallel, in place, then the gather
+    auto ki = row_inv_inplace_kernel<R, N, C::ROW_LINES>;
+    HZ_TRY(smem_attr(ki, C::row_smem()));
+    dim3 grid(unsigned((nrows + C::ROW_LINES - 1) / C::ROW_LINES), unsigned(K));
+    ki<<<grid, C::ROW_THREADS, C::row_smem(), st>>>(
+        static_cast<V*>(const_cast<void*>(planes)), rowmask, K, rows_per_rhs, nrows, n,
+        static_cast<const V*>(tw), active);
+    HZ_CUDA(cudaGetLastError());
+    const long total = nrows * N;
+    const long gblocks = std::min<long>((total + 255) / 256, 152L * 16);
+    weighted_gather_kernel<R, OutT><<<unsigned(gblocks), 256, 0, st>>>(
+        static_cast<const V*>(planes), static_cast<const typename RecT<R>::T*>(rec), segtab, K,
+        n, total, R(inv_n), static_cast<OutT*>(out), active);
+    HZ_CUDA(cudaGetLastError());
+    count_launches(1);  // the phase counts one
+    return HZ_OK;
+  }
+  constexpr int lines = C::ROW_LINES;
+  auto k = row_inv_acc_kernel<R, N, OutT, C::ROW_LINES>;
   HZ_TRY(smem_attr(k, C::row_acc_smem(lines)));
   const long blocks = (nrows + lines - 1) / lines;
   k<<<unsigned(blocks), lines * C::TPL_ROW, C::row_acc_smem(lines), st>>>(
@@ -68,15 +87,15 @@ hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segta
 hz_status row_inv_acc(int prec, int out_kind, const void* planes, const void* rec,
                       const uchar2* segtab, int nseg, const unsigned long long* rowmask, int K,
                       long rows_per_rhs, long nrows, long n, double inv_n, const void* tw,
-                      void* out, cudaStream_t st, const int* active) {
+                      void* out, cudaStream_t st, const int* active, int mode) {
   if (prec == 0)
     return row_inv_acc_t<double, double2>(planes, rec, segtab, nseg, rowmask, K, rows_per_rhs,
-                                          nrows, n, inv_n, tw, out, st, active);
+                                          nrows, n, inv_n, tw, out, st, active, mode);
   if (out_kind == 0)
     return row_inv_acc_t<float, float2>(planes, rec, segtab, nseg, rowmask, K, rows_per_rhs,
-                                        nrows, n, inv_n, tw, out, st, active);
+                                        nrows, n, inv_n, tw, out, st, active, mode);
   return row_inv_acc_t<float, double2>(planes, rec, segtab, nseg, rowmask, K, rows_per_rhs,
-                                       nrows, n, inv_n, tw, out, st, active);
+                                       nrows, n, inv_n, tw, out, st, active, mode);
 }
 
 template <typename R, int SIGN>
@@ -114,16 +133,18 @@ hz_status line_sym_inv_t(const void* vhat, void* planes, int nx, long outer, lon
                          cudaStream_t st, const int* active, int kpb) {
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
-  auto k = line_sym_inv_kernel<R, N>;
+  // nodes per block: 1, 2 or 4
+  kpb = kpb >= 4 ? 4 : (kpb >= 2 ? 2 : 1);
+  auto k = kpb == 4 ? line_sym_inv_kernel<R, N, 4>
+                    : (kpb == 2 ? line_sym_inv_kernel<R, N, 2> : line_sym_inv_kernel<R, N, 1>);
   HZ_TRY(smem_attr(k, C::col_smem()));
   const int ntile = (nx + C::TB - 1) / C::TB;
-  if (kpb < 1) kpb = 1;
   dim3 grid(unsigned(ntile * outer), unsigned((K + kpb - 1) / kpb), unsigned(batch));
   k<<<grid, C::COL_THREADS, C::col_smem(), st>>>(
       static_cast<const V*>(vhat), static_cast<V*>(planes), nx, ntile, S, ostride, n, K,
       static_cast<const R*>(xi2_x), static_cast<const R*>(xi2_o), static_cast<const R*>(xi2_l),
       static_cast<const V*>(symA), static_cast<const V*>(symG), smask, smO, smS,
-      static_cast<const V*>(tw), active, kpb);
+      static_cast<const V*>(tw), active);
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }

@@ -27,7 +27,8 @@ namespace hz {
 // block moves at least 64 contiguous bytes per row, has >= 128 threads, at
 // most 512, and its shared memory stays under ~200 KB.
 template <typename R, int N> struct LineCfg {
-  static constexpr int TPL = N / FftPlan<N>::E;  // strided kernels
+  using CP = typename ColPlan<R, N>::P;           // strided kernels
+  static constexpr int TPL = N / CP::E;
   using RP = typename RowPlan<R, N>::P;           // row kernels
   static constexpr int TPL_ROW = N / RP::E;
   static constexpr int ROW_THREADS = TPL_ROW > 128 ? TPL_ROW : 128;
@@ -78,6 +79,27 @@ __device__ __forceinline__ void decode_rec(double rec, int& seg, double& t) {
   t = rec - double(seg);
 }
 
+// Nodes per block of the symbol pass: 1, 2 or 4 (compiled variants).
+constexpr int SYM_KPB_MAX = 4;
+
+// 1/x for the symbol.  FP32: one MUFU reciprocal (PTX rcp.approx, at most
+// 1 ulp).
+__device__ __forceinline__ float recip(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// FP64: the MUFU approximation refined by two Newton-Raphson steps for 1/x,
+// r <- r + r (1 - x r), each of which doubles the number of correct bits.
+__device__ __forceinline__ double recip(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 template <typename R> struct RecT;
 template <> struct RecT<float> { using T = uint32_t; };
 template <> struct RecT<double> { using T = double; };
@@ -111,11 +133,11 @@ row_fwd_kernel(const double2* __restrict__ in, const double* __restrict__ scale,
     double2 v = valid ? src[F::stage0_index(t, e)] : make_double2(0.0, 0.0);
     x[e] = cmk<V>(R(v.x) * s, R(v.y) * s);
   }
-  F::run(line, t, x, tw);
+  F::run_regs(line, t, x, tw);
   if (valid) {
     V* dst = out + row * N;
 #pragma unroll
-    for (int i = 0; i < E; ++i) dst[t + i * TPL] = line[padded(t + i * TPL)];
+    for (int e = 0; e < E; ++e) dst[F::out_index(t, e)] = x[e];
   }
 }
 
@@ -160,10 +182,12 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
   V* stg = reinterpret_cast<V*>(smem_raw + LineCfg<R, N>::stage_offset(LPB)) + li * 2 * N;
   typename RecT<R>::T r_[E];
   V acc[E];
+  // this thread's output positions are those the transform's last stage
+  // leaves in its registers
 #pragma unroll
-  for (int i = 0; i < E; ++i) {
-    r_[i] = valid ? rec[lrow * N + t + i * TPL] : typename RecT<R>::T(0);
-    acc[i] = cmk<V>(R(0), R(0));
+  for (int e = 0; e < E; ++e) {
+    r_[e] = valid ? rec[lrow * N + F::out_index(t, e)] : typename RecT<R>::T(0);
+    acc[e] = cmk<V>(R(0), R(0));
   }
   __syncthreads();
   // planes to transform: those any line of the block needs, or with
@@ -200,27 +224,28 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
       cp_async_commit();  // keep one group in flight per step
     }
     cp_async_wait1();   // this thread's copies of plane kc are done
-    F::sync();          // ... and the line's; the previous results were read
+    F::sync();          // ... and the line's
     const bool need = (mymask >> kc) & 1ull;
     V x[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) x[e] = need ? stg[buf * N + F::stage0_index(t, e)] : cmk<V>(R(0), R(0));
-    F::run(line, t, x, tw);
+    // Multi-stage plans: the transform's barriers also order these staging
+    // reads before the next iteration's copies into the same buffer.  A
+    // single-stage plan has one thread per line, which reads only what it
+    // copied itself.
+    F::run_regs(line, t, x, tw);
     if (need) {
 #pragma unroll
-      for (int i = 0; i < E; ++i) {
+      for (int e = 0; e < E; ++e) {
         int seg;
         R tf;
-        decode_rec(r_[i], seg, tf);
+        decode_rec(r_[e], seg, tf);
         const uchar2 kk = seg_s[seg];
         R w = R(0);
         if (kk.x == kc) w += R(1) - tf;
         if (kk.y == kc) w += tf;
-        if (w != R(0)) {
-          const V v = line[padded(t + i * TPL)];
-          acc[i].x += w * v.x;
-          acc[i].y += w * v.y;
-        }
+        acc[e].x += w * x[e].x;
+        acc[e].y += w * x[e].y;
       }
     }
     kc = kn;
@@ -229,12 +254,87 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
   if (valid) {
     OutT* dst = out + rhs * n + lrow * N;
 #pragma unroll
-    for (int i = 0; i < E; ++i) {
+    for (int e = 0; e < E; ++e) {
       OutT o;
-      o.x = acc[i].x * inv_n;
-      o.y = acc[i].y * inv_n;
-      dst[t + i * TPL] = o;
+      o.x = acc[e].x * inv_n;
+      o.y = acc[e].y * inv_n;
+      dst[F::out_index(t, e)] = o;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The same pass in two kernels, for grids with too few rows to fill the GPU
+// with one block per row: the inverse FFT along x of every (row, node) line
+// that the row's points weight, in place in the planes, one line per thread
+// group (grid: row blocks x K); then the weighted sum as a gather of the two
+// weighted planes per point (Eqn. 405), in the same order as the fused
+// kernel: (1 - t) plane_lo first, then + t plane_hi.
+// ---------------------------------------------------------------------------
+template <typename R, int N, int LPB>
+__global__ void __launch_bounds__(LPB * LineCfg<R, N>::TPL_ROW)
+row_inv_inplace_kernel(typename cvec<R>::T* __restrict__ planes,
+                       const unsigned long long* __restrict__ rowmask, int K, long rows_per_rhs,
+                       long nrows, long n, const typename cvec<R>::T* __restrict__ tw,
+                       const int* __restrict__ active) {
+  using V = typename cvec<R>::T;
+  using F = LineFFT<R, N, +1, 1, LineCfg<R, N>::WS, typename LineCfg<R, N>::RP>;
+  constexpr int TPL = F::TPL, E = F::E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sm = reinterpret_cast<V*>(smem_raw);
+  const int li = threadIdx.x / TPL, t = threadIdx.x % TPL;
+  const long row = long(blockIdx.x) * LPB + li;
+  const int k = blockIdx.y;
+  const long rhs = row < nrows ? row / rows_per_rhs : 0;
+  const long lrow = row - rhs * rows_per_rhs;
+  const bool valid = row < nrows && (!active || active[rhs]) && ((rowmask[lrow] >> k) & 1ull);
+  V* g = planes + (rhs * K + k) * n + lrow * N;
+  V x[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) x[e] = valid ? g[F::stage0_index(t, e)] : cmk<V>(R(0), R(0));
+  // every thread of the block takes part in the transform's barriers; the
+  // line's reads are behind them before any of its writes
+  F::run_regs(sm + li * padded_len(N), t, x, tw);
+  if (valid) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) g[F::out_index(t, e)] = x[e];
+  }
+}
+
+template <typename R, typename OutT>
+__global__ void __launch_bounds__(256)
+weighted_gather_kernel(const typename cvec<R>::T* __restrict__ planes,
+                       const typename RecT<R>::T* __restrict__ rec, const uchar2* __restrict__ segtab,
+                       int K, long n, long total, R inv_n, OutT* __restrict__ out,
+                       const int* __restrict__ active) {
+  using V = typename cvec<R>::T;
+  for (long i = long(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+       i += long(gridDim.x) * blockDim.x) {
+    const long rhs = i / n, e = i - rhs * n;
+    if (active && !active[rhs]) continue;
+    int seg;
+    R tf;
+    decode_rec(rec[e], seg, tf);
+    const uchar2 kk = segtab[seg];
+    const V* pl = planes + rhs * K * n + e;
+    V acc = cmk<V>(R(0), R(0));
+    if (kk.x == kk.y) {
+      acc = pl[long(kk.x) * n];
+    } else {
+      const R wl = R(1) - tf;
+      if (wl != R(0)) {
+        const V a = pl[long(kk.x) * n];
+        acc = cmk<V>(wl * a.x, wl * a.y);
+      }
+      if (tf != R(0)) {
+        const V b = pl[long(kk.y) * n];
+        acc = cmk<V>(fma(tf, b.x, acc.x), fma(tf, b.y, acc.y));
+      }
+    }
+    OutT o;
+    o.x = acc.x * inv_n;
+    o.y = acc.y * inv_n;
+    out[i] = o;
   }
 }
 
@@ -253,8 +353,8 @@ line_pass_kernel(typename cvec<R>::T* __restrict__ data, int nx, int ntile, long
                  int per_rhs) {
   using V = typename cvec<R>::T;
   constexpr int TB = LineCfg<R, N>::TB;
-  using F = LineFFT<R, N, SIGN, TB>;
-  constexpr int TPL = F::TPL, E = F::E;
+  using F = LineFFT<R, N, SIGN, TB, false, typename LineCfg<R, N>::CP>;
+  constexpr int E = F::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
   const int col = threadIdx.x % TB, t = threadIdx.x / TB;
@@ -270,10 +370,10 @@ line_pass_kernel(typename cvec<R>::T* __restrict__ data, int nx, int ntile, long
   V v[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) v[e] = valid ? base[long(F::stage0_index(t, e)) * S] : cmk<V>(R(0), R(0));
-  F::run(line, t, v, tw);
+  F::run_regs(line, t, v, tw);
   if (valid) {
 #pragma unroll
-    for (int i = 0; i < E; ++i) base[long(t + i * TPL) * S] = line[padded(t + i * TPL) * TB];
+    for (int e = 0; e < E; ++e) base[long(F::out_index(t, e)) * S] = v[e];
   }
 }
 
@@ -284,7 +384,7 @@ line_pass_kernel(typename cvec<R>::T* __restrict__ data, int nx, int ntile, long
 // Plane k is only stored where smask[o smO + p smS] has bit k: per row in 2D
 // (the next pass is the x inverse), per z-slab in 3D (the next pass is the y
 // inverse, which needs the whole slab).
-template <typename R, int N>
+template <typename R, int N, int KPB>
 __global__ void __launch_bounds__(LineCfg<R, N>::COL_THREADS)
 line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
                     typename cvec<R>::T* __restrict__ planes, int nx, int ntile, long S,
@@ -293,20 +393,20 @@ line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
                     const typename cvec<R>::T* __restrict__ symA,
                     const typename cvec<R>::T* __restrict__ symG,
                     const unsigned long long* __restrict__ smask, long smO, long smS,
-                    const typename cvec<R>::T* __restrict__ tw, const int* __restrict__ active,
-                    int kpb) {
+                    const typename cvec<R>::T* __restrict__ tw, const int* __restrict__ active) {
   using V = typename cvec<R>::T;
   constexpr int TB = LineCfg<R, N>::TB;
-  using F = LineFFT<R, N, +1, TB>;
-  constexpr int TPL = F::TPL, E = F::E;
+  using F = LineFFT<R, N, +1, TB, false, typename LineCfg<R, N>::CP>;
+  constexpr int E = F::E;
+  static_assert(KPB == 1 || KPB == 2 || KPB == 4, "nodes per block");
   if (active && !active[blockIdx.z]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
   const int col = threadIdx.x % TB, t = threadIdx.x / TB;
   const int tile = blockIdx.x % ntile;
   const long o = blockIdx.x / ntile;
-  const int k0 = blockIdx.y * kpb;
-  const int k1 = min(K, k0 + kpb);
+  const int k0 = blockIdx.y * KPB;
+  const int k1 = min(K, k0 + KPB);
   const long rhs = blockIdx.z;
   const int x = tile * TB + col;
   const bool valid = x < nx;
@@ -321,24 +421,35 @@ line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
     spec[e] = valid ? src[long(p) * S] : cmk<V>(R(0), R(0));
     s2[e] = sxo + xi2_l[p];
   }
+  // plane-store bits of this block's nodes for the rows this thread writes
+  constexpr int MW = (E * KPB + 31) / 32;
+  uint32_t mb[MW];
+#pragma unroll
+  for (int w = 0; w < MW; ++w) mb[w] = 0u;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const long p = F::out_index(t, e);
+    const uint32_t bits = uint32_t(smask[o * smO + p * smS] >> k0) & ((1u << KPB) - 1u);
+    mb[(e * KPB) / 32] |= bits << ((e * KPB) % 32);
+  }
+#pragma unroll 1
   for (int k = k0; k < k1; ++k) {
     const V A = symA[k], G = symG[k];
+    const int kk = k - k0;
     V v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      // q = 1 / (A - G s) = conj(den) / |den|^2
+      // vhat q_k = vhat conj(den) / |den|^2,  den = A - G |xi|^2
       const V den = cmk<V>(A.x - G.x * s2[e], A.y - G.y * s2[e]);
-      const R inv = R(1) / (den.x * den.x + den.y * den.y);
-      v[e] = cmul(spec[e], cmk<V>(den.x * inv, -den.y * inv));
+      v[e] = cscale(cmulc(spec[e], den), recip(den.x * den.x + den.y * den.y));
     }
-    if (k > k0) __syncthreads();  // the previous node's results have been stored
-    F::run(sm + col, t, v, tw);
+    F::run_regs(sm + col, t, v, tw);
     if (valid) {
+      // offsets within one plane fit in 32 bits
       V* dst = planes + (rhs * K + k) * n + off;
 #pragma unroll
-      for (int i = 0; i < E; ++i) {
-        const int p = t + i * TPL;
-        if ((smask[o * smO + long(p) * smS] >> k) & 1ull) dst[long(p) * S] = sm[padded(p) * TB + col];
+      for (int e = 0; e < E; ++e) {
+        if ((mb[(e * KPB) / 32] >> ((e * KPB) % 32 + kk)) & 1u) dst[F::out_index(t, e) * int(S)] = v[e];
       }
     }
   }

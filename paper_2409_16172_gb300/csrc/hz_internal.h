@@ -117,10 +117,13 @@ struct FftOps {
   hz_status (*row_fwd)(int prec, const double2* in, const double* scale, long rows_per_rhs,
                        long nrows, const void* tw, void* out, cudaStream_t st, const int* active);
   // inverse FFT along x of the K planes + weighted sum; out_kind 0: c64, 1: c128
+  // mode 0: by size, 1: in-place inverse then gather (planes overwritten),
+  // 2: fused inverse + weighted sum
   hz_status (*row_inv_acc)(int prec, int out_kind, const void* planes, const void* rec,
                            const uchar2* segtab, int nseg, const unsigned long long* rowmask,
                            int K, long rows_per_rhs, long nrows, long n, double inv_n,
-                           const void* tw, void* out, cudaStream_t st, const int* active);
+                           const void* tw, void* out, cudaStream_t st, const int* active,
+                           int mode);
   // FFT along a strided axis, in place; sign -1 forward, +1 inverse
   hz_status (*line_pass)(int prec, int sign, void* data, int nx, long outer, long S,
                          long ostride, long bstride, int batch,
@@ -168,6 +171,7 @@ struct Tune {
   int dots_vc = 8;
   int upd_bps = 4;
   int syminv_kpb = 1;
+  int rowinv_mode = 0;  // FftOps::row_inv_acc mode
 };
 }
 

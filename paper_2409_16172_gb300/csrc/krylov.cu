@@ -235,7 +235,6 @@ update_kernel(const double2* __restrict__ V, long ldb, double2* __restrict__ w, 
 __device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ double2 conj_d(double2 a) { return make_double2(a.x, -a.y); }
 
 __device__ __forceinline__ double2 cfma_d(double2 a, double2 b, double2 c) {  // a b + c
   return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));

@@ -7,6 +7,7 @@
 //   CGS2 update       blocks per SM {2, 4, 6, 8}
 //   symbol pass       nodes per block {1, 2, 4} (the spectrum is read once
 //                     per block; fewer, longer blocks)
+//   x-inverse pass    fused weighted sum, or in place + gather
 // Timing uses CUDA events on the caller's stream around 3 repetitions of
 // each candidate at the middle Arnoldi step of a cycle.
 #include <algorithm>
@@ -65,6 +66,21 @@ struct Timer {
 
 }  // namespace
 
+extern "C" hz_status hz_plan_set_tune(hz_plan* plan, const hz_tune_report* r) {
+  if (!plan || !r) return set_error(HZ_ERR_INVALID_ARG, "null argument");
+  const bool ok = (r->dots_vc == 2 || r->dots_vc == 4 || r->dots_vc == 8) && r->dots_bps >= 1 &&
+                  r->dots_bps <= 32 && r->upd_bps >= 1 && r->upd_bps <= 32 &&
+                  (r->syminv_kpb == 1 || r->syminv_kpb == 2 || r->syminv_kpb == 4) &&
+                  r->rowinv_mode >= 0 && r->rowinv_mode <= 2;
+  if (!ok) return set_error(HZ_ERR_INVALID_ARG, "launch shape out of range");
+  plan->tune.dots_vc = r->dots_vc;
+  plan->tune.dots_bps = r->dots_bps;
+  plan->tune.upd_bps = r->upd_bps;
+  plan->tune.syminv_kpb = r->syminv_kpb;
+  plan->tune.rowinv_mode = r->rowinv_mode;
+  return HZ_OK;
+}
+
 extern "C" hz_status hz_plan_autotune(hz_plan* plan, void* stream, hz_tune_report* rep) {
   if (!plan) return set_error(HZ_ERR_INVALID_ARG, "null plan");
   const Key key = key_of(plan);
@@ -79,6 +95,7 @@ extern "C" hz_status hz_plan_autotune(hz_plan* plan, void* stream, hz_tune_repor
         rep->dots_vc = plan->tune.dots_vc;
         rep->upd_bps = plan->tune.upd_bps;
         rep->syminv_kpb = plan->tune.syminv_kpb;
+        rep->rowinv_mode = plan->tune.rowinv_mode;
         rep->cached = 1;
       }
       return HZ_OK;
@@ -167,6 +184,19 @@ extern "C" hz_status hz_plan_autotune(hz_plan* plan, void* stream, hz_tune_repor
       best.syminv_kpb = kpb;
     }
   }
+  // x-inverse pass: fused weighted sum vs in place + gather (grids with
+  // few rows always take the second)
+  for (int mode : {2, 1}) {
+    p->tune = best;
+    p->tune.rowinv_mode = mode;
+    const float ms = tm.best_ms([&] {
+      return precond_apply(p, prec, p->V, nullptr, B, out, prec == 1 ? 0 : 1, st, nullptr);
+    });
+    if (ms < tbest) {
+      tbest = ms;
+      best.rowinv_mode = mode;
+    }
+  }
   r.apply_us = 1e3f * tbest;
   r.apply_us_default = 1e3f * tdef;
   HZ_CUDA(cudaStreamSynchronize(st));
@@ -175,6 +205,7 @@ extern "C" hz_status hz_plan_autotune(hz_plan* plan, void* stream, hz_tune_repor
   r.dots_vc = best.dots_vc;
   r.upd_bps = best.upd_bps;
   r.syminv_kpb = best.syminv_kpb;
+  r.rowinv_mode = best.rowinv_mode;
   r.cached = 0;
   {
     std::lock_guard<std::mutex> lk(g_mu);

@@ -67,7 +67,7 @@ class hz_tune_report(C.Structure):
                 ("syminv_kpb", C.c_int), ("cached", C.c_int), ("dots_us", C.c_float),
                 ("dots_us_default", C.c_float), ("upd_us", C.c_float),
                 ("upd_us_default", C.c_float), ("apply_us", C.c_float),
-                ("apply_us_default", C.c_float)]
+                ("apply_us_default", C.c_float), ("rowinv_mode", C.c_int)]
 
 
 class hz_server_opts(C.Structure):
@@ -111,6 +111,7 @@ _SIGS = {
     "hz_server_get_stats": (C.c_int, [_vp, C.POINTER(hz_server_stats)]),
     "hz_server_destroy": (C.c_int, [_vp]),
     "hz_plan_autotune": (C.c_int, [_vp, _vp, C.POINTER(hz_tune_report)]),
+    "hz_plan_set_tune": (C.c_int, [_vp, C.POINTER(hz_tune_report)]),
     "hz_profile_enable": (C.c_int, [C.c_int]),
     "hz_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "hz_launch_count": (C.c_ulonglong, []),
@@ -269,6 +270,15 @@ class Plan:
         r = hz_tune_report()
         check(lib.hz_plan_autotune(self._h, _stream(stream), C.byref(r)))
         return {f: getattr(r, f) for f, _ in r._fields_}
+
+    def set_tune(self, **shape) -> None:
+        """Set launch shapes (hz_plan_set_tune); unspecified ones keep the
+        defaults dots_vc=8, dots_bps=2, upd_bps=4, syminv_kpb=1, rowinv_mode=0."""
+        r = hz_tune_report()
+        r.dots_vc, r.dots_bps, r.upd_bps, r.syminv_kpb, r.rowinv_mode = 8, 2, 4, 1, 0
+        for k, v in shape.items():
+            setattr(r, k, int(v))
+        check(lib.hz_plan_set_tune(self._h, C.byref(r)))
 
     def nbytes(self) -> int:
         b = C.c_size_t()

@@ -206,6 +206,33 @@ def test_gmres_3d_matches_oracle(hz, shape):
     assert abs(st[0]["iters"] - sto["iters"]) <= 3, (st[0]["iters"], sto["iters"])
 
 
+@pytest.mark.parametrize("shape", [(64, 32), (128, 128), (48, 192), (8, 2048), (12, 48, 8),
+                                   (24, 16, 32)])
+def test_apply_every_launch_shape(hz, shape):
+    """Every symbol-pass node grouping and both x-inverse forms (fused
+    weighted sum; in place + gather) give the oracle's apply, in both
+    precisions and with two right-hand sides."""
+    p = S.small_problem(shape, 14, M=6, Mt=3, width=2)
+    med_g, med_o = media(hz, p)
+    v = S.random_field(np.random.Generator(np.random.PCG64(15)), shape, 2)
+    ref = np.stack([O.apply_preconditioner(med_o, v[b]) for b in range(2)])
+    for prec, tol in ((0, 1e-10), (1, 5e-5)):
+        plan = hz.Plan(med_g, precision=prec, max_nrhs=2)
+        for kpb, mode in ((1, 1), (1, 2), (2, 2), (4, 1), (4, 2), (2, 0)):
+            plan.set_tune(syminv_kpb=kpb, rowinv_mode=mode)
+            got = plan.apply_preconditioner(_dev(v), precision=prec).cpu().numpy()
+            assert rel(got, ref) <= tol, (prec, kpb, mode, rel(got, ref))
+
+
+def test_set_tune_rejects_out_of_range(hz):
+    p = S.small_problem((16, 16), 3, M=4, Mt=2, width=2)
+    med_g, _ = media(hz, p)
+    plan = hz.Plan(med_g, precision=1)
+    for bad in (dict(syminv_kpb=3), dict(rowinv_mode=3), dict(dots_vc=5), dict(upd_bps=0)):
+        with pytest.raises(hz.HzError):
+            plan.set_tune(**bad)
+
+
 def test_autotune_choices_are_valid_and_cached(hz):
     p = S.bump_problem(128, 43, width=8, ppw=8.0, M=5, Mt=2, nrhs=2)
     med_g, med_o = media(hz, p)
@@ -214,6 +241,7 @@ def test_autotune_choices_are_valid_and_cached(hz):
     assert r["cached"] == 0
     assert r["dots_bps"] in (1, 2, 3, 4) and r["dots_vc"] in (2, 4, 8)
     assert r["upd_bps"] in (2, 4, 6, 8) and r["syminv_kpb"] in (1, 2, 4)
+    assert r["rowinv_mode"] in (0, 1, 2)
     assert 0 < r["dots_us"] <= r["dots_us_default"] * 1.0001
     u, st = plan.solve(np.ascontiguousarray(p.f))
     for b in range(2):

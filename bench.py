@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -49,8 +50,9 @@ ALPHA = 0.1
 WORKLOAD = WORKLOADS["cfg2"][3]
 
 
-def workload_config(p, name="cfg2", nrhs=1):
-    fac, alpha, graphs, label, l2 = WORKLOADS[name]
+def workload_config(p, name="cfg2", nrhs=1, graphs=None):
+    fac, alpha, g_default, label, l2 = WORKLOADS[name]
+    graphs = g_default if graphs is None else graphs
     return {"workload": label, "grid": list(p.shape), "K": p.K, "M": p.M, "Mt": p.Mt,
             "omega": round(p.omega, 4), "restart": p.restart, "tol": p.tol, "nrhs": nrhs,
             "alpha": alpha, "precond": "complex64" if p.precision == 1 else "complex128",
@@ -192,14 +194,14 @@ def run_reference(args, p):
         per_it.append(dt / max(it, 1))
     t_it = float(np.mean(per_it))
     value = 1.0 / (t_it * iters_per_solve)
-    sample = (f"{args.ref_sample} FGMRES(40) Arnoldi steps of the workload per step; solves/s = "
+    sample = (f"{args.ref_sample} (F)GMRES({p.restart}) Arnoldi steps of the workload per step; solves/s = "
               f"1 / (s per step x {iters_per_solve} steps per solve"
               f"{' (oracle full solve)' if med_iters else ' (GPU-measured count)'})")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * t_it * args.ref_sample, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-           "config": workload_config(p),
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(p, args.workload, p.f.shape[0]),
            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": workers,
                             "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
@@ -221,17 +223,19 @@ def apply_model_bytes(p):
     return n * (per + 8)
 
 
-def time_apply(plan, p, stream, reps=30, nbuf=8):
-    """Mean time (us) of one hz_apply_preconditioner (complex64) on one
-    right-hand side, back to back, rotating through nbuf input/output pairs
-    so that the inputs are not L2-resident."""
+def time_apply(plan, p, stream, reps=30):
+    """Mean time (us) of one hz_apply_preconditioner (complex64) on all the
+    workload's right-hand sides at once, back to back, rotating through
+    input/output pairs (>= 256 MB of inputs in all) so that the inputs are
+    not L2-resident."""
     import torch
-    n = p.n
+    n = p.n * p.f.shape[0]
+    nbuf = int(min(8, max(2, -(-(256 << 20) // (16 * n)))))
     g = torch.Generator(device="cuda").manual_seed(7)
     xs = [torch.randn(n, dtype=torch.complex128, device="cuda", generator=g) for _ in range(nbuf)]
     ys = [torch.empty_like(x) for x in xs]
     for i in range(3):
-        plan.apply_preconditioner(xs[i], 1, out=ys[i], stream=stream)
+        plan.apply_preconditioner(xs[i % nbuf], 1, out=ys[i % nbuf], stream=stream)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -285,11 +289,18 @@ def run_gpu(args, p, name):
     from paper_2409_16172_gb300 import hz
 
     fac, alpha, graphs, label, l2 = WORKLOADS[name]
+    if args.graphs >= 0:
+        graphs = bool(args.graphs)
     nrhs = p.f.shape[0]
     med = hz.Medium(p.c, p.zeta, omega=p.omega, M=p.M, Mt=p.Mt, c_o=p.c_o, alpha=alpha)
     plan = hz.Plan(med, precision=p.precision, restart=p.restart, tol=p.tol, maxit=4000,
                    max_nrhs=nrhs, graphs=graphs)
-    tune = plan.autotune() if not args.no_autotune else None
+    tune = None
+    if args.tune:
+        plan.set_tune(**json.loads(args.tune))
+        tune = {"set": json.loads(args.tune)}
+    elif not args.no_autotune:
+        tune = plan.autotune()
     f = torch.from_numpy(np.ascontiguousarray(p.f)).cuda()
     u = torch.zeros_like(f)
     stream = torch.cuda.current_stream()
@@ -333,7 +344,9 @@ def run_gpu(args, p, name):
     if graphs:
         plan_p = hz.Plan(med, precision=p.precision, restart=p.restart, tol=p.tol, maxit=4000,
                          max_nrhs=nrhs, graphs=False)
-        if tune is not None:
+        if args.tune:
+            plan_p.set_tune(**json.loads(args.tune))
+        elif tune is not None:
             plan_p.autotune()  # cached: same shapes as the timed plan
     hz.profile_enable(True)
     hz.profile_read(reset=True)
@@ -392,9 +405,13 @@ def run_gpu(args, p, name):
     precond = None
     if apply_us is not None:
         mb = apply_model_bytes(p)
+        # traffic of the passes as they run: planes only for the (row, node)
+        # or (slab, node) pairs in use
+        masked = pb / n_applies
         precond = {"bound": "hbm", "achieved": mb / apply_us / 1e3, "peak": hbm, "unit": "GB/s",
                    "frac": mb / apply_us / 1e3 / hbm, "traffic": None, "peak_source": hbm_src,
-                   "apply_us": apply_us, "model_bytes": mb,
+                   "apply_us": apply_us, "model_bytes": mb, "masked_bytes": masked,
+                   "masked_frac": masked / apply_us / 1e3 / hbm,
                    "model": "n*[(4+2K)s+4] (2D) or n*[(6+4K)s+4] (3D), s = 8 (complex64), "
                             "plus 8 B/pt for the complex128 output of the public apply",
                    "timing": "CUDA events around 30 back-to-back hz_apply_preconditioner calls, "
@@ -430,8 +447,8 @@ def run_gpu(args, p, name):
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "c64+c128" if p.precision == 1 else "c128", "data": "synthetic",
-           "config": workload_config(p, name, nrhs),
+           "dtype": "f32+f64" if p.precision == 1 else "f64", "data": "synthetic",
+           "config": workload_config(p, name, nrhs, graphs),
            "iters": [s["iters"] for s in stats[0]][:8],
            "rel_true_resid": max(s["rel_true_resid"] for s in stats[0]),
            "all_converged": ok,
@@ -442,6 +459,64 @@ def run_gpu(args, p, name):
            "gpu_launches": launches, "clocks": clocks, "phases": phases, "autotune": tune,
            "fp64_plain": plain,
            "fp64_peak_tflops": fp64_peak, "fp64_probe_tflops": fp64_probe / 1e3}
+    print(json.dumps(out), flush=True)
+
+
+def run_example1(args):
+    """The paper's Example 1 GMRES study (Section 5.1): circular inclusion,
+    a = 20, delta = 1, eta = 1/800, M = 8, PPW = 12, GMRES(10), 100
+    iterations, with the FP64 preconditioner, the complex64 preconditioner
+    (FGMRES) and no preconditioner; residual histories and time per step."""
+    import torch
+    from paper_2409_16172_gb300 import build, synth as S
+    build.build()
+    from paper_2409_16172_gb300 import hz
+    torch.cuda.set_device(0)
+    p = S.example1(args.ex1_n)
+    med = hz.Medium(p.c, p.zeta, p.a, omega=p.omega, M=p.M, Mt=0, c_o=1.0, alpha=0.0,
+                    a_node=p.meta["a_node"])
+    f = torch.from_numpy(np.ascontiguousarray(p.f[0])).cuda()
+    stream = torch.cuda.current_stream()
+    its = 100
+    sampler = ClockSampler(0)
+    sampler.start()
+    runs = {}
+    for key, kw in (("precond_fp64", dict(precision=0)), ("precond_c64", dict(precision=1)),
+                    ("none", dict(precision=0, no_precond=True))):
+        plan = hz.Plan(med, restart=p.restart, tol=1e-14, maxit=its, **kw)
+        plan.autotune()
+        u = torch.zeros_like(f)
+        plan.solve(f, u, stream=stream, history=its)  # warm-up
+        u.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st, H = plan.solve(f, u, stream=stream, history=its)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        h = H[0]
+        runs[key] = {"resid_at_100": float(h[its - 1]), "ms_per_step": ms / its,
+                     "history_every_10": [float(h[i]) for i in range(9, its, 10)],
+                     "rel_true_resid": st[0]["rel_true_resid"]}
+        del plan
+    clocks = sampler.stop()
+    gap = math.log10(runs["none"]["resid_at_100"] / runs["precond_fp64"]["resid_at_100"])
+    out = {"metric": "Example 1 (Section 5.1): orders of magnitude between the unpreconditioned "
+                     "and the preconditioned GMRES(10) relative residual after 100 iterations",
+           "value": gap, "unit": "orders of magnitude", "n_gpus": 1, "steps": its, "warmup": 1,
+           "ms_per_step": runs["precond_fp64"]["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64 (and f32 preconditioner)",
+           "data": "synthetic",
+           "config": {"workload": p.name, "grid": list(p.shape), "omega": p.omega,
+                      "omega_over_pi": p.omega / math.pi, "ppw": 12, "delta": 1.0,
+                      "eta": 1 / 800, "a": 20.0, "M": p.M, "restart": p.restart,
+                      "note": "the paper's N = 2400/3600/4800 need radix-5 transforms, which "
+                              "this build does not have; same PPW, contrast, damping and M at "
+                              "a power-of-two N"},
+           "paper_statement": ">= 7 orders at 100 iterations (N = 2400..4800)",
+           "runs": runs, "clocks": clocks}
     print(json.dumps(out), flush=True)
 
 
@@ -497,7 +572,7 @@ def run_serving(args):
     out = {"metric": METRIC + " (serving stream)", "value": rhs / span, "unit": "solves/s",
            "n_gpus": 1, "steps": len(reqs), "warmup": 2, "ms_per_step": 1e3 * span / len(reqs),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "c64+c128", "data": "synthetic",
+           "dtype": "f32+f64", "data": "synthetic",
            "config": {"workload": f"serving-{len(reqs)}req-poisson{args.rate}/s-slots{args.slots}",
                       "grids": sorted({"x".join(map(str, q.shape)) for q in reqs}),
                       "rhs_total": rhs},
@@ -512,14 +587,19 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["cfg2", "cfg1", "cfg3", "cfg4", "serving"],
+    ap.add_argument("--workload", choices=["cfg2", "cfg1", "cfg3", "cfg4", "serving", "example1"],
                     default="cfg2", help="cfg2 (default): the 2D 1024^2 K=16 workload")
     ap.add_argument("--requests", type=int, default=30, help="serving: number of requests")
+    ap.add_argument("--ex1-n", type=int, default=2048, help="example1: grid side N")
     ap.add_argument("--rate", type=float, default=4.0, help="serving: arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent requests")
     ap.add_argument("--cpu-iters", type=int, default=6, help="Arnoldi steps in the CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--tune", default="",
+                    help='launch shapes as JSON instead of autotuning, e.g. \'{"rowinv_mode": 1}\'')
+    ap.add_argument("--graphs", type=int, default=-1,
+                    help="1/0: force CUDA-graph cycles on/off (default: per workload)")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the plain FP64 one-rhs-at-a-time comparison solve")
     ap.add_argument("--ref-sample", type=int, default=3, help="reference arm: steps per sample")
@@ -530,6 +610,9 @@ def main():
     from paper_2409_16172_gb300 import synth as S
     if args.workload == "serving":
         run_serving(args)
+        return
+    if args.workload == "example1":
+        run_example1(args)
         return
     p = getattr(S, WORKLOADS[args.workload][0])()
     if args.impl == "reference":

@@ -89,13 +89,17 @@ typedef struct {
  *   maxit      cap on the total number of Arnoldi steps.
  *   graphs     1: capture each full Arnoldi cycle once as a CUDA graph and
  *              replay it (worth it for small grids, where launches cost as
- *              much as the kernels); 0: launch step by step.             */
+ *              much as the kernels); 0: launch step by step.
+ *   no_precond 1: plain GMRES(m) on P_N u = f without the preconditioner,
+ *              all in FP64 (the unpreconditioned baseline the paper compares
+ *              against in Section 5); 0: preconditioned by Q_M.         */
 typedef struct {
   int precision;
   int restart;
   double tol;
   int maxit;
   int graphs;
+  int no_precond;
 } hz_solver_opts;
 
 typedef struct {
@@ -168,13 +172,16 @@ typedef struct {
   float apply_us, apply_us_default;   /* whole preconditioner apply        */
   int rowinv_mode;          /* x-inverse pass: 0 by grid size, 1 in place
                                then a gather of the weighted sum, 2 fused  */
+  int col_pair;             /* complex64 symbol pass: 1 two columns per
+                               thread in packed FP32, 0 one column          */
 } hz_tune_report;
 
 hz_status hz_plan_autotune(hz_plan* plan, void* stream, hz_tune_report* report);
 
 /* Sets the plan's launch shapes from a report (e.g. one saved from an
- * earlier hz_plan_autotune): dots_vc in {2, 4, 8}, dots_bps and upd_bps in
- * 1..32, syminv_kpb in {1, 2, 4}, rowinv_mode in {0, 1, 2}; the timing
+ * earlier hz_plan_autotune): dots_vc in {2, 4, 8}, dots_bps in 1..4, upd_bps
+ * in 1..8, syminv_kpb in {1, 2, 4}, rowinv_mode in {0, 1, 2}, col_pair in
+ * {0, 1}; the timing
  * fields are ignored.  HZ_ERR_INVALID_ARG for any other value. */
 hz_status hz_plan_set_tune(hz_plan* plan, const hz_tune_report* report);
 
@@ -228,6 +235,16 @@ hz_status hz_apply_preconditioner_noalloc(const hz_medium* med, const void* x, v
  * (u still holds the last iterate) or HZ_ERR_BREAKDOWN otherwise. */
 hz_status hz_gmres_solve(hz_plan* plan, const void* f, void* u, int nrhs,
                          hz_solve_stats* stats, void* stream);
+
+/* hz_gmres_solve that also returns the residual history: history (host,
+ * nrhs * history_len doubles) receives, for right-hand side b and Arnoldi
+ * step s < history_len (counted across restarts), the Givens estimate of
+ * ||f - P_N u_s|| / ||f|| after that step (the quantity plotted against
+ * the GMRES iteration in Section 5); entries past the last step are NaN.
+ * Runs step by step (opts.graphs is ignored for this call). */
+hz_status hz_gmres_solve_history(hz_plan* plan, const void* f, void* u, int nrhs,
+                                 hz_solve_stats* stats, double* history, int history_len,
+                                 void* stream);
 
 /* ---- serving ----------------------------------------------------------
  * A server queues solve requests and admits them onto the GPU as slots and

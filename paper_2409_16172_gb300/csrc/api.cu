@@ -139,6 +139,10 @@ hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* s
   const AxisTables& tx = m->ax[0];
   const AxisTables& ty = m->ax[1];
   auto tw = [&](const AxisTables& t) -> const void* { return prec == 0 ? (const void*)t.tw64 : (const void*)t.tw32; };
+  // paired (two columns per thread) complex64 symbol pass unless tuned off
+  auto tw2 = [&](const AxisTables& t) -> const void* {
+    return prec == 1 && p->tune.col_pair ? (const void*)t.tw32p : nullptr;
+  };
   auto xi = [&](const AxisTables& t) -> const void* { return prec == 0 ? (const void*)t.xi2_64 : (const void*)t.xi2_32; };
   const void* A = prec == 0 ? (const void*)m->symA64 : (const void*)m->symA32;
   const void* G = prec == 0 ? (const void*)m->symG64 : (const void*)m->symG32;
@@ -163,7 +167,8 @@ hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* s
     PhaseScope ps(st, PH_SYMINV, B * (dn * s + m->rowk_used * nx * s),
                   B * K * (5.0 * dn * l2(ny) + 14.0 * dn));
     HZ_TRY(oy->line_sym_inv(prec, p->tmp, p->planes, nx, 1, nx, 0, n, m->K, nrhs, xi(tx), nullptr,
-                            xi(ty), A, G, m->rowmask, 0, 1, tw(ty), st, active, p->tune.syminv_kpb));
+                            xi(ty), A, G, m->rowmask, 0, 1, tw(ty), tw2(ty), st, active,
+                            p->tune.syminv_kpb));
   } else {
     const FftOps* oz = fft_ops(nz);
     const AxisTables& tz = m->ax[2];
@@ -177,8 +182,8 @@ hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* s
       PhaseScope ps(st, PH_SYMINV, B * (dn * s + m->slabk_used * slab * s),
                     B * K * (5.0 * dn * l2(nz) + 14.0 * dn));
       HZ_TRY(oz->line_sym_inv(prec, p->tmp, p->planes, nx, ny, slab, nx, n, m->K, nrhs, xi(tx),
-                              xi(ty), xi(tz), A, G, m->slabmask, 0, 1, tw(tz), st, active,
-                              p->tune.syminv_kpb));
+                              xi(ty), xi(tz), A, G, m->slabmask, 0, 1, tw(tz), tw2(tz), st,
+                              active, p->tune.syminv_kpb));
     }
     {
       PhaseScope ps(st, PH_LINE, B * 2.0 * s * m->slabk_used * slab,
@@ -222,6 +227,8 @@ extern "C" hz_status hz_plan_create(hz_medium* med, const hz_solver_opts* opts, 
   if (max_nrhs < 1) return set_error(HZ_ERR_INVALID_ARG, "max_nrhs must be >= 1");
   if (opts->precision != 0 && opts->precision != 1)
     return set_error(HZ_ERR_INVALID_ARG, "precision must be 0 or 1");
+  if (opts->no_precond != 0 && opts->no_precond != 1)
+    return set_error(HZ_ERR_INVALID_ARG, "no_precond must be 0 or 1");
   if (opts->restart < 1 || opts->restart > HZ_MAX_RESTART)
     return set_error(HZ_ERR_INVALID_ARG, "restart must be in [1, %d]", HZ_MAX_RESTART);
   if (!(opts->tol > 0) || opts->maxit < 1) return set_error(HZ_ERR_INVALID_ARG, "need tol > 0, maxit >= 1");
@@ -251,6 +258,9 @@ extern "C" hz_status hz_plan_create(hz_medium* med, const hz_solver_opts* opts, 
   p->Z = Z;
   if ((st = p->arena.alloc(&p->u, size_t(B) * n)) != HZ_OK) return fail(st);
   if ((st = p->arena.alloc(&p->f, size_t(B) * n)) != HZ_OK) return fail(st);
+  // block partial sums: the stencil residual (one per block), the CGS2 dot
+  // partials (2 (j+1) nblk doubles per rhs with at most 4 x 152 blocks over
+  // the launch, 8 vectors per chunk) and the update norms (<= 8 x 152 blocks)
   const int nblk = std::max(stencil_blocks(n), krylov_blocks(n, 1, 1));
   p->partial_len = size_t(B) * (m + 2) * std::max(nblk, 1024) * 2;
   if ((st = p->arena.alloc(&p->partial, p->partial_len)) != HZ_OK) return fail(st);

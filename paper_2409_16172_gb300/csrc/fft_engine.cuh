@@ -12,8 +12,9 @@
 // the last stage the line is in natural order (mixed-radix Stockham autosort).
 // Thread t of a line runs butterflies j = t + b TPL, b = 0 .. E/R - 1.
 //
-// Shared memory holds a line padded by one element every PAD_SHIFT elements
-// so that the stride-R writes of the early stages spread over the banks.
+// Shared memory holds a line padded by one element every 16 elements (32 for
+// plans with a radix-32 stage) so that the stride-R writes of the early
+// stages spread over the banks.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -170,6 +171,198 @@ template <int S, typename V> __device__ __forceinline__ void dft32(V* x) {
   }
 }
 
+// Twiddle multiply of the Stockham stages: x * w (forward, S = -1) or
+// x * conj(w) (inverse, S = +1), w = exp(-2 pi i m / N) from the table.
+template <typename V> struct TwiddleOf { using T = V; };
+template <int S, typename V> __device__ __forceinline__ V twiddle_mul(V a, V w) {
+  return S > 0 ? cmulc(a, w) : cmul(a, w);
+}
+
+// ---------------------------------------------------------------------------
+// Paired complex FP32: two independent lines transformed by one thread.  PV
+// holds the real parts of the two lines' values in x and the imaginary parts
+// in y, each an f32x2 pair, so that every butterfly add, subtract and multiply
+// is one packed FP32 instruction (PTX add/sub/mul/fma.rn.f32x2) for both
+// lines.
+// ---------------------------------------------------------------------------
+struct __align__(8) f2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ f2 f2_make(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2_splat(float a) { return f2_make(a, a); }
+__device__ __forceinline__ float f2_lo(f2 p) { return __uint_as_float(unsigned(p.v)); }
+__device__ __forceinline__ float f2_hi(f2 p) { return __uint_as_float(unsigned(p.v >> 32)); }
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {  // a b + c
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+__device__ __forceinline__ f2 neg2(f2 a) { return f2_splat(0.0f) - a; }
+
+struct __align__(16) PV {
+  f2 x, y;
+};
+// twiddles for pairs: (re, re, im, im) of exp(-2 pi i m / N)
+template <> struct TwiddleOf<PV> { using T = float4; };
+__device__ __forceinline__ float4 ld_twiddle(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
+template <int S> __device__ __forceinline__ PV twiddle_mul(PV a, float4 w) {
+  const f2 wr = f2_make(w.x, w.y), wi = f2_make(w.z, w.w);
+  PV r;
+  if constexpr (S > 0) {  // a conj(w)
+    r.x = fma2(a.y, wi, a.x * wr);
+    r.y = a.y * wr - a.x * wi;
+  } else {  // a w
+    r.x = a.x * wr - a.y * wi;
+    r.y = fma2(a.x, wi, a.y * wr);
+  }
+  return r;
+}
+__device__ __forceinline__ PV cmul(PV a, PV b) {
+  PV r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = fma2(a.x, b.y, a.y * b.x);
+  return r;
+}
+__device__ __forceinline__ PV cmulc(PV a, PV b) {  // a conj(b)
+  PV r;
+  r.x = fma2(a.x, b.x, a.y * b.y);
+  r.y = a.y * b.x - a.x * b.y;
+  return r;
+}
+// a (c + i s) for constants c, s
+__device__ __forceinline__ PV cmul_const(PV a, float c, float s) {
+  const f2 C = f2_splat(c), Sv = f2_splat(s), NS = f2_splat(-s);
+  PV r;
+  r.x = fma2(a.y, NS, a.x * C);
+  r.y = fma2(a.x, Sv, a.y * C);
+  return r;
+}
+template <int S> __device__ __forceinline__ PV cmul_si(PV a) {
+  PV r;
+  if constexpr (S > 0) { r.x = neg2(a.y); r.y = a.x; }
+  else { r.x = a.y; r.y = neg2(a.x); }
+  return r;
+}
+// b + S i e and b - S i e without forming S i e
+template <int S> __device__ __forceinline__ PV cadd_si(PV b, PV e) {
+  PV r;
+  if constexpr (S > 0) { r.x = b.x - e.y; r.y = b.y + e.x; }
+  else { r.x = b.x + e.y; r.y = b.y - e.x; }
+  return r;
+}
+template <int S> __device__ __forceinline__ PV csub_si(PV b, PV e) {
+  PV r;
+  if constexpr (S > 0) { r.x = b.x + e.y; r.y = b.y - e.x; }
+  else { r.x = b.x - e.y; r.y = b.y + e.x; }
+  return r;
+}
+
+template <int S> __device__ __forceinline__ void dft3(PV* x) {
+  const float h = 0.86602540378443864676f;  // sin(2 pi / 3)
+  const PV s = cadd(x[1], x[2]), d = csub(x[1], x[2]);
+  const f2 mh = f2_splat(-0.5f);
+  PV t;
+  t.x = fma2(s.x, mh, x[0].x);
+  t.y = fma2(s.y, mh, x[0].y);
+  // e = S i h d:  x1 = t + e, x2 = t - e
+  const f2 pH = f2_splat(float(S) * h), nH = f2_splat(-float(S) * h);
+  x[0] = cadd(x[0], s);
+  PV a, b;
+  a.x = fma2(d.y, nH, t.x);
+  a.y = fma2(d.x, pH, t.y);
+  b.x = fma2(d.y, pH, t.x);
+  b.y = fma2(d.x, nH, t.y);
+  x[1] = a;
+  x[2] = b;
+}
+
+template <int S> __device__ __forceinline__ void dft4(PV* x) {
+  const PV a = cadd(x[0], x[2]), b = csub(x[0], x[2]);
+  const PV c = cadd(x[1], x[3]), e = csub(x[1], x[3]);
+  x[0] = cadd(a, c);
+  x[2] = csub(a, c);
+  x[1] = cadd_si<S>(b, e);
+  x[3] = csub_si<S>(b, e);
+}
+
+template <int S> __device__ __forceinline__ void dft8(PV* x) {
+  const float r2 = 0.70710678118654752440f;
+  PV e[4] = {x[0], x[2], x[4], x[6]};
+  PV o[4] = {x[1], x[3], x[5], x[7]};
+  dft4<S>(e);
+  dft4<S>(o);
+  const f2 R2 = f2_splat(r2), NR2 = f2_splat(-r2);
+  // o1 w8^1 = r2 (o1 + S i o1); o3 w8^3 = r2 (S i o3 - o3)
+  PV o1, o3;
+  if constexpr (S > 0) {
+    o1.x = (o[1].x - o[1].y) * R2;
+    o1.y = (o[1].y + o[1].x) * R2;
+    o3.x = (o[3].x + o[3].y) * NR2;
+    o3.y = (o[3].x - o[3].y) * R2;
+  } else {
+    o1.x = (o[1].x + o[1].y) * R2;
+    o1.y = (o[1].y - o[1].x) * R2;
+    o3.x = (o[3].y - o[3].x) * R2;
+    o3.y = (o[3].x + o[3].y) * NR2;
+  }
+  x[0] = cadd(e[0], o[0]); x[4] = csub(e[0], o[0]);
+  x[1] = cadd(e[1], o1);   x[5] = csub(e[1], o1);
+  x[2] = cadd_si<S>(e[2], o[2]); x[6] = csub_si<S>(e[2], o[2]);
+  x[3] = cadd(e[3], o3);   x[7] = csub(e[3], o3);
+}
+
+template <int S> __device__ __forceinline__ PV w16mul(PV a, int m) {
+  const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f;
+  const float r2 = 0.70710678118654752440f;
+  switch (m) {
+    case 0: return a;
+    case 1: return cmul_const(a, c1, float(S) * s1);
+    case 2: return cmul_const(a, r2, float(S) * r2);
+    case 3: return cmul_const(a, s1, float(S) * c1);
+    case 4: return cmul_si<S>(a);
+    case 6: return cmul_const(a, -r2, float(S) * r2);
+    case 9: return cmul_const(a, -c1, -float(S) * s1);
+    default: return a;  // not reached for the 4x4 split
+  }
+}
+
+template <int S> __device__ __forceinline__ PV w32mul(PV a, int k) {
+  constexpr double C[9] = {1.0,
+                           0.980785280403230449126182, 0.923879532511286756128183,
+                           0.831469612302545237078788, 0.707106781186547524400844,
+                           0.555570233019602224742831, 0.382683432365089771728460,
+                           0.195090322016128267848285, 0.0};
+  if (k == 0) return a;
+  if (k == 8) return cmul_si<S>(a);
+  if (k < 8) return cmul_const(a, float(C[k]), float(S) * float(C[8 - k]));
+  // w^k = S i w^(k-8): (c + i S s) S i = -s' + i S c' with c' = C[k-8], s' = C[16-k]
+  return cmul_const(a, -float(C[16 - k]), float(S) * float(C[k - 8]));
+}
+
 template <int RAD, int S, typename V> __device__ __forceinline__ void dftR(V* x) {
   if constexpr (RAD == 2) dft2<S>(x);
   else if constexpr (RAD == 3) dft3<S>(x);
@@ -252,20 +445,32 @@ HZ_DPLAN(256)
 #undef HZ_PLAN_T
 
 constexpr int PAD_SHIFT = 4;
-__host__ __device__ constexpr int padded(int i) { return i + (i >> PAD_SHIFT); }
+// shared-memory elements of one padded line (enough for either padding)
 __host__ __device__ constexpr int padded_len(int n) { return n + (n >> PAD_SHIFT) + 1; }
 
 // LS: distance in elements between consecutive positions of a line in shared
 // memory (1 for a private line, TB when TB lines are interleaved).
 // WS: the threads of a line lie in one warp (TPL <= 32 and lines laid out
 // warp by warp), so the stage barriers are warp barriers.
-template <typename R, int N, int S, int LS = 1, bool WS = false, typename PL = FftPlan<N>>
+template <typename R, int N, int S, int LS = 1, bool WS = false, typename PL = FftPlan<N>,
+          typename VT = typename cvec<R>::T>
 struct LineFFT {
-  using V = typename cvec<R>::T;
+  using V = VT;                        // one complex value, or a pair (PV)
+  using TW = typename TwiddleOf<V>::T;  // twiddle table entry
   using P = PL;
   static constexpr int E = P::E;
   static constexpr int TPL = N / E;
   static constexpr int R0 = P::rad(0);
+  // shared-memory padding: one element per 16, or per 32 for plans with a
+  // radix-32 stage, whose stride-32 writes would otherwise put every eighth
+  // lane on the same banks (padded_len(N) covers both)
+  static constexpr int max_rad() {
+    int m = 0;
+    for (int s = 0; s < P::NST; ++s) m = P::rad(s) > m ? P::rad(s) : m;
+    return m;
+  }
+  static constexpr int PS = max_rad() >= 32 ? 5 : PAD_SHIFT;
+  __device__ static __forceinline__ int pad(int i) { return i + (i >> PS); }
   static_assert(!WS || TPL <= 32, "warp-synchronous lines need TPL <= 32");
 
   // lanes of the warp that exist: a block smaller than a warp holds lanes
@@ -286,11 +491,11 @@ struct LineFFT {
 
   __device__ static __forceinline__ void load_stage0(const V* line, int t, V (&x)[E]) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = line[padded(stage0_index(t, e)) * LS];
+    for (int e = 0; e < E; ++e) x[e] = line[pad(stage0_index(t, e)) * LS];
   }
 
   template <int STAGE, int NS, bool KEEP>
-  __device__ static __forceinline__ void stage(V* line, int t, V (&x)[E], const V* __restrict__ tw) {
+  __device__ static __forceinline__ void stage(V* line, int t, V (&x)[E], const TW* __restrict__ tw) {
     if constexpr (STAGE < P::NST) {
       constexpr int RAD = P::rad(STAGE);
       if constexpr (STAGE > 0) {
@@ -298,7 +503,7 @@ struct LineFFT {
         for (int b = 0; b < E / RAD; ++b) {
           const int j = t + b * TPL;
 #pragma unroll
-          for (int r = 0; r < RAD; ++r) x[b * RAD + r] = line[padded(j + r * (N / RAD)) * LS];
+          for (int r = 0; r < RAD; ++r) x[b * RAD + r] = line[pad(j + r * (N / RAD)) * LS];
         }
         sync();
       }
@@ -309,16 +514,14 @@ struct LineFFT {
         if constexpr (NS > 1) {
 #pragma unroll
           for (int r = 1; r < RAD; ++r) {
-            V w = ld_twiddle(&tw[r * k * (N / (NS * RAD))]);
-            if constexpr (S > 0) w.y = -w.y;
-            x[b * RAD + r] = cmul(x[b * RAD + r], w);
+            x[b * RAD + r] = twiddle_mul<S>(x[b * RAD + r], ld_twiddle(&tw[r * k * (N / (NS * RAD))]));
           }
         }
         dftR<RAD, S>(&x[b * RAD]);
         if constexpr (!(KEEP && STAGE == P::NST - 1)) {
           const int d = (j / NS) * NS * RAD + k;
 #pragma unroll
-          for (int r = 0; r < RAD; ++r) line[padded(d + r * NS) * LS] = x[b * RAD + r];
+          for (int r = 0; r < RAD; ++r) line[pad(d + r * NS) * LS] = x[b * RAD + r];
         }
       }
       if constexpr (!(KEEP && STAGE == P::NST - 1)) sync();
@@ -330,7 +533,7 @@ struct LineFFT {
   // thread of the line has finished reading it (the caller syncs).  On exit
   // the line holds the result in natural order and the line's threads (the
   // block, unless WS) are synchronised.  tw[i] = exp(-2 pi i * i / N) for i < N.
-  __device__ static __forceinline__ void run(V* line, int t, V (&x)[E], const V* __restrict__ tw) {
+  __device__ static __forceinline__ void run(V* line, int t, V (&x)[E], const TW* __restrict__ tw) {
     stage<0, 1, false>(line, t, x, tw);
   }
 
@@ -342,7 +545,7 @@ struct LineFFT {
   __device__ static __forceinline__ int out_index(int t, int e) {
     return t + (e / RL) * TPL + (e % RL) * (N / RL);
   }
-  __device__ static __forceinline__ void run_regs(V* line, int t, V (&x)[E], const V* __restrict__ tw) {
+  __device__ static __forceinline__ void run_regs(V* line, int t, V (&x)[E], const TW* __restrict__ tw) {
     stage<0, 1, true>(line, t, x, tw);
   }
 };

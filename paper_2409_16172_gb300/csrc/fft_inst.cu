@@ -2,6 +2,7 @@
 // exposes them as an FftOps table.  The build compiles this file once per
 // supported length, in parallel.
 #include <algorithm>
+#include <type_traits>
 
 #include "fft_kernels.cuh"
 
@@ -27,11 +28,19 @@ hz_status row_fwd_t(const double2* in, const double* scale, long rows_per_rhs, l
                     const void* tw, void* out, cudaStream_t st, const int* active) {
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
-  // blocks of ROW_LINES lines, or one warp per block when that leaves the
-  // GPU under-filled (small grids)
+  // blocks of ROW_LINES lines, or one line per block when that leaves the
+  // GPU under-filled (few rows)
   const bool small = (nrows + C::ROW_LINES - 1) / C::ROW_LINES < 2L * 152;
-  const int lines = small ? C::ROW_LINES_SMALL : C::ROW_LINES;
-  auto k = small ? row_fwd_kernel<R, N, C::ROW_LINES_SMALL> : row_fwd_kernel<R, N, C::ROW_LINES>;
+  if (small) {
+    auto k = row_fwd_kernel<R, N, 1>;
+    HZ_TRY(smem_attr(k, C::row_smem(1)));
+    k<<<unsigned(nrows), C::TPL_ROW, C::row_smem(1), st>>>(
+        in, scale, rows_per_rhs, nrows, static_cast<const V*>(tw), static_cast<V*>(out), active);
+    HZ_CUDA(cudaGetLastError());
+    return HZ_OK;
+  }
+  constexpr int lines = C::ROW_LINES;
+  auto k = row_fwd_kernel<R, N, C::ROW_LINES>;
   HZ_TRY(smem_attr(k, C::row_smem(lines)));
   const long blocks = (nrows + lines - 1) / lines;
   k<<<unsigned(blocks), lines * C::TPL_ROW, C::row_smem(lines), st>>>(
@@ -53,7 +62,8 @@ hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segta
                         const int* active, int mode) {
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
-  const bool small = (nrows + C::ROW_LINES - 1) / C::ROW_LINES < 2L * 152;
+  // fewer blocks of ROW_LINES rows than SMs: few rows
+  const bool small = (nrows + C::ROW_LINES - 1) / C::ROW_LINES < 152L;
   if (mode == 1 || (mode == 0 && small)) {
     // few rows: (row, node) lines in parallel, in place, then the gather
     auto ki = row_inv_inplace_kernel<R, N, C::ROW_LINES>;
@@ -130,11 +140,28 @@ hz_status line_sym_inv_t(const void* vhat, void* planes, int nx, long outer, lon
                          long n, int K, int batch, const void* xi2_x, const void* xi2_o,
                          const void* xi2_l, const void* symA, const void* symG,
                          const unsigned long long* smask, long smO, long smS, const void* tw,
-                         cudaStream_t st, const int* active, int kpb) {
+                         const void* tw2, cudaStream_t st, const int* active, int kpb) {
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
   // nodes per block: 1, 2 or 4
   kpb = kpb >= 4 ? 4 : (kpb >= 2 ? 2 : 1);
+  if constexpr (std::is_same<R, float>::value) {
+    if (tw2 && nx % 2 == 0) {
+      auto k = kpb == 4 ? line_sym_inv_pair_kernel<N, 4>
+                        : (kpb == 2 ? line_sym_inv_pair_kernel<N, 2> : line_sym_inv_pair_kernel<N, 1>);
+      HZ_TRY(smem_attr(k, C::col_pair_smem()));
+      const int ntile = (nx / 2 + C::TB - 1) / C::TB;
+      dim3 grid(unsigned(ntile * outer), unsigned((K + kpb - 1) / kpb), unsigned(batch));
+      k<<<grid, C::COL_THREADS, C::col_pair_smem(), st>>>(
+          static_cast<const float2*>(vhat), static_cast<float2*>(planes), nx, ntile, S, ostride,
+          n, K, static_cast<const float*>(xi2_x), static_cast<const float*>(xi2_o),
+          static_cast<const float*>(xi2_l), static_cast<const float2*>(symA),
+          static_cast<const float2*>(symG), smask, smO, smS, static_cast<const float4*>(tw2),
+          active);
+      HZ_CUDA(cudaGetLastError());
+      return HZ_OK;
+    }
+  }
   auto k = kpb == 4 ? line_sym_inv_kernel<R, N, 4>
                     : (kpb == 2 ? line_sym_inv_kernel<R, N, 2> : line_sym_inv_kernel<R, N, 1>);
   HZ_TRY(smem_attr(k, C::col_smem()));
@@ -153,12 +180,14 @@ hz_status line_sym_inv(int prec, const void* vhat, void* planes, int nx, long ou
                        long ostride, long n, int K, int batch, const void* xi2_x,
                        const void* xi2_o, const void* xi2_l, const void* symA, const void* symG,
                        const unsigned long long* smask, long smO, long smS, const void* tw,
-                       cudaStream_t st, const int* active, int kpb) {
+                       const void* tw2, cudaStream_t st, const int* active, int kpb) {
   return prec == 0
              ? line_sym_inv_t<double>(vhat, planes, nx, outer, S, ostride, n, K, batch, xi2_x,
-                                      xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, st, active, kpb)
+                                      xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, nullptr, st,
+                                      active, kpb)
              : line_sym_inv_t<float>(vhat, planes, nx, outer, S, ostride, n, K, batch, xi2_x,
-                                     xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, st, active, kpb);
+                                     xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, tw2, st,
+                                     active, kpb);
 }
 
 const FftOps ops = {N, row_fwd, row_inv_acc, line_pass, line_sym_inv};

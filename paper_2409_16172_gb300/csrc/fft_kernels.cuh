@@ -46,9 +46,6 @@ template <typename R, int N> struct LineCfg {
   }
   static constexpr int TB = tb_calc();
   static constexpr int COL_THREADS = TB * TPL;
-  // one line per block (TPL_ROW threads, possibly less than a warp) when
-  // there are too few rows to fill the GPU with ROW_LINES-line blocks
-  static constexpr int ROW_LINES_SMALL = 1;
   static constexpr size_t row_smem(int lines = ROW_LINES) { return size_t(lines) * padded_len(N) * VB; }
   // row_inv_acc: padded work lines, then (16-byte aligned for cp.async) two
   // unpadded staging rows per line
@@ -57,6 +54,7 @@ template <typename R, int N> struct LineCfg {
     return stage_offset(lines) + size_t(lines) * 2 * N * VB;
   }
   static constexpr size_t col_smem() { return size_t(TB) * padded_len(N) * VB; }
+  static constexpr size_t col_pair_smem() { return size_t(TB) * padded_len(N) * 16; }
 };
 
 // 16-byte asynchronous global -> shared copies (L2 only), in groups.
@@ -89,15 +87,14 @@ __device__ __forceinline__ float recip(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-// FP64: the MUFU approximation refined by two Newton-Raphson steps for 1/x,
-// r <- r + r (1 - x r), each of which doubles the number of correct bits.
+// FP64: the MUFU approximation refined by three Newton-Raphson steps for
+// 1/x, r <- r + r (1 - x r), each of which doubles the number of correct bits.
 __device__ __forceinline__ double recip(double x) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+#pragma unroll
+  for (int it = 0; it < 3; ++it) r = fma(r, fma(-x, r, 1.0), r);
+  return r;
 }
 
 template <typename R> struct RecT;
@@ -342,7 +339,7 @@ weighted_gather_kernel(const typename cvec<R>::T* __restrict__ planes,
 // Strided-axis kernels.  A line has N elements at stride S; a block handles
 // TB lines at adjacent x (thread = t * TB + column), so that loads and stores
 // move TB contiguous elements, and keeps them interleaved in shared memory
-// (position p of column col at padded(p) * TB + col).  Line (x, o, b) starts
+// (position p of column col at pad(p) * TB + col).  Line (x, o, b) starts
 // at b * bstride + o * ostride + x; grid.x = ceil(nx / TB) * outer.
 // ---------------------------------------------------------------------------
 template <typename R, int N, int SIGN>
@@ -450,6 +447,92 @@ line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         if ((mb[(e * KPB) / 32] >> ((e * KPB) % 32 + kk)) & 1u) dst[F::out_index(t, e) * int(S)] = v[e];
+      }
+    }
+  }
+}
+
+
+// The complex64 symbol pass with two adjacent columns per thread (x, x + 1;
+// nx even), their values paired in f32x2 registers (PV): the same arithmetic
+// per column as line_sym_inv_kernel, in packed FP32 instructions, 16-byte
+// global accesses, and tw2 = the (re, re, im, im) twiddle table.
+template <int N, int KPB>
+__global__ void __launch_bounds__(LineCfg<float, N>::COL_THREADS, KPB == 1 ? 2 : 1)
+line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ planes, int nx,
+                         int ntile, long S, long ostride, long n, int K,
+                         const float* __restrict__ xi2_x, const float* __restrict__ xi2_o,
+                         const float* __restrict__ xi2_l, const float2* __restrict__ symA,
+                         const float2* __restrict__ symG,
+                         const unsigned long long* __restrict__ smask, long smO, long smS,
+                         const float4* __restrict__ tw2, const int* __restrict__ active) {
+  constexpr int TB = LineCfg<float, N>::TB;
+  using F = LineFFT<float, N, +1, TB, false, typename LineCfg<float, N>::CP, PV>;
+  constexpr int E = F::E;
+  static_assert(KPB == 1 || KPB == 2 || KPB == 4, "nodes per block");
+  if (active && !active[blockIdx.z]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PV* sm = reinterpret_cast<PV*>(smem_raw);
+  const int col = threadIdx.x % TB, t = threadIdx.x / TB;
+  const int tile = blockIdx.x % ntile;
+  const long o = blockIdx.x / ntile;
+  const int k0 = blockIdx.y * KPB;
+  const int k1 = min(K, k0 + KPB);
+  const long rhs = blockIdx.z;
+  const int x = 2 * (tile * TB + col);
+  const bool valid = x < nx;
+  const long off = o * ostride + x;
+  const float2* src = vhat + rhs * n + off;
+  const float so = xi2_o ? xi2_o[o] : 0.0f;
+  const float sx0 = (valid ? xi2_x[x] : 0.0f) + so, sx1 = (valid ? xi2_x[x + 1] : 0.0f) + so;
+  PV spec[E];
+  f2 s2[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int p = F::stage0_index(t, e);
+    const float4 a = valid ? *reinterpret_cast<const float4*>(src + long(p) * S)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+    spec[e].x = f2_make(a.x, a.z);
+    spec[e].y = f2_make(a.y, a.w);
+    const float xl = xi2_l[p];
+    s2[e] = f2_make(sx0 + xl, sx1 + xl);
+  }
+  constexpr int MW = (E * KPB + 31) / 32;
+  uint32_t mb[MW];
+#pragma unroll
+  for (int w = 0; w < MW; ++w) mb[w] = 0u;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const long p = F::out_index(t, e);
+    const uint32_t bits = uint32_t(smask[o * smO + p * smS] >> k0) & ((1u << KPB) - 1u);
+    mb[(e * KPB) / 32] |= bits << ((e * KPB) % 32);
+  }
+#pragma unroll 1
+  for (int k = k0; k < k1; ++k) {
+    const float2 A = symA[k], G = symG[k];
+    const f2 AX = f2_splat(A.x), AY = f2_splat(A.y), NGX = f2_splat(-G.x), NGY = f2_splat(-G.y);
+    const int kk = k - k0;
+    PV v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      // vhat q_k = vhat conj(den) / |den|^2,  den = A - G |xi|^2
+      PV den;
+      den.x = fma2(NGX, s2[e], AX);
+      den.y = fma2(NGY, s2[e], AY);
+      const f2 nrm = fma2(den.x, den.x, den.y * den.y);
+      const f2 inv = f2_make(recip(f2_lo(nrm)), recip(f2_hi(nrm)));
+      const PV q = cmulc(spec[e], den);
+      v[e].x = q.x * inv;
+      v[e].y = q.y * inv;
+    }
+    F::run_regs(sm + col, t, v, tw2);
+    if (valid) {
+      float2* dst = planes + (rhs * K + k) * n + off;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        if ((mb[(e * KPB) / 32] >> ((e * KPB) % 32 + kk)) & 1u)
+          *reinterpret_cast<float4*>(dst + F::out_index(t, e) * int(S)) =
+              make_float4(f2_lo(v[e].x), f2_lo(v[e].y), f2_hi(v[e].x), f2_hi(v[e].y));
       }
     }
   }

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <limits>
 #include <complex>
 #include <vector>
 
@@ -61,6 +62,7 @@ hz_status solve_ws_create(hz_plan* p) {
   A(w->ar.alloc(&ks.sn, size_t(B) * m));
   A(w->ar.alloc(&ks.g, size_t(B) * (m + 1)));
   A(w->ar.alloc(&ks.est, B));
+  A(w->ar.alloc(&ks.hist, size_t(B) * m));
   A(w->ar.alloc(&ks.bnorm, B));
   A(w->ar.alloc(&ks.jend, B));
   A(w->ar.alloc(&ks.active, B));
@@ -102,8 +104,9 @@ void solve_ws_destroy(hz_plan* p) {
 
 }  // namespace hz
 
-extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs,
-                                    hz_solve_stats* stats, void* stream) {
+namespace {
+hz_status gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs, hz_solve_stats* stats,
+                      double* history, int hlen, void* stream) {
   if (!plan || !f_in || !u_io) return set_error(HZ_ERR_INVALID_ARG, "null argument");
   if (nrhs < 1 || nrhs > plan->max_nrhs) return set_error(HZ_ERR_INVALID_ARG, "nrhs out of range");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -156,6 +159,9 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
   std::vector<double> h_sigma0(B, 0.0);
   std::vector<double2> h_g(size_t(nrhs) * (m + 1)), h_H(size_t(nrhs) * m * (m + 1)), h_y(size_t(B) * m);
   std::vector<double> h_est(nrhs);
+  const bool noq = p->opts.no_precond != 0;
+  std::vector<double> h_hist(history ? size_t(nrhs) * m : 0);
+  std::vector<std::vector<double>> hist_b(history ? nrhs : 0);
   int total_iters = 0;
 
   for (;;) {
@@ -213,7 +219,16 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
       const double* sig_j = ks.sigma + long(j) * B;
       const double stb = Bn * ((prec == 1 ? 8.0 : 16.0) + 32.0 + (med->a ? 8.0 : 0.0));
       const double stf = Bn * (med->dim == 3 ? 30.0 : 26.0);
-      if (prec == 1) {
+      if (noq) {
+        // unpreconditioned: w = P_N (sigma_j V_j)
+        double2* zt = static_cast<double2*>(p->Z);
+        {
+          PhaseScope ps(st, PH_SOLUPD, 32.0 * Bn, 2.0 * Bn);
+          HZ_TRY(launch_scale_copy(Vj, sig_j, zt, n, nrhs, ks.active, st));
+        }
+        PhaseScope ps(st, PH_STENCIL, stb, stf);
+        HZ_TRY(launch_stencil(med, 0, zt, n, Vn, n, nrhs, ks.active, st));
+      } else if (prec == 1) {
         float2* Zj = static_cast<float2*>(p->Z) + long(j) * ldb * n;
         HZ_TRY(precond_apply(p, 1, Vj, sig_j, nrhs, Zj, 0, st, ks.active));
         PhaseScope ps(st, PH_STENCIL, stb, stf);
@@ -241,7 +256,7 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
       HZ_TRY(launch_givens(ks, j, nrhs, st));
       return HZ_OK;
     };
-    if (p->opts.graphs && jmax == m) {
+    if (p->opts.graphs && jmax == m && !history) {
       // The whole cycle as one CUDA graph, captured once per plan and right-
       // hand-side count and replayed; steps after a right-hand side retires
       // return at once on its device-side flag.
@@ -296,6 +311,9 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
     HZ_CUDA(cudaMemcpyAsync(h_est.data(), ks.est, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
     HZ_CUDA(cudaMemcpyAsync(h_H.data(), ks.H, h_H.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
     HZ_CUDA(cudaMemcpyAsync(h_g.data(), ks.g, h_g.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    if (history)
+      HZ_CUDA(cudaMemcpyAsync(h_hist.data(), ks.hist, h_hist.size() * sizeof(double),
+                              cudaMemcpyDeviceToHost, st));
     HZ_CUDA(cudaStreamSynchronize(st));
 
     // back substitution R y = g on the host (m <= 128)
@@ -306,6 +324,8 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
       const int J = h_jend[b];
       jn[b] = J;
       iters[b] += J;
+      if (history)
+        for (int i = 0; i < J; ++i) hist_b[b].push_back(h_hist[size_t(b) * m + i]);
       restarts[b] += 1;
       est[b] = h_est[b] / bnorm[b];
       if (h_status[b] != HZ_OK) {
@@ -331,9 +351,15 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
     HZ_CUDA(cudaMemcpyAsync(d_jn, jn.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
     HZ_CUDA(cudaMemcpyAsync(w.y, h_y.data(), size_t(nrhs) * m * sizeof(double2), cudaMemcpyHostToDevice, st));
     const int Jmax = *std::max_element(jn.begin(), jn.end());
-    if (prec == 1) {
+    if (prec == 1 && !noq) {
       PhaseScope ps(st, PH_SOLUPD, Bn * (8.0 * Jmax + 32.0), Bn * 8.0 * Jmax);
       HZ_TRY(launch_solution_update(1, p->Z, ldb, u, n, n, nrhs, w.y, m, d_jn, st));
+    } else if (noq) {
+      // u += V (sigma y)
+      double2* t = p->V + long(m) * ldb * n;
+      PhaseScope ps(st, PH_SOLUPD, Bn * (16.0 * Jmax + 64.0), Bn * (8.0 * Jmax + 2.0));
+      HZ_TRY(launch_combine(p->V, ldb, t, n, n, nrhs, w.y, m, ks.sigma, B, d_jn, st));
+      HZ_TRY(launch_axpy(u, t, n, n, nrhs, d_jn, st));
     } else {
       // t = V (sigma y), then u += Q_M t in complex128
       double2* t = p->V + long(m) * ldb * n;  // V_m is free once the cycle is over
@@ -371,6 +397,25 @@ extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io,
     }
   }
   (void)total_iters;
+  if (history) {
+    for (int b = 0; b < nrhs; ++b)
+      for (int s = 0; s < hlen; ++s)
+        history[size_t(b) * hlen + s] =
+            s < int(hist_b[b].size()) ? hist_b[b][s] : std::numeric_limits<double>::quiet_NaN();
+  }
   if (ret != HZ_OK) set_error(ret, "%s", ret == HZ_ERR_BREAKDOWN ? "Krylov breakdown (NaN/Inf)" : "not converged within maxit");
   return ret;
+}
+}  // namespace
+
+extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs,
+                                    hz_solve_stats* stats, void* stream) {
+  return gmres_solve(plan, f_in, u_io, nrhs, stats, nullptr, 0, stream);
+}
+
+extern "C" hz_status hz_gmres_solve_history(hz_plan* plan, const void* f_in, void* u_io, int nrhs,
+                                            hz_solve_stats* stats, double* history,
+                                            int history_len, void* stream) {
+  if (!history || history_len < 1) return set_error(HZ_ERR_INVALID_ARG, "history buffer required");
+  return gmres_solve(plan, f_in, u_io, nrhs, stats, history, history_len, stream);
 }

@@ -68,6 +68,7 @@ struct AxisTables {
   int N = 0;
   double2* tw64 = nullptr;  // exp(-2 pi i j / N)
   float2* tw32 = nullptr;
+  float4* tw32p = nullptr;  // (re, re, im, im) of tw32, for paired lines
   double* xi2_64 = nullptr;  // squared wavenumber per bin
   float* xi2_32 = nullptr;
 };
@@ -88,7 +89,7 @@ struct hz_medium {
   std::vector<uchar2> segtab_h;
   // device data
   hz::DevArena arena;
-  double2* gamma2 = nullptr;        // per point gamma^2 (Eqn. Complex_wave_speed squared)
+  double2* gamma2 = nullptr;        // per point gamma^2 / h_x^2 (Eqn. Complex_wave_speed squared)
   double* a = nullptr;              // per point operator damping (NULL when a == 0)
   double* rec64 = nullptr;          // per point segment + t (complex128 path)
   uint32_t* rec32 = nullptr;        // per point segment:8 | t:24 (complex64 path)
@@ -129,13 +130,15 @@ struct FftOps {
                          long ostride, long bstride, int batch,
                          const unsigned long long* omask, int K, const void* tw,
                          cudaStream_t st, const int* active, int per_rhs);
-  // last axis: symbol multiply of the spectrum and inverse FFT, one plane per k
+  // last axis: symbol multiply of the spectrum and inverse FFT, one plane per k;
+  // tw2 (complex64 only, nullable): the paired twiddle table, selects the
+  // two-columns-per-thread kernel when nx is even
   hz_status (*line_sym_inv)(int prec, const void* vhat, void* planes, int nx, long outer, long S,
                             long ostride, long n, int K, int batch, const void* xi2_x,
                             const void* xi2_o, const void* xi2_l, const void* symA,
                             const void* symG, const unsigned long long* smask, long smO,
-                            long smS, const void* tw, cudaStream_t st, const int* active,
-                            int kpb);
+                            long smS, const void* tw, const void* tw2, cudaStream_t st,
+                            const int* active, int kpb);
 };
 
 const FftOps* fft_ops(int N);
@@ -172,6 +175,7 @@ struct Tune {
   int upd_bps = 4;
   int syminv_kpb = 1;
   int rowinv_mode = 0;  // FftOps::row_inv_acc mode
+  int col_pair = 1;     // complex64 symbol pass: two columns per thread
 };
 }
 

@@ -18,6 +18,7 @@ struct KsDev {
   double2* sn;      // [b][m] rotation sines
   double2* g;       // [b][m+1] rotated right-hand side
   double* est;      // [b] |g_{j+1}|
+  double* hist;     // [b][m] est / ||f|| after each step of the cycle
   double* bnorm;    // [b] ||f||
   int* jend;        // [b] columns built in this cycle
   int* active;      // [b] 1 while the cycle continues
@@ -65,6 +66,8 @@ hz_status launch_solution_update(int zprec, const void* Z, long ldb, double2* u,
 hz_status launch_combine(const double2* V, long ldb, double2* out, long ostride, long n, int nrhs,
                          const double2* y, int ldy, const double* sigma, int ldsig, const int* jn,
                          cudaStream_t st);
+hz_status launch_scale_copy(const double2* V, const double* sigma, double2* out, long n, int nrhs,
+                           const int* active, cudaStream_t st);
 hz_status launch_axpy(double2* u, const double2* t, long stride, long n, int nrhs, const int* jn,
                       cudaStream_t st);
 hz_status launch_norm2(const double2* x, long stride, long n, int nrhs, double* partial, int nblk,

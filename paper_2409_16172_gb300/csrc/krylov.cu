@@ -239,6 +239,28 @@ __device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
 __device__ __forceinline__ double2 cfma_d(double2 a, double2 b, double2 c) {  // a b + c
   return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
+// 1/sqrt(x) for x > 0: the MUFU approximation refined by three Newton-Raphson
+// steps y <- y + y (1 - x y^2) / 2 (each doubles the correct bits).  The
+// Givens kernel runs in one warp, where every FP64 instruction holds the
+// sub-partition's FP64 unit for ~64 cycles; this takes fewer of them than a
+// square root followed by a division.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+#pragma unroll
+  for (int it = 0; it < 3; ++it) {
+    const double e = fma(-x * y, y, 1.0);
+    y = fma(0.5 * y, e, y);
+  }
+  return y;
+}
+// max(|a|, |b|) of finite doubles as an integer max of the magnitude bits
+// (IEEE order of non-negative doubles is that of their bit patterns), off the
+// FP64 pipe
+__device__ __forceinline__ long long absbits(double a) {
+  return __double_as_longlong(a) & 0x7fffffffffffffffLL;
+}
+
 __device__ __forceinline__ double2 shfl_up_d2(double2 v, int o) {
   return make_double2(__shfl_up_sync(0xffffffffu, v.x, o), __shfl_up_sync(0xffffffffu, v.y, o));
 }
@@ -263,19 +285,20 @@ __global__ void givens_kernel(KsDev ks, int j, int nrhs) {
   double* cs = ks.cs + long(b) * m;
   double2* sn = ks.sn + long(b) * m;
   double2* g = ks.g + long(b) * (m + 1);
-  double hmax = 0.0;
+  long long hbits = 0;  // bits of max |Re h|, |Im h|
   bool bad = false;
   for (int i = lane; i <= j; i += 32) {
     const double s = ks.sigma[long(i) * ks.ldsig + b];
     const double2 h = make_double2(s * (S1[i].x + S2[i].x), s * (S1[i].y + S2[i].y));
     col[i] = h;
-    hmax = fmax(hmax, fmax(fabs(h.x), fabs(h.y)));
+    hbits = max(hbits, max(absbits(h.x), absbits(h.y)));
     bad |= !isfinite(h.x) || !isfinite(h.y);
   }
-  const double hn = sqrt(ks.nrm2[b]);
+  const double hn2 = ks.nrm2[b];  // |w|^2 after orthogonalisation
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) hmax = fmax(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
-  bad = __any_sync(0xffffffffu, bad) || !isfinite(hn);
+  for (int o = 16; o > 0; o >>= 1) hbits = max(hbits, __shfl_xor_sync(0xffffffffu, hbits, o));
+  const double hmax = __longlong_as_double(hbits);
+  bad = __any_sync(0xffffffffu, bad) || !isfinite(hn2);
   __syncwarp();
   // chunk of maps i in [i0, i1) of this lane; composite F(x) = A x + B
   const int per = (j + 31) / 32;
@@ -314,21 +337,28 @@ __global__ void givens_kernel(KsDev ks, int j, int nrhs) {
   const double2 a = make_double2(__shfl_sync(0xffffffffu, xall.x, 31), __shfl_sync(0xffffffffu, xall.y, 31));
   __syncwarp();
   if (lane == 0) {
+    // h_{j+1,j} = hn = |w|; sigma_{j+1} = 1 / hn normalises the next vector
+    const double inv_hn = hn2 > 0.0 ? rsqrt_nr(hn2) : 0.0;
+    const double hn = hn2 * inv_hn;
     const bool happy = hn <= 1e-14 * hmax;
-    ks.sigma[long(j + 1) * ks.ldsig + b] = (hn > 0.0 && !happy) ? 1.0 / hn : 0.0;
-    const double aa = hypot(a.x, a.y);
+    ks.sigma[long(j + 1) * ks.ldsig + b] = (hn > 0.0 && !happy) ? inv_hn : 0.0;
+    const double aa2 = fma(a.x, a.x, a.y * a.y);
     double c;
     double2 s, r;
     if (hn == 0.0) {
       c = 1.0; s = make_double2(0.0, 0.0); r = a;
-    } else if (aa == 0.0) {
+    } else if (aa2 == 0.0) {
       c = 0.0; s = make_double2(1.0, 0.0); r = make_double2(hn, 0.0);
     } else {
-      const double rho = hypot(aa, hn);
-      const double inv_aa = 1.0 / aa, inv_rho = 1.0 / rho;
+      // rho = sqrt(|a|^2 + hn^2); c = |a| / rho; s = (a / |a|) hn / rho;
+      // r = (a / |a|) rho
+      const double rho2 = aa2 + hn2;
+      const double inv_aa = rsqrt_nr(aa2), inv_rho = rsqrt_nr(rho2);
+      const double aa = aa2 * inv_aa, rho = rho2 * inv_rho;
       c = aa * inv_rho;
       const double2 ph = make_double2(a.x * inv_aa, a.y * inv_aa);
-      s = make_double2(ph.x * hn * inv_rho, ph.y * hn * inv_rho);  // ph conj(hn) / rho
+      const double hr = hn * inv_rho;
+      s = make_double2(ph.x * hr, ph.y * hr);  // ph conj(hn) / rho
       r = make_double2(ph.x * rho, ph.y * rho);
     }
     cs[j] = c;
@@ -339,8 +369,10 @@ __global__ void givens_kernel(KsDev ks, int j, int nrhs) {
     const double2 gn = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
     g[j + 1] = gn;  // -conj(s) g_j
     g[j] = make_double2(c * gj.x, c * gj.y);
-    const double est = hypot(gn.x, gn.y);
+    const double gn2 = fma(gn.x, gn.x, gn.y * gn.y);
+    const double est = gn2 > 0.0 ? gn2 * rsqrt_nr(gn2) : 0.0;
     ks.est[b] = est;
+    ks.hist[long(b) * m + j] = est / ks.bnorm[b];
     ks.jend[b] = j + 1;
     bad |= !isfinite(est) || !isfinite(r.x) || !isfinite(r.y);
     int act = 1;
@@ -423,6 +455,18 @@ __global__ void axpy_kernel(double2* __restrict__ u, const double2* __restrict__
   }
 }
 
+// out[b] = sigma[b] V[b]: the operator input of an unpreconditioned step
+__global__ void scale_copy_kernel(const double2* __restrict__ V, const double* __restrict__ sigma,
+                                  double2* __restrict__ out, long n, const int* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  const double s = sigma[b];
+  for (long p = long(blockIdx.x) * KT + threadIdx.x; p < n; p += long(gridDim.x) * KT) {
+    const double2 v = V[b * n + p];
+    out[b * n + p] = make_double2(s * v.x, s * v.y);
+  }
+}
+
 // |x|^2 partials of nrhs vectors
 __global__ void __launch_bounds__(KT)
 norm2_kernel(const double2* __restrict__ x, long stride, long n, double* __restrict__ partial) {
@@ -439,22 +483,20 @@ norm2_kernel(const double2* __restrict__ x, long stride, long n, double* __restr
 
 }  // namespace
 
+// Blocks per right-hand side of the element-wise FP64 kernels: bps blocks
+// per SM over the whole launch, but at least one point per thread.  Short
+// vectors thus still spread over every SM: an FP64 warp instruction holds a
+// sub-partition's FP64 unit for ~64 cycles, so a few long-running warps
+// would serialise the work.
 int krylov_blocks_bps(long n, int nrhs, int nchunk, int bps) {
   long per = (long(bps) * 152 + long(nrhs) * nchunk - 1) / (long(nrhs) * nchunk);
-  long maxb = (n + 4L * KT - 1) / (4L * KT);
+  long maxb = (n + KT - 1) / KT;
   if (per > maxb) per = maxb;
   if (per < 1) per = 1;
   return int(per);
 }
 
-int krylov_blocks(long n, int nrhs, int nchunk) {
-  // aim at ~4 blocks per SM over the whole launch, >= 4 points per thread
-  long per = (4L * 152 + long(nrhs) * nchunk - 1) / (long(nrhs) * nchunk);
-  long maxb = (n + 4L * KT - 1) / (4L * KT);
-  if (per > maxb) per = maxb;
-  if (per < 1) per = 1;
-  return int(per);
-}
+int krylov_blocks(long n, int nrhs, int nchunk) { return krylov_blocks_bps(n, nrhs, nchunk, 4); }
 
 hz_status launch_dots(const double2* V, long ldb, const double2* w, long wstride, long n, int j,
                       int nrhs, const int* active, double2* partial, const Tune& tn, double2* S,
@@ -522,6 +564,14 @@ hz_status launch_combine(const double2* V, long ldb, double2* out, long ostride,
                          cudaStream_t st) {
   const int nblk = krylov_blocks(n, nrhs, 1);
   combine_kernel<<<dim3(nblk, nrhs), KT, 0, st>>>(V, ldb, out, ostride, n, y, ldy, sigma, ldsig, jn);
+  HZ_CUDA(cudaGetLastError());
+  return HZ_OK;
+}
+
+hz_status launch_scale_copy(const double2* V, const double* sigma, double2* out, long n, int nrhs,
+                           const int* active, cudaStream_t st) {
+  const int nblk = krylov_blocks(n, nrhs, 1);
+  scale_copy_kernel<<<dim3(nblk, nrhs), KT, 0, st>>>(V, sigma, out, n, active);
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }

@@ -76,7 +76,7 @@ struct NodeDev {
 __global__ void record_kernel(const double* __restrict__ c, const double* __restrict__ zeta,
                               long n, int nx, NodeDev nd, double* __restrict__ rec64,
                               uint32_t* __restrict__ rec32, double2* __restrict__ gamma2,
-                              unsigned long long* __restrict__ rowmask) {
+                              double ih2x, unsigned long long* __restrict__ rowmask) {
   const long i = blockIdx.x * long(blockDim.x) + threadIdx.x;
   unsigned long long bits = 0ull;
   long row = -1;
@@ -106,8 +106,9 @@ __global__ void record_kernel(const double* __restrict__ c, const double* __rest
     const uchar2 kk = nd.seg[seg];
     if (t < 1.0) bits |= 1ull << kk.x;
     if (t > 0.0) bits |= 1ull << kk.y;
+    // gamma^2 = c^2 (1 - i zeta)^2, stored times 1 / h_x^2 for the stencil
     const double c2 = ci * ci;
-    gamma2[i] = make_double2(c2 * (1.0 - zi * zi), -2.0 * c2 * zi);
+    gamma2[i] = make_double2(c2 * (1.0 - zi * zi) * ih2x, -2.0 * c2 * zi * ih2x);
     row = i / nx;
   }
   // OR the bits of the warp's points that share a row, then one atomic each
@@ -370,8 +371,9 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
   if (st != HZ_OK) return fail(st);
   ce = cudaMemsetAsync(m->rowmask, 0, nrows * sizeof(unsigned long long), cs);
   if (ce != cudaSuccess) return fail(cuda_error(ce, "memset"));
+  const double hx = m->L / m->nx;
   record_kernel<<<unsigned((n + 255) / 256), 256, 0, cs>>>(dc, dz, n, m->nx, nd, m->rec64, m->rec32,
-                                                          m->gamma2, m->rowmask);
+                                                          m->gamma2, 1.0 / (hx * hx), m->rowmask);
   slab_kernel<<<(m->nz + 127) / 128, 128, 0, cs>>>(m->rowmask, m->ny, m->nz, m->slabmask);
   count_launches(2);
   ce = cudaGetLastError();
@@ -415,15 +417,18 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
     twiddles(N, tw);
     xi2_table(N, m->L, interp->symbol_kind, xi);
     std::vector<float2> twf(N);
+    std::vector<float4> twp(N);
     std::vector<float> xif(N);
     for (int j = 0; j < N; ++j) {
       twf[j] = make_float2(float(tw[j].x), float(tw[j].y));
+      twp[j] = make_float4(twf[j].x, twf[j].x, twf[j].y, twf[j].y);
       xif[j] = float(xi[j]);
     }
     AxisTables& t = m->ax[d];
     t.N = N;
     if ((st = upload(m->arena, &t.tw64, tw, cs)) != HZ_OK) return fail(st);
     if ((st = upload(m->arena, &t.tw32, twf, cs)) != HZ_OK) return fail(st);
+    if ((st = upload(m->arena, &t.tw32p, twp, cs)) != HZ_OK) return fail(st);
     if ((st = upload(m->arena, &t.xi2_64, xi, cs)) != HZ_OK) return fail(st);
     if ((st = upload(m->arena, &t.xi2_32, xif, cs)) != HZ_OK) return fail(st);
     const double h = m->L / N;

@@ -31,11 +31,16 @@ __device__ __forceinline__ double2 ld2(const float2* p, long i) {
   return make_double2(f2d_bits(v.x), f2d_bits(v.y));
 }
 
+// The stencil in the form that takes the fewest FP64 instructions per point
+// (the FP64 pipe is this kernel's limit): with g = gamma^2 / h_x^2 (stored
+// so by the medium), rho_a = h_x^2 / h_a^2 and diag = 2 sum_a rho_a,
+//   (P x)_j = g_j [ (x_{j-ex} + x_{j+ex}) + rho_y (x_{j-ey} + x_{j+ey})
+//                  (+ rho_z (...)) - diag x_j ] + (omega^2 + i omega a_j) x_j.
 template <typename InT, bool RESID>
 __global__ void __launch_bounds__(ST_THREADS)
 stencil_kernel(const InT* __restrict__ x, double2* __restrict__ y, const double2* __restrict__ f,
-               const double2* __restrict__ gamma2, const double* __restrict__ a, double omega,
-               double ih2x, double ih2y, double ih2z, int nx, int ny, int nz, long n,
+               const double2* __restrict__ gs, const double* __restrict__ a, double omega,
+               double w2, double rho_y, double rho_z, double diag, int nx, int ny, int nz, long n,
                long in_stride, long out_stride, const int* __restrict__ active,
                double* __restrict__ partial) {
   const int b = blockIdx.y;
@@ -59,23 +64,20 @@ stencil_kernel(const InT* __restrict__ x, double2* __restrict__ y, const double2
       const long yu = iy == ny - 1 ? i - sy * (ny - 1) : i + sy;
       const double2 c = ld2(xb, i);
       const double2 vxl = ld2(xb, xl), vxr = ld2(xb, xr), vyd = ld2(xb, yd), vyu = ld2(xb, yu);
-      double sr = ih2x * (vxl.x + vxr.x) + ih2y * (vyd.x + vyu.x);
-      double si = ih2x * (vxl.y + vxr.y) + ih2y * (vyd.y + vyu.y);
-      double diag = 2.0 * (ih2x + ih2y);
+      double sr = fma(rho_y, vyd.x + vyu.x, vxl.x + vxr.x);
+      double si = fma(rho_y, vyd.y + vyu.y, vxl.y + vxr.y);
       if (nz > 1) {
         const long sz = long(nx) * ny;
         const long zd = iz == 0 ? i + sz * (nz - 1) : i - sz;
         const long zu = iz == nz - 1 ? i - sz * (nz - 1) : i + sz;
         const double2 vzd = ld2(xb, zd), vzu = ld2(xb, zu);
-        sr += ih2z * (vzd.x + vzu.x);
-        si += ih2z * (vzd.y + vzu.y);
-        diag += 2.0 * ih2z;
+        sr = fma(rho_z, vzd.x + vzu.x, sr);
+        si = fma(rho_z, vzd.y + vzu.y, si);
       }
-      sr -= diag * c.x;
-      si -= diag * c.y;
-      const double2 g = gamma2[i];
-      const double w2 = omega * omega;
-      // gamma^2 * lap + (w^2 + i w a) x
+      sr = fma(-diag, c.x, sr);
+      si = fma(-diag, c.y, si);
+      const double2 g = gs[i];
+      // g * lap + (w^2 + i w a) x
       double yr = fma(g.x, sr, fma(-g.y, si, w2 * c.x));
       double yi = fma(g.x, si, fma(g.y, sr, w2 * c.y));
       if (a) {
@@ -109,19 +111,33 @@ stencil_kernel(const InT* __restrict__ x, double2* __restrict__ y, const double2
 
 int stencil_blocks(long n) { return int((n + ST_THREADS - 1) / ST_THREADS); }
 
+namespace {
+struct StencilConsts {
+  double w2, rho_y, rho_z, diag;
+};
+StencilConsts stencil_consts(const hz_medium* m) {
+  StencilConsts k;
+  k.w2 = m->omega * m->omega;
+  k.rho_y = m->inv_h2[1] / m->inv_h2[0];
+  k.rho_z = m->dim == 3 ? m->inv_h2[2] / m->inv_h2[0] : 0.0;
+  k.diag = 2.0 * (1.0 + k.rho_y + k.rho_z);
+  return k;
+}
+}  // namespace
+
 hz_status launch_stencil(const hz_medium* m, int in_prec, const void* x, long in_stride,
                          double2* y, long out_stride, int nrhs, const int* active,
                          cudaStream_t st) {
   dim3 grid(unsigned(stencil_blocks(m->n)), unsigned(nrhs));
-  const double ih2z = m->dim == 3 ? m->inv_h2[2] : 0.0;
+  const StencilConsts k = stencil_consts(m);
   if (in_prec == 0)
     stencil_kernel<double2, false><<<grid, ST_THREADS, 0, st>>>(
-        static_cast<const double2*>(x), y, nullptr, m->gamma2, m->a, m->omega, m->inv_h2[0],
-        m->inv_h2[1], ih2z, m->nx, m->ny, m->nz, m->n, in_stride, out_stride, active, nullptr);
+        static_cast<const double2*>(x), y, nullptr, m->gamma2, m->a, m->omega, k.w2, k.rho_y,
+        k.rho_z, k.diag, m->nx, m->ny, m->nz, m->n, in_stride, out_stride, active, nullptr);
   else
     stencil_kernel<float2, false><<<grid, ST_THREADS, 0, st>>>(
-        static_cast<const float2*>(x), y, nullptr, m->gamma2, m->a, m->omega, m->inv_h2[0],
-        m->inv_h2[1], ih2z, m->nx, m->ny, m->nz, m->n, in_stride, out_stride, active, nullptr);
+        static_cast<const float2*>(x), y, nullptr, m->gamma2, m->a, m->omega, k.w2, k.rho_y,
+        k.rho_z, k.diag, m->nx, m->ny, m->nz, m->n, in_stride, out_stride, active, nullptr);
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
@@ -130,9 +146,9 @@ hz_status launch_residual(const hz_medium* m, const double2* u, const double2* f
                           long stride, int nrhs, const int* active, double* partial,
                           cudaStream_t st) {
   dim3 grid(unsigned(stencil_blocks(m->n)), unsigned(nrhs));
-  const double ih2z = m->dim == 3 ? m->inv_h2[2] : 0.0;
+  const StencilConsts k = stencil_consts(m);
   stencil_kernel<double2, true><<<grid, ST_THREADS, 0, st>>>(
-      u, r, f, m->gamma2, m->a, m->omega, m->inv_h2[0], m->inv_h2[1], ih2z, m->nx, m->ny, m->nz,
+      u, r, f, m->gamma2, m->a, m->omega, k.w2, k.rho_y, k.rho_z, k.diag, m->nx, m->ny, m->nz,
       m->n, stride, stride, active, partial);
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;

@@ -6,7 +6,8 @@
 //                     {(8, 1), (8, 2), (4, 2), (4, 3), (2, 2), (2, 4)}
 //   CGS2 update       blocks per SM {2, 4, 6, 8}
 //   symbol pass       nodes per block {1, 2, 4} (the spectrum is read once
-//                     per block; fewer, longer blocks)
+//                     per block; fewer, longer blocks), one or two columns
+//                     per thread (complex64)
 //   x-inverse pass    fused weighted sum, or in place + gather
 // Timing uses CUDA events on the caller's stream around 3 repetitions of
 // each candidate at the middle Arnoldi step of a cycle.
@@ -68,16 +69,18 @@ struct Timer {
 
 extern "C" hz_status hz_plan_set_tune(hz_plan* plan, const hz_tune_report* r) {
   if (!plan || !r) return set_error(HZ_ERR_INVALID_ARG, "null argument");
+  // the plan's partial-sum buffer is sized for these ranges
   const bool ok = (r->dots_vc == 2 || r->dots_vc == 4 || r->dots_vc == 8) && r->dots_bps >= 1 &&
-                  r->dots_bps <= 32 && r->upd_bps >= 1 && r->upd_bps <= 32 &&
+                  r->dots_bps <= 4 && r->upd_bps >= 1 && r->upd_bps <= 8 &&
                   (r->syminv_kpb == 1 || r->syminv_kpb == 2 || r->syminv_kpb == 4) &&
-                  r->rowinv_mode >= 0 && r->rowinv_mode <= 2;
+                  r->rowinv_mode >= 0 && r->rowinv_mode <= 2 && (r->col_pair == 0 || r->col_pair == 1);
   if (!ok) return set_error(HZ_ERR_INVALID_ARG, "launch shape out of range");
   plan->tune.dots_vc = r->dots_vc;
   plan->tune.dots_bps = r->dots_bps;
   plan->tune.upd_bps = r->upd_bps;
   plan->tune.syminv_kpb = r->syminv_kpb;
   plan->tune.rowinv_mode = r->rowinv_mode;
+  plan->tune.col_pair = r->col_pair;
   return HZ_OK;
 }
 
@@ -96,6 +99,7 @@ extern "C" hz_status hz_plan_autotune(hz_plan* plan, void* stream, hz_tune_repor
         rep->upd_bps = plan->tune.upd_bps;
         rep->syminv_kpb = plan->tune.syminv_kpb;
         rep->rowinv_mode = plan->tune.rowinv_mode;
+        rep->col_pair = plan->tune.col_pair;
         rep->cached = 1;
       }
       return HZ_OK;
@@ -171,17 +175,22 @@ extern "C" hz_status hz_plan_autotune(hz_plan* plan, void* stream, hz_tune_repor
   tbest = 1e30f;
   const int prec = p->opts.precision;
   void* out = p->Z;
-  for (int kpb : {1, 2, 4}) {
-    if (kpb > 1 && kpb > med->K) break;
-    p->tune = best;
-    p->tune.syminv_kpb = kpb;
-    const float ms = tm.best_ms([&] {
-      return precond_apply(p, prec, p->V, nullptr, B, out, prec == 1 ? 0 : 1, st, nullptr);
-    });
-    if (kpb == def.syminv_kpb) tdef = ms;
-    if (ms < tbest) {
-      tbest = ms;
-      best.syminv_kpb = kpb;
+  for (int pair : {1, 0}) {
+    if (pair == 0 && prec == 0) continue;  // FP64 has one form
+    for (int kpb : {1, 2, 4}) {
+      if (kpb > 1 && kpb > med->K) break;
+      p->tune = best;
+      p->tune.syminv_kpb = kpb;
+      p->tune.col_pair = pair;
+      const float ms = tm.best_ms([&] {
+        return precond_apply(p, prec, p->V, nullptr, B, out, prec == 1 ? 0 : 1, st, nullptr);
+      });
+      if (kpb == def.syminv_kpb && pair == def.col_pair) tdef = ms;
+      if (ms < tbest) {
+        tbest = ms;
+        best.syminv_kpb = kpb;
+        best.col_pair = pair;
+      }
     }
   }
   // x-inverse pass: fused weighted sum vs in place + gather (grids with
@@ -206,6 +215,7 @@ extern "C" hz_status hz_plan_autotune(hz_plan* plan, void* stream, hz_tune_repor
   r.upd_bps = best.upd_bps;
   r.syminv_kpb = best.syminv_kpb;
   r.rowinv_mode = best.rowinv_mode;
+  r.col_pair = best.col_pair;
   r.cached = 0;
   {
     std::lock_guard<std::mutex> lk(g_mu);

@@ -46,7 +46,7 @@ class hz_interp(C.Structure):
 
 class hz_solver_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("restart", C.c_int), ("tol", C.c_double),
-                ("maxit", C.c_int), ("graphs", C.c_int)]
+                ("maxit", C.c_int), ("graphs", C.c_int), ("no_precond", C.c_int)]
 
 
 class hz_solve_stats(C.Structure):
@@ -67,7 +67,8 @@ class hz_tune_report(C.Structure):
                 ("syminv_kpb", C.c_int), ("cached", C.c_int), ("dots_us", C.c_float),
                 ("dots_us_default", C.c_float), ("upd_us", C.c_float),
                 ("upd_us_default", C.c_float), ("apply_us", C.c_float),
-                ("apply_us_default", C.c_float), ("rowinv_mode", C.c_int)]
+                ("apply_us_default", C.c_float), ("rowinv_mode", C.c_int),
+                ("col_pair", C.c_int)]
 
 
 class hz_server_opts(C.Structure):
@@ -101,6 +102,8 @@ _SIGS = {
     "hz_apply_operator": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
     "hz_apply_preconditioner": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
     "hz_gmres_solve": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(hz_solve_stats), _vp]),
+    "hz_gmres_solve_history": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(hz_solve_stats),
+                                         C.POINTER(C.c_double), C.c_int, _vp]),
     "hz_apply_preconditioner_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
     "hz_request_footprint": (C.c_size_t, [C.POINTER(hz_grid), C.POINTER(hz_interp),
                                           C.POINTER(hz_solver_opts), C.c_int, C.c_int]),
@@ -253,10 +256,12 @@ class Plan:
     """Workspace for applying and solving on one medium."""
 
     def __init__(self, medium: Medium, *, precision: int = 1, restart: int = 40,
-                 tol: float = 1e-6, maxit: int = 4000, max_nrhs: int = 1, graphs: bool = False):
+                 tol: float = 1e-6, maxit: int = 4000, max_nrhs: int = 1, graphs: bool = False,
+                 no_precond: bool = False):
         self.medium = medium
         self.max_nrhs = max_nrhs
-        self.opts = hz_solver_opts(precision, restart, tol, maxit, 1 if graphs else 0)
+        self.opts = hz_solver_opts(precision, restart, tol, maxit, 1 if graphs else 0,
+                                   1 if no_precond else 0)
         h = _vp()
         check(lib.hz_plan_create(medium.handle, C.byref(self.opts), max_nrhs, C.byref(h)))
         self._h = h
@@ -273,9 +278,11 @@ class Plan:
 
     def set_tune(self, **shape) -> None:
         """Set launch shapes (hz_plan_set_tune); unspecified ones keep the
-        defaults dots_vc=8, dots_bps=2, upd_bps=4, syminv_kpb=1, rowinv_mode=0."""
+        defaults dots_vc=8, dots_bps=2, upd_bps=4, syminv_kpb=1, rowinv_mode=0,
+        col_pair=1."""
         r = hz_tune_report()
         r.dots_vc, r.dots_bps, r.upd_bps, r.syminv_kpb, r.rowinv_mode = 8, 2, 4, 1, 0
+        r.col_pair = 1
         for k, v in shape.items():
             setattr(r, k, int(v))
         check(lib.hz_plan_set_tune(self._h, C.byref(r)))
@@ -305,9 +312,12 @@ class Plan:
                                           precision, _stream(stream)))
         return out
 
-    def solve(self, f, u=None, stream=None, raise_on_fail: bool = False):
+    def solve(self, f, u=None, stream=None, raise_on_fail: bool = False, history: int = 0):
         """Solve P u = f.  f, u: complex128 CUDA tensors or numpy arrays
-        (host buffers are staged by the library).  Returns (u, [stats])."""
+        (host buffers are staged by the library).  Returns (u, [stats]), or
+        with history > 0 (u, [stats], H): H[b, s] is the estimated relative
+        residual after Arnoldi step s (hz_gmres_solve_history), NaN past the
+        last step."""
         import torch
         if isinstance(f, torch.Tensor):
             _check_dev(f, "f")
@@ -323,9 +333,17 @@ class Plan:
                 raise TypeError("u must be a contiguous complex128 numpy array")
             fp, up = _vp(f.ctypes.data), _vp(u.ctypes.data)
         stats = (hz_solve_stats * nrhs)()
-        st = lib.hz_gmres_solve(self._h, fp, up, nrhs, stats, _stream(stream))
+        if history > 0:
+            H = np.empty((nrhs, int(history)), np.float64)
+            st = lib.hz_gmres_solve_history(self._h, fp, up, nrhs, stats,
+                                            H.ctypes.data_as(C.POINTER(C.c_double)),
+                                            int(history), _stream(stream))
+        else:
+            st = lib.hz_gmres_solve(self._h, fp, up, nrhs, stats, _stream(stream))
         ok = (HZ_OK,) if raise_on_fail else (HZ_OK, 4, 5)
         check(st, ok)
+        if history > 0:
+            return u, [s.as_dict() for s in stats], H
         return u, [s.as_dict() for s in stats]
 
     def close(self):
@@ -349,7 +367,7 @@ def _grid_of(shape, L=1.0):
 def request_footprint(shape, M, Mt, precision=1, restart=40, nrhs=1, has_a=False) -> int:
     g = _grid_of(tuple(shape))
     it = hz_interp(M, Mt, 1.0, 0.0, 0.15, 0.0, 0)
-    o = hz_solver_opts(precision, restart, 1e-6, 4000, 0)
+    o = hz_solver_opts(precision, restart, 1e-6, 4000, 0, 0)
     return int(lib.hz_request_footprint(C.byref(g), C.byref(it), C.byref(o), nrhs, 1 if has_a else 0))
 
 
@@ -381,7 +399,7 @@ class Server:
         r.a = _dptr(a)
         r.omega = omega
         r.interp = hz_interp(M, Mt, c_o, zeta_max, alpha, a_node, symbol_kind)
-        r.opts = hz_solver_opts(precision, restart, tol, maxit, 1 if graphs else 0)
+        r.opts = hz_solver_opts(precision, restart, tol, maxit, 1 if graphs else 0, 0)
         r.nrhs = nrhs
         r.f = _vp(f.ctypes.data)
         t = C.c_uint64()

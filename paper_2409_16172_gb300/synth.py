@@ -269,6 +269,26 @@ def serving_request(rng, grids=SERVING_GRIDS, max_rhs: int = 8) -> Problem:
                    1e-6, 1, width, meta=dict(ppw=ppw))
 
 
+def example1(N: int = 2048, *, ppw: float = 12.0, delta: float = 1.0, eta: float = 1.0 / 800,
+             a: float = 20.0, M: int = 8, restart: int = 10) -> Problem:
+    """The paper's Example 1 (Section 5.1): periodic unit square, circular
+    inclusion c = c_o + delta H_eta(0.05 - |x|) with c_o = 1 (Eqn. WS),
+    constant damping a, plane-wave source exp(i omega x_1 / c_o) along the
+    x axis (Eqn. Source), omega from PPW = 2 pi c_o N / (L omega), M real
+    nodes and no absorbing layer, GMRES(restart).  The symbol uses the
+    operator's damping (a_node = a, alpha = 0 for the medium)."""
+    shape = (N, N)
+    X = coords(shape)
+    r = np.sqrt(X[0] ** 2 + X[1] ** 2)
+    c = np.broadcast_to(1.0 + delta * smooth_heaviside(0.05 - r, eta), shape).copy()
+    omega = 2.0 * np.pi * 1.0 * N / ppw
+    f = np.exp(1j * omega * np.broadcast_to(X[1], shape))[None].astype(np.complex128)
+    return Problem(f"example1-{N}-ppw{ppw:g}-delta{delta:g}-a{a:g}-M{M}", shape, c,
+                   np.zeros(shape), np.full(shape, float(a)), omega, 1.0, M, 0, f, restart,
+                   1e-14, 0, 0, meta={"a_node": float(a), "alpha": 0.0, "eta": eta,
+                                      "delta": delta, "ppw": ppw})
+
+
 def random_field(rng, shape, nrhs: int | None = None) -> np.ndarray:
     """Complex Gaussian test vector(s) with i.i.d. N(0,1) parts."""
     s = tuple(shape) if nrhs is None else (nrhs,) + tuple(shape)

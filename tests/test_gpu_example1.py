@@ -1,0 +1,79 @@
+"""The paper's Example 1 (Section 5.1) on the GPU: residual histories of
+preconditioned and unpreconditioned GMRES(10) through the C ABI
+(hz_gmres_solve_history, opts.no_precond), step by step against the oracle's
+GMRES on the same (deterministic) recipe, at a size the oracle runs in seconds."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2409_16172_gb300 import synth as S
+
+from gpu_util import hz_module
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hz():
+    import torch
+    assert torch.cuda.is_available()
+    return hz_module()
+
+
+def _media(hz, p):
+    med_o = O.make_medium(p.c, p.zeta, p.a, p.omega, p.M, 0, 1.0, None, 0.0, p.meta["a_node"])
+    med_g = hz.Medium(p.c, p.zeta, p.a, omega=p.omega, M=p.M, Mt=0, c_o=1.0, alpha=0.0,
+                      a_node=p.meta["a_node"])
+    return med_o, med_g
+
+
+@pytest.mark.parametrize("no_precond", [False, True])
+def test_residual_history_matches_oracle(hz, no_precond):
+    p = S.example1(128)
+    med_o, med_g = _media(hz, p)
+    plan = hz.Plan(med_g, precision=0, restart=10, tol=1e-14, maxit=100, no_precond=no_precond)
+    u, st, H = plan.solve(np.ascontiguousarray(p.f[0]), history=120)
+    assert st[0]["iters"] == 100 and not st[0]["converged"]
+    h = H[0]
+    assert np.all(np.isfinite(h[:100])) and np.all(np.isnan(h[100:]))
+    A = lambda x: O.apply_operator(med_o, x)
+    Q = None if no_precond else (lambda v: O.apply_preconditioner(med_o, v))
+    uo, so = O.gmres(A, p.f[0], Q, restart=10, tol=1e-14, maxit=100, record_history=True)
+    ho = np.asarray(so["history"])
+    r_gpu = np.linalg.norm(p.f[0] - A(u)) / np.linalg.norm(p.f[0])
+    if no_precond:
+        # stable: step by step, and the returned iterate's true residual
+        np.testing.assert_allclose(h[:100], ho, rtol=1e-6)
+        assert abs(r_gpu - so["rel_true_resid"]) <= 1e-6 * so["rel_true_resid"]
+    else:
+        # Restarted, preconditioned GMRES(10) on this problem amplifies
+        # rounding differences: the oracle's own history moves by 4e-6 at
+        # step 40 and by 13% at step 49 when f is perturbed by 1e-13
+        # (relative).  So: the first three cycles step by step, the rest
+        # within the spread such runs show.
+        np.testing.assert_allclose(h[:30], ho[:30], rtol=1e-6)
+        assert np.all(np.abs(np.log10(h[:100] / ho)) <= 0.2)
+        assert abs(np.log10(r_gpu / so["rel_true_resid"])) <= 0.2
+
+
+def test_preconditioning_gap_and_mixed_precision(hz):
+    """Preconditioned GMRES(10) ends 100 iterations orders of magnitude below
+    the unpreconditioned run; the complex64 preconditioner inside FGMRES
+    follows the FP64 history over the first cycle and ends within the spread
+    that restarted runs of this problem show (see above)."""
+    p = S.example1(256)
+    _, med_g = _media(hz, p)
+    f = np.ascontiguousarray(p.f[0])
+    hs = {}
+    for key, kw in (("fp64", dict(precision=0)), ("c64", dict(precision=1)),
+                    ("none", dict(precision=0, no_precond=True))):
+        plan = hz.Plan(med_g, restart=10, tol=1e-14, maxit=100, **kw)
+        _, _, H = plan.solve(f, history=100)
+        hs[key] = H[0]
+    for key in ("fp64", "c64"):
+        gap = math.log10(hs["none"][99] / hs[key][99])
+        assert gap >= 3.5, (key, gap)
+    assert np.all(np.abs(np.log10(hs["c64"][:10] / hs["fp64"][:10])) <= 0.01)
+    assert abs(math.log10(hs["c64"][99] / hs["fp64"][99])) <= 1.0

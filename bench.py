@@ -37,13 +37,13 @@ METRIC = "Helmholtz solves/s at 1e-6 true relative residual"
 
 # name -> (problem factory, alpha, graphs, workload label, L2 note)
 WORKLOADS = {
-    "cfg2": ("config2", 0.1, False, "2d-1024x1024-bumps20+gradient-layer32-ppw8-K16-fgmres40-c64",
+    "cfg2": ("config2", 0.1, True, "2d-1024x1024-bumps20+gradient-layer32-ppw8-K16-fgmres40-c64",
              "working set larger than L2 (basis 0.7 GB, planes 134 MB); no flush"),
     "cfg1": ("config1", 0.15, True, "2d-128x128-bumps3-layer16-ppw10-K8-gmres30-fp64",
              "L2-resident (17 MB working set); timed as repeated solves, not an HBM figure"),
     "cfg3": ("config3", 0.15, False, "3d-256^3-layers6+incl10-layer24-ppw8-K16-fgmres40-c64",
              "working set larger than L2 (basis 11 GB); no flush"),
-    "cfg4": ("config4", 0.15, False, "2d-512x512-bumps3-layer16-ppw10-K12-64rhs-fgmres40-c64",
+    "cfg4": ("config4", 0.15, True, "2d-512x512-bumps3-layer16-ppw10-K12-64rhs-fgmres40-c64",
              "working set larger than L2 (basis 11 GB for 64 rhs); no flush"),
 }
 ALPHA = 0.1
@@ -292,7 +292,8 @@ def run_gpu(args, p, name):
     if args.graphs >= 0:
         graphs = bool(args.graphs)
     nrhs = p.f.shape[0]
-    med = hz.Medium(p.c, p.zeta, omega=p.omega, M=p.M, Mt=p.Mt, c_o=p.c_o, alpha=alpha)
+    med = hz.Medium(p.c, p.zeta, omega=p.omega, M=p.M, Mt=p.Mt, c_o=p.c_o, alpha=alpha,
+                    symbol_kind=args.symbol_kind)
     plan = hz.Plan(med, precision=p.precision, restart=p.restart, tol=p.tol, maxit=4000,
                    max_nrhs=nrhs, graphs=graphs)
     tune = None
@@ -386,6 +387,10 @@ def run_gpu(args, p, name):
         achieved = d["flops"] / d["ms"] / 1e9  # TFLOP/s
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                "traffic_note": "per-launch DRAM bytes vary with the Arnoldi step j (the launches "
+                                "averaged here run j = 0..39); one ncu capture at 1024^2, j = 12: "
+                                "190 MB read + write per dot launch against 218 MB algorithmic "
+                                "(profiles/kernels_2d1024_K16_ncu_full.md)",
                 "peak_source": f"FP64: {FP64_DFMA_PER_CLK_PER_SM} DFMA/clk/SM x 2 flops x "
                                f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz "
                                f"(in-library FMA probe {fp64_probe / 1e3:.3f} TFLOP/s)",
@@ -448,7 +453,7 @@ def run_gpu(args, p, name):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64" if p.precision == 1 else "f64", "data": "synthetic",
-           "config": workload_config(p, name, nrhs, graphs),
+           "config": dict(workload_config(p, name, nrhs, graphs), symbol_kind=args.symbol_kind),
            "iters": [s["iters"] for s in stats[0]][:8],
            "rel_true_resid": max(s["rel_true_resid"] for s in stats[0]),
            "all_converged": ok,
@@ -598,6 +603,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--tune", default="",
                     help='launch shapes as JSON instead of autotuning, e.g. \'{"rowinv_mode": 1}\'')
+    ap.add_argument("--symbol-kind", type=int, default=0, choices=[0, 1],
+                    help="0: continuous |xi|^2 (Eqn. 021), 1: the FD-consistent discrete symbol")
     ap.add_argument("--graphs", type=int, default=-1,
                     help="1/0: force CUDA-graph cycles on/off (default: per workload)")
     ap.add_argument("--no-plain", action="store_true",

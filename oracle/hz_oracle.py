@@ -20,7 +20,7 @@ the order the paper states them, with no blocking or fusion:
                         the FFT on the same grid                   (Section 5, Eqn. MainDiscrete)
   * solver              restarted GMRES, matrix-free               (Section 5, "GMRES implementation")
 
-Readings of places where the paper is silent (all also listed in the design doc):
+Readings of places where the paper is silent:
   * a = 0 in the operator is allowed; every node symbol carries the damping
     a_k = a_node + alpha * omega (alpha is a plan parameter).
   * |xi|^2 is the continuous (2 pi k / L)^2 by default (Eqn. 021); the

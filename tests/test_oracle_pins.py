@@ -202,6 +202,26 @@ def test_fft_apply_equals_direct_interpolated_operator():
     np.testing.assert_allclose(a, b, atol=1e-13 * abs(a).max())
 
 
+@pytest.mark.parametrize("shape,kvec", [((48, 64), (5, -7)), ((16, 24, 32), (3, -5, 16))])
+def test_plane_wave_closed_form(shape, kvec):
+    """A discrete plane wave e^{2 pi i k.j / N} has a single Fourier bin, so
+    Q_M of it is the per-point closed form sum_k w_k(x) q_k(|xi_k|^2) times
+    the wave (Eqn. 103 with the weights of Eqn. 405 and the symbols of
+    Eqn. 021), written here from the hat weights and the node table, not
+    from the apply."""
+    p = S.small_problem(shape, 3, M=5, Mt=3, width=2)
+    med = O.make_medium(p.c, p.zeta, p.a, p.omega, p.M, p.Mt, p.c_o, None, 0.15)
+    idx = np.indices(shape, dtype=np.float64)
+    w = np.exp(1j * sum(2 * np.pi * k * idx[a] / shape[a] for a, k in enumerate(kvec)))
+    xi2 = sum((2 * np.pi * ((k % N) if (k % N) < N / 2 else (k % N) - N)) ** 2
+              for k, N in zip(kvec, shape))
+    qk = np.array([1.0 / (med.omega ** 2 + 1j * med.omega * med.nodes.a[k]
+                          - med.nodes.gamma[k] ** 2 * xi2) for k in range(med.nodes.K)])
+    expected = np.tensordot(qk, med.W, axes=(0, 0)) * w
+    got = O.apply_preconditioner(med, w)
+    np.testing.assert_allclose(got, expected, atol=1e-12 * abs(expected).max())
+
+
 def test_node_exactness_against_direct_uninterpolated_operator():
     """Where gamma(x) is a node, q_M(gamma(x), .) = q(gamma(x), .): Q_M v
     equals the un-interpolated Q v of Eqn. Precond (direct sum) there."""

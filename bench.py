@@ -247,15 +247,28 @@ def time_apply(plan, p, stream, reps=30):
     return 1e3 * e0.elapsed_time(e1) / reps
 
 
-def plain_fp64(hz, med, p, f, stream, graphs, dist, world, max_rhs=2):
+def plain_fp64(hz, med, p, f, stream, graphs, dist, world, plan_mixed=None, u_mixed=None,
+               max_rhs=2):
     """The plain FP64 path one right-hand side at a time (complex128
     preconditioner, right GMRES): the comparison the mixed-precision batched
     solver is measured against.  One warm-up solve, then up to max_rhs
-    right-hand sides solved one by one."""
+    right-hand sides solved one by one.  Also the error of the reduced-
+    precision results against it: the complex64 apply of the mixed plan vs
+    the complex128 apply on one random vector, and the mixed solution of
+    the first right-hand side vs the FP64 one."""
     import torch
     plan = hz.Plan(med, precision=0, restart=p.restart, tol=p.tol, maxit=4000, max_nrhs=1,
                    graphs=graphs)
     plan.autotune()
+    errs = {}
+    if plan_mixed is not None:
+        g = torch.Generator(device="cuda").manual_seed(11)
+        x = torch.randn(p.n, dtype=torch.complex128, device="cuda", generator=g)
+        y64 = plan.apply_preconditioner(x, 0, stream=stream)
+        y32 = plan_mixed.apply_preconditioner(x, 1, stream=stream)
+        torch.cuda.synchronize()
+        errs["c64_apply_rel_err"] = float(torch.linalg.vector_norm(y32 - y64) /
+                                          torch.linalg.vector_norm(y64))
     nr = min(f.shape[0], max_rhs)
     u = torch.zeros_like(f[:1])
     plan.solve(f[:1], u, stream=stream)
@@ -268,10 +281,16 @@ def plain_fp64(hz, med, p, f, stream, graphs, dist, world, max_rhs=2):
     for i in range(nr):
         u.zero_()
         sts += plan.solve(f[i:i + 1], u, stream=stream)[1]
+        if i == 0:
+            u0 = u.clone()
     e1.record(stream)
     torch.cuda.synchronize()
     ms, value = job_rate(dist, world, nr, e0.elapsed_time(e1))
+    if u_mixed is not None:
+        errs["solution_rel_diff_vs_fp64"] = float(torch.linalg.vector_norm(u_mixed[:1] - u0) /
+                                                  torch.linalg.vector_norm(u0))
     return {"value": value, "unit": "solves/s", "ms_per_solve": ms / nr, "rhs_sampled": nr,
+            "reduced_precision_errors": errs,
             "iters": [s["iters"] for s in sts], "rel_true_resid": max(s["rel_true_resid"] for s in sts),
             "converged": all(s["converged"] for s in sts),
             "path": "precision 0: complex128 preconditioner, FP64 right GMRES, one rhs at a time"}
@@ -375,7 +394,11 @@ def run_gpu(args, p, name):
 
     ok = all(s["converged"] and s["rel_true_resid"] <= p.tol for st in stats for s in st)
     apply_us = time_apply(plan, p, stream) if p.precision == 1 else None
-    plain = None if args.no_plain else plain_fp64(hz, med, p, f, stream, graphs, dist, world)
+    plain = None
+    if not args.no_plain:
+        mixed = p.precision == 1
+        plain = plain_fp64(hz, med, p, f, stream, graphs, dist, world,
+                           plan if mixed else None, u if mixed else None)
     if rank != 0:
         return
     hbm = float(peaks.get("hbm_gbs", 6800.0))

@@ -73,6 +73,23 @@ struct AxisTables {
   float* xi2_32 = nullptr;
 };
 
+#ifdef __CUDACC__
+// float -> double by moving the bit fields with integer operations, so that
+// the conversion does not occupy the FP64 pipe (the limit of the FP64
+// kernels that read complex64 data).
+// Exact for normal numbers, zeros, infinities and NaNs; single-precision
+// subnormals (|x| < 1.2e-38) are read as signed zeros.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long ed = e == 0u ? 0ull : (e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u));
+  const unsigned long long m = e == 0u ? 0ull : (unsigned long long)(u & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(sign | (ed << 52) | m));
+}
+
+#endif
+
 }  // namespace hz
 
 struct hz_medium {

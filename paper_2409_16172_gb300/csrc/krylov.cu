@@ -391,6 +391,9 @@ __global__ void givens_kernel(KsDev ks, int j, int nrhs) {
   for (int i = lane; i <= j + 1; i += 32) colg[i] = rcol[i];
 }
 
+__device__ __forceinline__ double2 widen(double2 v) { return v; }
+__device__ __forceinline__ double2 widen(float2 v) { return make_double2(f2d_bits(v.x), f2d_bits(v.y)); }
+
 // u += sum_{i < jn} y[b][i] Z_i  (Z in c64 or c128), one pass.
 template <typename ZT>
 __global__ void __launch_bounds__(KT)
@@ -404,15 +407,26 @@ solution_update_kernel(const ZT* __restrict__ Z, long ldb, double2* __restrict__
   __syncthreads();
   double2* ub = u + b * ustride;
   for (long p = long(blockIdx.x) * KT + threadIdx.x; p < n; p += long(gridDim.x) * KT) {
-    double2 x = ub[p];
-    for (int i = 0; i < J; ++i) {
-      const ZT zv = Z[(long(i) * ldb + b) * n + p];
-      const double zr = double(zv.x), zi = double(zv.y);
-      const double2 c = ys[i];
-      x.x = fma(c.x, zr, fma(-c.y, zi, x.x));
-      x.y = fma(c.x, zi, fma(c.y, zr, x.y));
+    // two interleaved partial sums; complex64 Z widened by integer bit moves
+    // (off the FP64 pipe, the limit here)
+    double2 x = ub[p], x1 = make_double2(0.0, 0.0);
+    int i = 0;
+    for (; i + 1 < J; i += 2) {
+      const double2 z0 = widen(Z[(long(i) * ldb + b) * n + p]);
+      const double2 z1 = widen(Z[(long(i + 1) * ldb + b) * n + p]);
+      const double2 c0 = ys[i], c1 = ys[i + 1];
+      x.x = fma(c0.x, z0.x, fma(-c0.y, z0.y, x.x));
+      x.y = fma(c0.x, z0.y, fma(c0.y, z0.x, x.y));
+      x1.x = fma(c1.x, z1.x, fma(-c1.y, z1.y, x1.x));
+      x1.y = fma(c1.x, z1.y, fma(c1.y, z1.x, x1.y));
     }
-    ub[p] = x;
+    if (i < J) {
+      const double2 z0 = widen(Z[(long(i) * ldb + b) * n + p]);
+      const double2 c0 = ys[i];
+      x.x = fma(c0.x, z0.x, fma(-c0.y, z0.y, x.x));
+      x.y = fma(c0.x, z0.y, fma(c0.y, z0.x, x.y));
+    }
+    ub[p] = make_double2(x.x + x1.x, x.y + x1.y);
   }
 }
 

@@ -12,19 +12,6 @@ namespace {
 
 constexpr int ST_THREADS = 256;
 
-// float -> double by moving the bit fields with integer operations, so that
-// the conversion does not occupy the FP64 pipe (the limit of this kernel).
-// Exact for normal numbers, zeros, infinities and NaNs; single-precision
-// subnormals (|x| < 1.2e-38) are read as signed zeros.
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xffu;
-  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
-  const unsigned long long ed = e == 0u ? 0ull : (e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u));
-  const unsigned long long m = e == 0u ? 0ull : (unsigned long long)(u & 0x7fffffu) << 29;
-  return __longlong_as_double((long long)(sign | (ed << 52) | m));
-}
-
 __device__ __forceinline__ double2 ld2(const double2* p, long i) { return p[i]; }
 __device__ __forceinline__ double2 ld2(const float2* p, long i) {
   const float2 v = p[i];

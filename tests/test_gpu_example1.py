@@ -77,3 +77,25 @@ def test_preconditioning_gap_and_mixed_precision(hz):
         assert gap >= 3.5, (key, gap)
     assert np.all(np.abs(np.log10(hs["c64"][:10] / hs["fp64"][:10])) <= 0.01)
     assert abs(math.log10(hs["c64"][99] / hs["fp64"][99])) <= 1.0
+
+
+def test_history_is_per_step_and_monotone_within_cycles(hz):
+    """The recorded estimates: one per Arnoldi step, non-increasing within
+    each cycle of GMRES(10) (the Givens residual of a growing Krylov space),
+    and the call rejects an empty history buffer."""
+    import ctypes as C
+    p = S.example1(64)
+    _, med_g = _media(hz, p)
+    plan = hz.Plan(med_g, precision=1, restart=10, tol=1e-14, maxit=35)
+    _, st, H = plan.solve(np.ascontiguousarray(p.f[0]), history=40)
+    h = H[0]
+    assert st[0]["iters"] == 35 and np.all(np.isnan(h[35:]))
+    for c0 in range(0, 35, 10):
+        cyc = h[c0:min(c0 + 10, 35)]
+        assert np.all(np.diff(cyc) <= 1e-12 * cyc[:-1])
+    f = np.ascontiguousarray(p.f[0])
+    u = np.zeros_like(f)
+    stats = (hz.hz_solve_stats * 1)()
+    rc = hz.lib.hz_gmres_solve_history(plan._h, C.c_void_p(f.ctypes.data), C.c_void_p(u.ctypes.data),
+                                       1, stats, None, 0, None)
+    assert hz.STATUS[rc] == "HZ_ERR_INVALID_ARG"

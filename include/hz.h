@@ -132,7 +132,9 @@ hz_status hz_set_allocator(void* (*alloc)(size_t bytes, void* ctx),
  * gamma^2 of Eqn. Complex_wave_speed) from HOST arrays of n doubles each,
  * indexed [z][y][x].  c: wave speed (> 0); zeta: layer profile (>= 0, NULL =
  * no layer); a: operator damping of Eqn. 001 (NULL = 0).  The arrays are
- * copied; the call returns after the medium is ready.
+ * copied; the call returns after the medium is ready.  Axis lengths: 8, 12,
+ * 16, 24, 32, 48, 64, 96, 128, 192, 256, 512, 1024, 2048 (z <= 1024); fewer
+ * than 2^31 points.
  * Errors: HZ_ERR_INVALID_ARG (grid, options), HZ_ERR_MEDIUM (c <= 0, zeta < 0,
  * NaN, c != c_o in the layer, too few nodes), HZ_ERR_OOM, HZ_ERR_CUDA. */
 hz_status hz_create_medium(const hz_grid* grid, const double* c, const double* zeta,
@@ -171,7 +173,9 @@ typedef struct {
   float upd_us, upd_us_default;
   float apply_us, apply_us_default;   /* whole preconditioner apply        */
   int rowinv_mode;          /* x-inverse pass: 0 by grid size, 1 in place
-                               then a gather of the weighted sum, 2 fused  */
+                               then a gather of the weighted sum, 2 fused
+                               with staged loads, 3 fused with direct loads
+                               (fewer registers)                           */
   int col_pair;             /* complex64 symbol pass: 1 two columns per
                                thread in packed FP32, 0 one column          */
 } hz_tune_report;
@@ -180,7 +184,7 @@ hz_status hz_plan_autotune(hz_plan* plan, void* stream, hz_tune_report* report);
 
 /* Sets the plan's launch shapes from a report (e.g. one saved from an
  * earlier hz_plan_autotune): dots_vc in {2, 4, 8}, dots_bps in 1..4, upd_bps
- * in 1..8, syminv_kpb in {1, 2, 4}, rowinv_mode in {0, 1, 2}, col_pair in
+ * in 1..8, syminv_kpb in {1, 2, 4}, rowinv_mode in {0, 1, 2, 3}, col_pair in
  * {0, 1}; the timing
  * fields are ignored.  HZ_ERR_INVALID_ARG for any other value. */
 hz_status hz_plan_set_tune(hz_plan* plan, const hz_tune_report* report);

@@ -236,6 +236,11 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
   }
   if (grid->dim == 3 && grid->n[2] > 1024)
     return set_error(HZ_ERR_INVALID_ARG, "z axis longer than 1024");
+  {
+    // kernels index one right-hand side's points with 32-bit integers
+    const long long pts = (long long)grid->n[0] * grid->n[1] * (grid->dim == 3 ? grid->n[2] : 1);
+    if (pts >= (1LL << 31)) return set_error(HZ_ERR_INVALID_ARG, "grid has %lld >= 2^31 points", pts);
+  }
   if (!(omega > 0) || !std::isfinite(omega)) return set_error(HZ_ERR_INVALID_ARG, "omega must be > 0");
   if (interp->M < 1 || interp->Mt < 0 || interp->M + interp->Mt > HZ_MAX_K)
     return set_error(HZ_ERR_INVALID_ARG, "need 1 <= M and M + Mt <= %d", HZ_MAX_K);

@@ -99,3 +99,24 @@ def test_history_is_per_step_and_monotone_within_cycles(hz):
     rc = hz.lib.hz_gmres_solve_history(plan._h, C.c_void_p(f.ctypes.data), C.c_void_p(u.ctypes.data),
                                        1, stats, None, 0, None)
     assert hz.STATUS[rc] == "HZ_ERR_INVALID_ARG"
+
+
+def test_unpreconditioned_with_graphs_and_multi_rhs(hz):
+    """no_precond through the captured-cycle path and with two right-hand
+    sides: the same iterates as step-by-step launches (fixed-order sums), and
+    the oracle's unpreconditioned residual."""
+    p = S.example1(64)
+    med_o, med_g = _media(hz, p)
+    f = np.ascontiguousarray(np.stack([p.f[0], np.conj(p.f[0])]))
+    out = {}
+    for graphs in (False, True):
+        plan = hz.Plan(med_g, precision=0, restart=10, tol=1e-14, maxit=40, max_nrhs=2,
+                       graphs=graphs, no_precond=True)
+        u, st = plan.solve(f)
+        out[graphs] = (u, st)
+    np.testing.assert_array_equal(out[False][0], out[True][0])
+    A = lambda x: O.apply_operator(med_o, x)
+    for b in range(2):
+        _, so = O.gmres(A, f[b], None, restart=10, tol=1e-14, maxit=40)
+        r = np.linalg.norm(f[b] - A(out[True][0][b])) / np.linalg.norm(f[b])
+        assert abs(r / so["rel_true_resid"] - 1) <= 1e-6

@@ -223,11 +223,11 @@ def apply_model_bytes(p):
     return n * (per + 8)
 
 
-def time_apply(plan, p, stream, reps=30):
-    """Mean time (us) of one hz_apply_preconditioner (complex64) on all the
-    workload's right-hand sides at once, back to back, rotating through
-    input/output pairs (>= 256 MB of inputs in all) so that the inputs are
-    not L2-resident."""
+def time_apply(plan, p, stream, reps=30, precision=1):
+    """Mean time (us) of one hz_apply_preconditioner (complex64, or complex128
+    with precision 0) on all the workload's right-hand sides at once, back to
+    back, rotating through input/output pairs (>= 256 MB of inputs in all)
+    so that the inputs are not L2-resident."""
     import torch
     n = p.n * p.f.shape[0]
     nbuf = int(min(8, max(2, -(-(256 << 20) // (16 * n)))))
@@ -235,13 +235,13 @@ def time_apply(plan, p, stream, reps=30):
     xs = [torch.randn(n, dtype=torch.complex128, device="cuda", generator=g) for _ in range(nbuf)]
     ys = [torch.empty_like(x) for x in xs]
     for i in range(3):
-        plan.apply_preconditioner(xs[i % nbuf], 1, out=ys[i % nbuf], stream=stream)
+        plan.apply_preconditioner(xs[i % nbuf], precision, out=ys[i % nbuf], stream=stream)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for r in range(reps):
-        plan.apply_preconditioner(xs[r % nbuf], 1, out=ys[r % nbuf], stream=stream)
+        plan.apply_preconditioner(xs[r % nbuf], precision, out=ys[r % nbuf], stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     return 1e3 * e0.elapsed_time(e1) / reps
@@ -548,6 +548,115 @@ def run_example1(args):
     print(json.dumps(out), flush=True)
 
 
+def fit_beta(Ns, T_rows, d=2):
+    """Order beta of T ~ M N^(d beta) log N as the paper's Table 1 computes
+    it: slope / d of a least-squares line through (log N, log T) for each row
+    (one M), and pooled over all rows with one intercept per row."""
+    x = np.log(np.asarray(Ns, np.float64))
+    rows = [float(np.polyfit(x, np.log(np.asarray(T, np.float64)), 1)[0] / d) for T in T_rows]
+    X = np.zeros((len(T_rows) * len(x), 1 + len(T_rows)))
+    y = np.concatenate([np.log(np.asarray(T, np.float64)) for T in T_rows])
+    for r in range(len(T_rows)):
+        X[r * len(x):(r + 1) * len(x), 0] = x
+        X[r * len(x):(r + 1) * len(x), 1 + r] = 1.0
+    pooled = float(np.linalg.lstsq(X, y, rcond=None)[0][0] / d)
+    return rows, pooled
+
+
+def run_complexity(args):
+    """Table 1's study on the GPU: time of one Q_{N,M} apply for N = 256 ..
+    2048 and M = 2, 4, 8 on the Example 1 medium (PPW 12), complex64 (the
+    solver's preconditioner) and complex128, normalised to the smallest
+    (N, M = 2), and the fitted order beta of T ~ M N^(2 beta) log N."""
+    import torch
+    from paper_2409_16172_gb300 import build, synth as S
+    build.build()
+    from paper_2409_16172_gb300 import hz
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    Ns, Ms = list(args.cx_n), [2, 4, 8]
+    res = {}
+    for prec in (1, 0):
+        T = []
+        for M in Ms:
+            row = []
+            for N in Ns:
+                p = S.example1(N, M=M)
+                med = hz.Medium(p.c, p.zeta, p.a, omega=p.omega, M=M, Mt=0, c_o=1.0, alpha=0.0,
+                                a_node=p.meta["a_node"])
+                plan = hz.Plan(med, precision=prec)
+                if prec == 1:
+                    plan.autotune()
+                row.append(time_apply(plan, p, stream, precision=prec))
+                del plan, med
+            T.append(row)
+        rows, pooled = fit_beta(Ns, T)
+        t0 = T[0][0]
+        res["c64" if prec == 1 else "c128"] = {
+            "apply_us": {f"M={M}": [round(t, 2) for t in T[i]] for i, M in enumerate(Ms)},
+            "normalised": {f"M={M}": [round(t / t0, 3) for t in T[i]] for i, M in enumerate(Ms)},
+            "beta": {f"M={M}": round(b, 3) for M, b in zip(Ms, rows)}, "beta_pooled": round(pooled, 3)}
+    out = {"metric": "Table 1 (Section 5.1): order beta of the Q_{N,M} apply time, T ~ M N^(2 beta) log N",
+           "value": res["c64"]["beta_pooled"], "unit": "beta (pooled, complex64 apply)",
+           "n_gpus": 1, "steps": 30, "warmup": 3, "ms_per_step": None, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32 / f64", "data": "synthetic",
+           "config": {"workload": "example1 medium, PPW 12, a 20, delta 1", "N": Ns, "M": Ms,
+                      "note": "the paper's N = 180..2880 are not FFT sizes of this build"},
+           "paper_context": "Table 1 (MATLAB, CPU): beta 1.02 / 1.03 / 1.04 for M = 2 / 4 / 8, "
+                            "pooled 1.03",
+           "results": res}
+    print(json.dumps(out), flush=True)
+
+
+def run_spectrum(args):
+    """Spectral estimates (Section 5.1, Table 2's setting: delta = 4,
+    eta = 1/800, a = 20, PPW = 12): Ritz values of P_N Q_M from one Arnoldi
+    cycle of 100 steps (FP64) started from a seeded random vector (the plane
+    wave of Eqn. Source is nearly an eigenvector and ends the process in a
+    few steps), cond estimate max|theta| / min|theta|, for M = 1 (Q_1 of
+    Eqn. OneInterpPoint), 2, 4, 8, 16, 32 and without the preconditioner, at
+    several N."""
+    import torch
+    from paper_2409_16172_gb300 import build, synth as S
+    build.build()
+    from paper_2409_16172_gb300 import hz
+    torch.cuda.set_device(0)
+    m = 100
+    rows = []
+    t0 = time.perf_counter()
+    for N in args.spec_n:
+        p = S.example1(N, delta=4.0)
+        f = np.ascontiguousarray(S.random_field(np.random.Generator(np.random.PCG64(N)), p.shape))
+        for M in (None, 1, 2, 4, 8, 16, 32):
+            med = hz.Medium(p.c, p.zeta, p.a, omega=p.omega, M=M or 1, Mt=0, c_o=1.0, alpha=0.0,
+                            a_node=p.meta["a_node"])
+            plan = hz.Plan(med, precision=0, restart=m, tol=1e-14, maxit=m,
+                           no_precond=M is None)
+            plan.solve(f)
+            H = plan.hessenberg(0)
+            J = H.shape[1]
+            th = np.abs(np.linalg.eigvals(H[:J, :J]))
+            rows.append({"N": N, "omega_over_pi": p.omega / math.pi,
+                         "M": M if M is not None else "none", "ritz_steps": J,
+                         "cond_est": float(th.max() / th.min()),
+                         "ritz_abs_max": float(th.max()), "ritz_abs_min": float(th.min())})
+            del plan, med
+    span = time.perf_counter() - t0
+    out = {"metric": "Ritz-value estimate of cond(P_N Q_M) (Table 2 setting)",
+           "value": next(r["cond_est"] for r in rows if r["M"] == 8), "unit": "cond estimate at M = 8, smallest N",
+           "n_gpus": 1, "steps": len(rows), "warmup": 0, "ms_per_step": 1e3 * span / len(rows),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "table2-setting delta4-eta1/800-a20-ppw12", "arnoldi_steps": m,
+                      "N": list(args.spec_n),
+                      "note": "the paper's N = 120..1920 are not FFT sizes of this build; "
+                              "power-of-two N at the same PPW"},
+           "paper_context": "Table 2 (MATLAB eigs): M = 1: 1.2e7..2.4e8, M = 8: 5.3e2..1.7e1, "
+                            "M = 32: 4.9e2..1.4e1 for omega = 20 pi..320 pi",
+           "rows": rows}
+    print(json.dumps(out), flush=True)
+
+
 def run_serving(args):
     """Serving stream: requests drawn from the serving recipe arrive with
     seeded exponential gaps; the server admits them by HBM footprint."""
@@ -615,10 +724,15 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["cfg2", "cfg1", "cfg3", "cfg4", "serving", "example1"],
+    ap.add_argument("--workload", choices=["cfg2", "cfg1", "cfg3", "cfg4", "serving", "example1",
+                                           "spectrum", "complexity"],
                     default="cfg2", help="cfg2 (default): the 2D 1024^2 K=16 workload")
     ap.add_argument("--requests", type=int, default=30, help="serving: number of requests")
     ap.add_argument("--ex1-n", type=int, default=2048, help="example1: grid side N")
+    ap.add_argument("--spec-n", type=int, nargs="+", default=[128, 256, 512],
+                    help="spectrum: grid sides N")
+    ap.add_argument("--cx-n", type=int, nargs="+", default=[256, 512, 1024, 2048],
+                    help="complexity: grid sides N")
     ap.add_argument("--rate", type=float, default=4.0, help="serving: arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent requests")
     ap.add_argument("--cpu-iters", type=int, default=6, help="Arnoldi steps in the CPU sample")
@@ -643,6 +757,12 @@ def main():
         return
     if args.workload == "example1":
         run_example1(args)
+        return
+    if args.workload == "spectrum":
+        run_spectrum(args)
+        return
+    if args.workload == "complexity":
+        run_complexity(args)
         return
     p = getattr(S, WORKLOADS[args.workload][0])()
     if args.impl == "reference":

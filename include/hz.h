@@ -173,9 +173,7 @@ typedef struct {
   float upd_us, upd_us_default;
   float apply_us, apply_us_default;   /* whole preconditioner apply        */
   int rowinv_mode;          /* x-inverse pass: 0 by grid size, 1 in place
-                               then a gather of the weighted sum, 2 fused
-                               with staged loads, 3 fused with direct loads
-                               (fewer registers)                           */
+                               then a gather of the weighted sum, 2 fused  */
   int col_pair;             /* complex64 symbol pass: 1 two columns per
                                thread in packed FP32, 0 one column          */
 } hz_tune_report;
@@ -184,7 +182,7 @@ hz_status hz_plan_autotune(hz_plan* plan, void* stream, hz_tune_report* report);
 
 /* Sets the plan's launch shapes from a report (e.g. one saved from an
  * earlier hz_plan_autotune): dots_vc in {2, 4, 8}, dots_bps in 1..4, upd_bps
- * in 1..8, syminv_kpb in {1, 2, 4}, rowinv_mode in {0, 1, 2, 3}, col_pair in
+ * in 1..8, syminv_kpb in {1, 2, 4}, rowinv_mode in {0, 1, 2}, col_pair in
  * {0, 1}; the timing
  * fields are ignored.  HZ_ERR_INVALID_ARG for any other value. */
 hz_status hz_plan_set_tune(hz_plan* plan, const hz_tune_report* report);
@@ -249,6 +247,17 @@ hz_status hz_gmres_solve(hz_plan* plan, const void* f, void* u, int nrhs,
 hz_status hz_gmres_solve_history(hz_plan* plan, const void* f, void* u, int nrhs,
                                  hz_solve_stats* stats, double* history, int history_len,
                                  void* stream);
+
+/* The Hessenberg matrix of the last Arnoldi cycle of right-hand side rhs in
+ * the plan's most recent solve, before the Givens rotations: column j holds
+ * h_{0..j+1, j} of the (F)GMRES relation P_N Z_J = V_{J+1} H, i.e. of the
+ * right-preconditioned operator P_N Q_M (or P_N alone with no_precond), so
+ * the eigenvalues of its square part are Ritz values of that operator (the
+ * spectral estimates compared with Tables 2-6).  H: host array of
+ * (restart + 1) * restart complex128 entries, written column by column with
+ * leading dimension restart + 1; *cols receives the number of columns J
+ * (0 if rhs did not run in the final cycle).  Synchronous. */
+hz_status hz_plan_hessenberg(const hz_plan* plan, int rhs, void* H, int* cols);
 
 /* ---- serving ----------------------------------------------------------
  * A server queues solve requests and admits them onto the GPU as slots and

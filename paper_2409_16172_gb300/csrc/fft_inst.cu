@@ -82,18 +82,6 @@ hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segta
     count_launches(1);  // the phase counts one
     return HZ_OK;
   }
-  if (mode == 3) {
-    constexpr int lines = C::ROW_LINES;
-    auto k = row_inv_acc_direct_kernel<R, N, OutT, C::ROW_LINES>;
-    HZ_TRY(smem_attr(k, C::row_acc_direct_smem(lines)));
-    const long blocks = (nrows + lines - 1) / lines;
-    k<<<unsigned(blocks), lines * C::TPL_ROW, C::row_acc_direct_smem(lines), st>>>(
-        static_cast<const V*>(planes), static_cast<const typename RecT<R>::T*>(rec), segtab, nseg,
-        rowmask, K, rows_per_rhs, nrows, n, R(inv_n), static_cast<const V*>(tw),
-        static_cast<OutT*>(out), active);
-    HZ_CUDA(cudaGetLastError());
-    return HZ_OK;
-  }
   constexpr int lines = C::ROW_LINES;
   auto k = row_inv_acc_kernel<R, N, OutT, C::ROW_LINES>;
   HZ_TRY(smem_attr(k, C::row_acc_smem(lines)));

@@ -26,8 +26,6 @@ namespace hz {
 // Strided kernels: TB adjacent columns x TPL threads, TB chosen so that a
 // block moves at least 64 contiguous bytes per row, has >= 128 threads, at
 // most 512, and its shared memory stays under ~200 KB.
-template <typename R> struct RecT;  // per-point interpolation record type
-
 template <typename R, int N> struct LineCfg {
   using CP = typename ColPlan<R, N>::P;           // strided kernels
   static constexpr int TPL = N / CP::E;
@@ -54,10 +52,6 @@ template <typename R, int N> struct LineCfg {
   static constexpr size_t stage_offset(int lines = ROW_LINES) { return (row_smem(lines) + 15) / 16 * 16; }
   static constexpr size_t row_acc_smem(int lines = ROW_LINES) {
     return stage_offset(lines) + size_t(lines) * 2 * N * VB;
-  }
-  // direct-load variant: padded work lines, then the rows' records
-  static constexpr size_t row_acc_direct_smem(int lines = ROW_LINES) {
-    return stage_offset(lines) + size_t(lines) * N * sizeof(typename RecT<R>::T);
   }
   static constexpr size_t col_smem() { return size_t(TB) * padded_len(N) * VB; }
   static constexpr size_t col_pair_smem() { return size_t(TB) * padded_len(N) * 16; }
@@ -253,89 +247,6 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
     }
     kc = kn;
     buf ^= 1;
-  }
-  if (valid) {
-    OutT* dst = out + rhs * n + lrow * N;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      OutT o;
-      o.x = acc[e].x * inv_n;
-      o.y = acc[e].y * inv_n;
-      dst[F::out_index(t, e)] = o;
-    }
-  }
-}
-
-// The fused pass with fewer registers per thread: the plane rows are read
-// straight from global memory in the transform's stage-0 order (coalesced
-// for the row plans) instead of through cp.async staging, and the rows'
-// interpolation records sit in shared memory, so that three blocks fit on
-// an SM instead of two.
-template <typename R, int N, typename OutT, int LPB>
-__global__ void __launch_bounds__(LPB * LineCfg<R, N>::TPL_ROW, 3)
-row_inv_acc_direct_kernel(const typename cvec<R>::T* __restrict__ planes,
-                          const typename RecT<R>::T* __restrict__ rec,
-                          const uchar2* __restrict__ segtab, int nseg,
-                          const unsigned long long* __restrict__ rowmask, int K, long rows_per_rhs,
-                          long nrows, long n, R inv_n, const typename cvec<R>::T* __restrict__ tw,
-                          OutT* __restrict__ out, const int* __restrict__ active) {
-  using V = typename cvec<R>::T;
-  using RT = typename RecT<R>::T;
-  constexpr bool WS = LineCfg<R, N>::WS;
-  using F = LineFFT<R, N, +1, 1, WS, typename LineCfg<R, N>::RP>;
-  constexpr int TPL = F::TPL, E = F::E;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* sm = reinterpret_cast<V*>(smem_raw);
-  __shared__ uchar2 seg_s[HZ_MAX_SEG];
-  __shared__ unsigned long long cta_mask;
-  for (int i = threadIdx.x; i < nseg; i += blockDim.x) seg_s[i] = segtab[i];
-  const int li = threadIdx.x / TPL, t = threadIdx.x % TPL;
-  const long row = long(blockIdx.x) * LPB + li;
-  const bool valid = row < nrows && (!active || active[row / rows_per_rhs]);
-  const long rhs = valid ? row / rows_per_rhs : 0;
-  const long lrow = valid ? row - rhs * rows_per_rhs : 0;
-  const unsigned long long mymask = valid ? rowmask[lrow] : 0ull;
-  if (threadIdx.x == 0) cta_mask = 0ull;
-  V* line = sm + li * padded_len(N);
-  RT* rec_s = reinterpret_cast<RT*>(smem_raw + LineCfg<R, N>::stage_offset(LPB)) + li * N;
-  for (int i = t; i < N; i += TPL) rec_s[i] = valid ? rec[lrow * N + i] : RT(0);
-  __syncthreads();
-  if (t == 0 && mymask) atomicOr(&cta_mask, mymask);
-  V acc[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) acc[e] = cmk<V>(R(0), R(0));
-  __syncthreads();
-  unsigned long long todo = cta_mask;
-  if constexpr (WS) {
-    const unsigned lm = F::lane_mask();
-    const unsigned lo = __reduce_or_sync(lm, unsigned(mymask & 0xFFFFFFFFull));
-    const unsigned hi = __reduce_or_sync(lm, unsigned(mymask >> 32));
-    todo = (unsigned long long)lo | ((unsigned long long)hi << 32);
-  }
-  const V* pbase = planes + (rhs * K) * n + lrow * N;
-  while (todo) {
-    const int kc = __ffsll((long long)todo) - 1;
-    todo &= todo - 1;
-    const bool need = (mymask >> kc) & 1ull;
-    const V* src = pbase + long(kc) * n;
-    V x[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = need ? src[F::stage0_index(t, e)] : cmk<V>(R(0), R(0));
-    F::run_regs(line, t, x, tw);
-    if (need) {
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        int seg;
-        R tf;
-        decode_rec(rec_s[F::out_index(t, e)], seg, tf);
-        const uchar2 kk = seg_s[seg];
-        R w = R(0);
-        if (kk.x == kc) w += R(1) - tf;
-        if (kk.y == kc) w += tf;
-        acc[e].x += w * x[e].x;
-        acc[e].y += w * x[e].y;
-      }
-    }
   }
   if (valid) {
     OutT* dst = out + rhs * n + lrow * N;

@@ -63,6 +63,7 @@ hz_status solve_ws_create(hz_plan* p) {
   A(w->ar.alloc(&ks.g, size_t(B) * (m + 1)));
   A(w->ar.alloc(&ks.est, B));
   A(w->ar.alloc(&ks.hist, size_t(B) * m));
+  A(w->ar.alloc(&ks.Hraw, size_t(B) * m * (m + 1)));
   A(w->ar.alloc(&ks.bnorm, B));
   A(w->ar.alloc(&ks.jend, B));
   A(w->ar.alloc(&ks.active, B));
@@ -411,6 +412,27 @@ hz_status gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs, hz_
 extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs,
                                     hz_solve_stats* stats, void* stream) {
   return gmres_solve(plan, f_in, u_io, nrhs, stats, nullptr, 0, stream);
+}
+
+extern "C" hz_status hz_plan_hessenberg(const hz_plan* plan, int rhs, void* H, int* cols) {
+  if (!plan || !H || !cols) return set_error(HZ_ERR_INVALID_ARG, "null argument");
+  if (!plan->ws) return set_error(HZ_ERR_INVALID_ARG, "no solve has run on this plan");
+  if (rhs < 0 || rhs >= plan->max_nrhs) return set_error(HZ_ERR_INVALID_ARG, "rhs out of range");
+  const int m = plan->opts.restart;
+  const KsDev& ks = plan->ws->ks;
+  int J = 0;
+  HZ_CUDA(cudaMemcpy(&J, ks.jend + rhs, sizeof(int), cudaMemcpyDeviceToHost));
+  J = std::max(0, std::min(J, m));
+  *cols = J;
+  if (J > 0) {
+    HZ_CUDA(cudaMemcpy(H, ks.Hraw + long(rhs) * m * (m + 1), size_t(J) * (m + 1) * sizeof(double2),
+                       cudaMemcpyDeviceToHost));
+    // below the subdiagonal: zero (those entries are never written)
+    double2* h = static_cast<double2*>(H);
+    for (int j = 0; j < J; ++j)
+      for (int i = j + 2; i <= m; ++i) h[size_t(j) * (m + 1) + i] = make_double2(0.0, 0.0);
+  }
+  return HZ_OK;
 }
 
 extern "C" hz_status hz_gmres_solve_history(hz_plan* plan, const void* f_in, void* u_io, int nrhs,

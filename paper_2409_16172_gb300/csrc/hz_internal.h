@@ -136,8 +136,7 @@ struct FftOps {
                        long nrows, const void* tw, void* out, cudaStream_t st, const int* active);
   // inverse FFT along x of the K planes + weighted sum; out_kind 0: c64, 1: c128
   // mode 0: by size, 1: in-place inverse then gather (planes overwritten),
-  // 2: fused inverse + weighted sum (cp.async staging), 3: fused with direct
-  // loads and the records in shared memory
+  // 2: fused inverse + weighted sum
   hz_status (*row_inv_acc)(int prec, int out_kind, const void* planes, const void* rec,
                            const uchar2* segtab, int nseg, const unsigned long long* rowmask,
                            int K, long rows_per_rhs, long nrows, long n, double inv_n,

@@ -19,6 +19,7 @@ struct KsDev {
   double2* g;       // [b][m+1] rotated right-hand side
   double* est;      // [b] |g_{j+1}|
   double* hist;     // [b][m] est / ||f|| after each step of the cycle
+  double2* Hraw;    // [b][j][m+1] Hessenberg columns of the cycle before rotation
   double* bnorm;    // [b] ||f||
   int* jend;        // [b] columns built in this cycle
   int* active;      // [b] 1 while the cycle continues

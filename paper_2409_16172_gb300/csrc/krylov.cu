@@ -291,6 +291,7 @@ __global__ void givens_kernel(KsDev ks, int j, int nrhs) {
     const double s = ks.sigma[long(i) * ks.ldsig + b];
     const double2 h = make_double2(s * (S1[i].x + S2[i].x), s * (S1[i].y + S2[i].y));
     col[i] = h;
+    ks.Hraw[(long(b) * m + j) * (m + 1) + i] = h;
     hbits = max(hbits, max(absbits(h.x), absbits(h.y)));
     bad |= !isfinite(h.x) || !isfinite(h.y);
   }
@@ -340,6 +341,7 @@ __global__ void givens_kernel(KsDev ks, int j, int nrhs) {
     // h_{j+1,j} = hn = |w|; sigma_{j+1} = 1 / hn normalises the next vector
     const double inv_hn = hn2 > 0.0 ? rsqrt_nr(hn2) : 0.0;
     const double hn = hn2 * inv_hn;
+    ks.Hraw[(long(b) * m + j) * (m + 1) + j + 1] = make_double2(hn, 0.0);
     const bool happy = hn <= 1e-14 * hmax;
     ks.sigma[long(j + 1) * ks.ldsig + b] = (hn > 0.0 && !happy) ? inv_hn : 0.0;
     const double aa2 = fma(a.x, a.x, a.y * a.y);

@@ -115,6 +115,7 @@ _SIGS = {
     "hz_server_destroy": (C.c_int, [_vp]),
     "hz_plan_autotune": (C.c_int, [_vp, _vp, C.POINTER(hz_tune_report)]),
     "hz_plan_set_tune": (C.c_int, [_vp, C.POINTER(hz_tune_report)]),
+    "hz_plan_hessenberg": (C.c_int, [_vp, C.c_int, _vp, C.POINTER(C.c_int)]),
     "hz_profile_enable": (C.c_int, [C.c_int]),
     "hz_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "hz_launch_count": (C.c_ulonglong, []),
@@ -286,6 +287,17 @@ class Plan:
         for k, v in shape.items():
             setattr(r, k, int(v))
         check(lib.hz_plan_set_tune(self._h, C.byref(r)))
+
+    def hessenberg(self, rhs: int = 0) -> np.ndarray:
+        """Unrotated Hessenberg matrix (J + 1, J) of the last Arnoldi cycle of
+        right-hand side rhs (hz_plan_hessenberg); its square part's
+        eigenvalues are Ritz values of the preconditioned operator."""
+        m = self.opts.restart
+        buf = np.zeros((m, m + 1), np.complex128)  # column j at buf[j]
+        cols = C.c_int()
+        check(lib.hz_plan_hessenberg(self._h, rhs, _vp(buf.ctypes.data), C.byref(cols)))
+        J = cols.value
+        return np.ascontiguousarray(buf[:J, :J + 1].T)
 
     def nbytes(self) -> int:
         b = C.c_size_t()

@@ -219,7 +219,7 @@ def test_apply_every_launch_shape(hz, shape):
     for prec, tol in ((0, 1e-10), (1, 5e-5)):
         plan = hz.Plan(med_g, precision=prec, max_nrhs=2)
         for kpb, mode, pair in ((1, 1, 1), (1, 2, 0), (2, 2, 1), (4, 1, 0), (4, 2, 1), (2, 0, 1),
-                                (1, 0, 0), (1, 3, 1), (4, 3, 0)):
+                                (1, 0, 0)):
             plan.set_tune(syminv_kpb=kpb, rowinv_mode=mode, col_pair=pair)
             got = plan.apply_preconditioner(_dev(v), precision=prec).cpu().numpy()
             assert rel(got, ref) <= tol, (prec, kpb, mode, pair, rel(got, ref))
@@ -229,7 +229,7 @@ def test_set_tune_rejects_out_of_range(hz):
     p = S.small_problem((16, 16), 3, M=4, Mt=2, width=2)
     med_g, _ = media(hz, p)
     plan = hz.Plan(med_g, precision=1)
-    for bad in (dict(syminv_kpb=3), dict(rowinv_mode=4), dict(dots_vc=5), dict(upd_bps=0),
+    for bad in (dict(syminv_kpb=3), dict(rowinv_mode=3), dict(dots_vc=5), dict(upd_bps=0),
                 dict(dots_bps=5), dict(upd_bps=9), dict(col_pair=2)):
         with pytest.raises(hz.HzError):
             plan.set_tune(**bad)
@@ -243,7 +243,7 @@ def test_autotune_choices_are_valid_and_cached(hz):
     assert r["cached"] == 0
     assert r["dots_bps"] in (1, 2, 3, 4) and r["dots_vc"] in (2, 4, 8)
     assert r["upd_bps"] in (2, 4, 6, 8) and r["syminv_kpb"] in (1, 2, 4)
-    assert r["rowinv_mode"] in (0, 1, 2, 3)
+    assert r["rowinv_mode"] in (0, 1, 2)
     assert 0 < r["dots_us"] <= r["dots_us_default"] * 1.0001
     u, st = plan.solve(np.ascontiguousarray(p.f))
     for b in range(2):

@@ -34,8 +34,9 @@ hz_status row_fwd_t(const double2* in, const double* scale, long rows_per_rhs, l
   if (small) {
     auto k = row_fwd_kernel<R, N, 1>;
     HZ_TRY(smem_attr(k, C::row_smem(1)));
-    k<<<unsigned(nrows), C::TPL_ROW, C::row_smem(1), st>>>(
-        in, scale, rows_per_rhs, nrows, static_cast<const V*>(tw), static_cast<V*>(out), active);
+    HZ_CUDA(launch_pdl(k, dim3(unsigned(nrows)), dim3(C::TPL_ROW), C::row_smem(1), st, in, scale,
+                       rows_per_rhs, nrows, static_cast<const V*>(tw), static_cast<V*>(out),
+                       active));
     HZ_CUDA(cudaGetLastError());
     return HZ_OK;
   }
@@ -43,8 +44,9 @@ hz_status row_fwd_t(const double2* in, const double* scale, long rows_per_rhs, l
   auto k = row_fwd_kernel<R, N, C::ROW_LINES>;
   HZ_TRY(smem_attr(k, C::row_smem(lines)));
   const long blocks = (nrows + lines - 1) / lines;
-  k<<<unsigned(blocks), lines * C::TPL_ROW, C::row_smem(lines), st>>>(
-      in, scale, rows_per_rhs, nrows, static_cast<const V*>(tw), static_cast<V*>(out), active);
+  HZ_CUDA(launch_pdl(k, dim3(unsigned(blocks)), dim3(lines * C::TPL_ROW), C::row_smem(lines), st,
+                     in, scale, rows_per_rhs, nrows, static_cast<const V*>(tw),
+                     static_cast<V*>(out), active));
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
@@ -69,15 +71,15 @@ hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segta
     auto ki = row_inv_inplace_kernel<R, N, C::ROW_LINES>;
     HZ_TRY(smem_attr(ki, C::row_smem()));
     dim3 grid(unsigned((nrows + C::ROW_LINES - 1) / C::ROW_LINES), unsigned(K));
-    ki<<<grid, C::ROW_THREADS, C::row_smem(), st>>>(
-        static_cast<V*>(const_cast<void*>(planes)), rowmask, K, rows_per_rhs, nrows, n,
-        static_cast<const V*>(tw), active);
+    HZ_CUDA(launch_pdl(ki, dim3(grid), dim3(C::ROW_THREADS), C::row_smem(), st,
+                       static_cast<V*>(const_cast<void*>(planes)), rowmask, K, rows_per_rhs, nrows,
+                       n, static_cast<const V*>(tw), active));
     HZ_CUDA(cudaGetLastError());
     const long total = nrows * N;
     const long gblocks = std::min<long>((total + 255) / 256, 152L * 16);
-    weighted_gather_kernel<R, OutT><<<unsigned(gblocks), 256, 0, st>>>(
-        static_cast<const V*>(planes), static_cast<const typename RecT<R>::T*>(rec), segtab, K,
-        n, total, R(inv_n), static_cast<OutT*>(out), active);
+    HZ_CUDA(launch_pdl(weighted_gather_kernel<R, OutT>, dim3(unsigned(gblocks)), dim3(256), 0, st,
+                       static_cast<const V*>(planes), static_cast<const typename RecT<R>::T*>(rec),
+                       segtab, K, n, total, R(inv_n), static_cast<OutT*>(out), active));
     HZ_CUDA(cudaGetLastError());
     count_launches(1);  // the phase counts one
     return HZ_OK;
@@ -86,10 +88,11 @@ hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segta
   auto k = row_inv_acc_kernel<R, N, OutT, C::ROW_LINES>;
   HZ_TRY(smem_attr(k, C::row_acc_smem(lines)));
   const long blocks = (nrows + lines - 1) / lines;
-  k<<<unsigned(blocks), lines * C::TPL_ROW, C::row_acc_smem(lines), st>>>(
-      static_cast<const V*>(planes), static_cast<const typename RecT<R>::T*>(rec), segtab, nseg,
-      rowmask, K, rows_per_rhs, nrows, n, R(inv_n), static_cast<const V*>(tw),
-      static_cast<OutT*>(out), active);
+  HZ_CUDA(launch_pdl(k, dim3(unsigned(blocks)), dim3(lines * C::TPL_ROW), C::row_acc_smem(lines),
+                     st, static_cast<const V*>(planes),
+                     static_cast<const typename RecT<R>::T*>(rec), segtab, nseg, rowmask, K,
+                     rows_per_rhs, nrows, n, R(inv_n), static_cast<const V*>(tw),
+                     static_cast<OutT*>(out), active));
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
@@ -118,9 +121,9 @@ hz_status line_pass_t(void* data, int nx, long outer, long S, long ostride, long
   HZ_TRY(smem_attr(k, C::col_smem()));
   const int ntile = (nx + C::TB - 1) / C::TB;
   dim3 grid(unsigned(ntile * outer), 1, unsigned(batch));
-  k<<<grid, C::COL_THREADS, C::col_smem(), st>>>(static_cast<V*>(data), nx, ntile, S,
-                                                       ostride, bstride, omask, K,
-                                                       static_cast<const V*>(tw), active, per_rhs);
+  HZ_CUDA(launch_pdl(k, dim3(grid), dim3(C::COL_THREADS), C::col_smem(), st, static_cast<V*>(data),
+                     nx, ntile, S, ostride, bstride, omask, K, static_cast<const V*>(tw), active,
+                     per_rhs));
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
@@ -152,12 +155,12 @@ hz_status line_sym_inv_t(const void* vhat, void* planes, int nx, long outer, lon
       HZ_TRY(smem_attr(k, C::col_pair_smem()));
       const int ntile = (nx / 2 + C::TB - 1) / C::TB;
       dim3 grid(unsigned(ntile * outer), unsigned((K + kpb - 1) / kpb), unsigned(batch));
-      k<<<grid, C::COL_THREADS, C::col_pair_smem(), st>>>(
-          static_cast<const float2*>(vhat), static_cast<float2*>(planes), nx, ntile, S, ostride,
-          n, K, static_cast<const float*>(xi2_x), static_cast<const float*>(xi2_o),
-          static_cast<const float*>(xi2_l), static_cast<const float2*>(symA),
-          static_cast<const float2*>(symG), smask, smO, smS, static_cast<const float4*>(tw2),
-          active);
+      HZ_CUDA(launch_pdl(k, dim3(grid), dim3(C::COL_THREADS), C::col_pair_smem(), st,
+                         static_cast<const float2*>(vhat), static_cast<float2*>(planes), nx, ntile,
+                         S, ostride, n, K, static_cast<const float*>(xi2_x),
+                         static_cast<const float*>(xi2_o), static_cast<const float*>(xi2_l),
+                         static_cast<const float2*>(symA), static_cast<const float2*>(symG), smask,
+                         smO, smS, static_cast<const float4*>(tw2), active));
       HZ_CUDA(cudaGetLastError());
       return HZ_OK;
     }
@@ -167,11 +170,12 @@ hz_status line_sym_inv_t(const void* vhat, void* planes, int nx, long outer, lon
   HZ_TRY(smem_attr(k, C::col_smem()));
   const int ntile = (nx + C::TB - 1) / C::TB;
   dim3 grid(unsigned(ntile * outer), unsigned((K + kpb - 1) / kpb), unsigned(batch));
-  k<<<grid, C::COL_THREADS, C::col_smem(), st>>>(
-      static_cast<const V*>(vhat), static_cast<V*>(planes), nx, ntile, S, ostride, n, K,
-      static_cast<const R*>(xi2_x), static_cast<const R*>(xi2_o), static_cast<const R*>(xi2_l),
-      static_cast<const V*>(symA), static_cast<const V*>(symG), smask, smO, smS,
-      static_cast<const V*>(tw), active);
+  HZ_CUDA(launch_pdl(k, dim3(grid), dim3(C::COL_THREADS), C::col_smem(), st,
+                     static_cast<const V*>(vhat), static_cast<V*>(planes), nx, ntile, S, ostride, n,
+                     K, static_cast<const R*>(xi2_x), static_cast<const R*>(xi2_o),
+                     static_cast<const R*>(xi2_l), static_cast<const V*>(symA),
+                     static_cast<const V*>(symG), smask, smO, smS, static_cast<const V*>(tw),
+                     active));
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }

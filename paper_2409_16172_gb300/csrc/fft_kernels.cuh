@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(LPB * LineCfg<R, N>::TPL_ROW)
 row_fwd_kernel(const double2* __restrict__ in, const double* __restrict__ scale,
                long rows_per_rhs, long nrows, const typename cvec<R>::T* __restrict__ tw,
                typename cvec<R>::T* __restrict__ out, const int* __restrict__ active) {
+  pdl_wait();
   using V = typename cvec<R>::T;
   using F = LineFFT<R, N, -1, 1, LineCfg<R, N>::WS, typename LineCfg<R, N>::RP>;
   constexpr int TPL = F::TPL, E = F::E;
@@ -155,6 +156,7 @@ row_inv_acc_kernel(const typename cvec<R>::T* __restrict__ planes,
                    long rows_per_rhs, long nrows, long n, R inv_n,
                    const typename cvec<R>::T* __restrict__ tw, OutT* __restrict__ out,
                    const int* __restrict__ active) {
+  pdl_wait();
   using V = typename cvec<R>::T;
   constexpr bool WS = LineCfg<R, N>::WS;
   using F = LineFFT<R, N, +1, 1, WS, typename LineCfg<R, N>::RP>;
@@ -274,6 +276,7 @@ row_inv_inplace_kernel(typename cvec<R>::T* __restrict__ planes,
                        const unsigned long long* __restrict__ rowmask, int K, long rows_per_rhs,
                        long nrows, long n, const typename cvec<R>::T* __restrict__ tw,
                        const int* __restrict__ active) {
+  pdl_wait();
   using V = typename cvec<R>::T;
   using F = LineFFT<R, N, +1, 1, LineCfg<R, N>::WS, typename LineCfg<R, N>::RP>;
   constexpr int TPL = F::TPL, E = F::E;
@@ -304,6 +307,7 @@ weighted_gather_kernel(const typename cvec<R>::T* __restrict__ planes,
                        const typename RecT<R>::T* __restrict__ rec, const uchar2* __restrict__ segtab,
                        int K, long n, long total, R inv_n, OutT* __restrict__ out,
                        const int* __restrict__ active) {
+  pdl_wait();
   using V = typename cvec<R>::T;
   for (long i = long(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
        i += long(gridDim.x) * blockDim.x) {
@@ -348,6 +352,7 @@ line_pass_kernel(typename cvec<R>::T* __restrict__ data, int nx, int ntile, long
                  long bstride, const unsigned long long* __restrict__ omask, int K,
                  const typename cvec<R>::T* __restrict__ tw, const int* __restrict__ active,
                  int per_rhs) {
+  pdl_wait();
   using V = typename cvec<R>::T;
   constexpr int TB = LineCfg<R, N>::TB;
   using F = LineFFT<R, N, SIGN, TB, false, typename LineCfg<R, N>::CP>;
@@ -392,6 +397,7 @@ line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
                     const typename cvec<R>::T* __restrict__ symG,
                     const unsigned long long* __restrict__ smask, long smO, long smS,
                     const typename cvec<R>::T* __restrict__ tw, const int* __restrict__ active) {
+  pdl_wait();
   using V = typename cvec<R>::T;
   constexpr int TB = LineCfg<R, N>::TB;
   using F = LineFFT<R, N, +1, TB, false, typename LineCfg<R, N>::CP>;
@@ -467,6 +473,7 @@ line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ p
                          const float2* __restrict__ symG,
                          const unsigned long long* __restrict__ smask, long smO, long smS,
                          const float4* __restrict__ tw2, const int* __restrict__ active) {
+  pdl_wait();
   constexpr int TB = LineCfg<float, N>::TB;
   using F = LineFFT<float, N, +1, TB, false, typename LineCfg<float, N>::CP, PV>;
   constexpr int E = F::E;

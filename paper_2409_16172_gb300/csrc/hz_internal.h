@@ -1,5 +1,6 @@
 // Internal definitions shared by the library's translation units.
 #pragma once
+#include <utility>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -72,6 +73,33 @@ struct AxisTables {
   double* xi2_64 = nullptr;  // squared wavenumber per bin
   float* xi2_32 = nullptr;
 };
+
+#ifdef __CUDACC__
+// Programmatic dependent launch.  Every hot-path kernel starts with
+// pdl_wait() (griddepcontrol.wait), which returns once the kernel before it
+// on the stream has finished and its writes are visible, and touches no
+// global memory before it; launched with launch_pdl, a kernel's launch and
+// block scheduling then overlap the tail of the previous kernel (also as
+// programmatic edges inside captured graphs).  Without a PDL predecessor the
+// wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+#endif
 
 #ifdef __CUDACC__
 // float -> double by moving the bit fields with integer operations, so that

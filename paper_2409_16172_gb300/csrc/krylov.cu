@@ -60,6 +60,7 @@ template <int VC>
 __global__ void __launch_bounds__(KT, DotsCfg<VC>::MINB)
 dots_kernel(const double2* __restrict__ V, long ldb, const double2* __restrict__ w, long wstride,
             long n, int j, int vpc, const int* __restrict__ active, double2* __restrict__ partial) {
+  pdl_wait();
   constexpr int NA = DotsCfg<VC>::NA;
   const int b = blockIdx.y;
   const int i0 = blockIdx.z * vpc;
@@ -150,6 +151,7 @@ dots_kernel(const double2* __restrict__ V, long ldb, const double2* __restrict__
 __global__ void __launch_bounds__(KT)
 reduce_c_kernel(const double2* __restrict__ part, int nblk, int jp1, int ldo,
                 double2* __restrict__ out) {
+  pdl_wait();
   const long q = blockIdx.x;
   double v[2] = {0.0, 0.0};
   for (int i = threadIdx.x; i < nblk; i += KT) {
@@ -165,6 +167,7 @@ reduce_c_kernel(const double2* __restrict__ part, int nblk, int jp1, int ldo,
 
 __global__ void __launch_bounds__(KT)
 reduce_r_kernel(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+  pdl_wait();
   const long q = blockIdx.x;
   double v[1] = {0.0};
   for (int i = threadIdx.x; i < nblk; i += KT) v[0] += part[q * nblk + i];
@@ -179,6 +182,7 @@ __global__ void __launch_bounds__(KT)
 update_kernel(const double2* __restrict__ V, long ldb, double2* __restrict__ w, long wstride,
               long n, int j, const double2* __restrict__ S, int ldS, const double* __restrict__ sigma,
               int ldsig, const int* __restrict__ active, double* __restrict__ partial) {
+  pdl_wait();
   const int b = blockIdx.y;
   __shared__ double2 coef[HZ_MAX_RESTART + 1];
   const bool on = active[b] != 0;
@@ -273,6 +277,7 @@ __device__ __forceinline__ double2 shfl_up_d2(double2 v, int o) {
 // evaluated as a warp scan of affine maps (each lane composes a contiguous
 // chunk, a shuffle scan composes the chunks) instead of j serial steps.
 __global__ void givens_kernel(KsDev ks, int j, int nrhs) {
+  pdl_wait();
   const int b = blockIdx.x;
   const int lane = threadIdx.x;
   if (b >= nrhs || !ks.active[b]) return;
@@ -401,6 +406,7 @@ template <typename ZT>
 __global__ void __launch_bounds__(KT)
 solution_update_kernel(const ZT* __restrict__ Z, long ldb, double2* __restrict__ u, long ustride,
                        long n, const double2* __restrict__ y, int ldy, const int* __restrict__ jn) {
+  pdl_wait();
   const int b = blockIdx.y;
   const int J = jn[b];
   if (J <= 0) return;
@@ -438,6 +444,7 @@ __global__ void __launch_bounds__(KT)
 combine_kernel(const double2* __restrict__ V, long ldb, double2* __restrict__ out, long ostride,
                long n, const double2* __restrict__ y, int ldy, const double* __restrict__ sigma,
                int ldsig, const int* __restrict__ jn) {
+  pdl_wait();
   const int b = blockIdx.y;
   const int J = jn[b];
   __shared__ double2 ys[HZ_MAX_RESTART];
@@ -463,6 +470,7 @@ combine_kernel(const double2* __restrict__ V, long ldb, double2* __restrict__ ou
 // u += t (element-wise, FP64), for active right-hand sides with jn > 0
 __global__ void axpy_kernel(double2* __restrict__ u, const double2* __restrict__ t, long stride,
                             long n, const int* __restrict__ jn) {
+  pdl_wait();
   const int b = blockIdx.y;
   if (jn[b] <= 0) return;
   for (long p = long(blockIdx.x) * KT + threadIdx.x; p < n; p += long(gridDim.x) * KT) {
@@ -474,6 +482,7 @@ __global__ void axpy_kernel(double2* __restrict__ u, const double2* __restrict__
 // out[b] = sigma[b] V[b]: the operator input of an unpreconditioned step
 __global__ void scale_copy_kernel(const double2* __restrict__ V, const double* __restrict__ sigma,
                                   double2* __restrict__ out, long n, const int* __restrict__ active) {
+  pdl_wait();
   const int b = blockIdx.y;
   if (!active[b]) return;
   const double s = sigma[b];
@@ -486,6 +495,7 @@ __global__ void scale_copy_kernel(const double2* __restrict__ V, const double* _
 // |x|^2 partials of nrhs vectors
 __global__ void __launch_bounds__(KT)
 norm2_kernel(const double2* __restrict__ x, long stride, long n, double* __restrict__ partial) {
+  pdl_wait();
   const int b = blockIdx.y;
   double v[1] = {0.0};
   for (long p = long(blockIdx.x) * KT + threadIdx.x; p < n; p += long(gridDim.x) * KT) {
@@ -528,12 +538,16 @@ hz_status launch_dots(const double2* V, long ldb, const double2* w, long wstride
   if (per > cap) per = cap;
   const int nblk = int(per < 1 ? 1 : per);
   if (vc == 2)
-    dots_kernel<2><<<dim3(nblk, nrhs, nchunk), KT, 0, st>>>(V, ldb, w, wstride, n, j, vpc, active, partial);
+    HZ_CUDA(launch_pdl(dots_kernel<2>, dim3(nblk, nrhs, nchunk), dim3(KT), 0, st, V, ldb, w,
+                       wstride, n, j, vpc, active, partial));
   else if (vc == 4)
-    dots_kernel<4><<<dim3(nblk, nrhs, nchunk), KT, 0, st>>>(V, ldb, w, wstride, n, j, vpc, active, partial);
+    HZ_CUDA(launch_pdl(dots_kernel<4>, dim3(nblk, nrhs, nchunk), dim3(KT), 0, st, V, ldb, w,
+                       wstride, n, j, vpc, active, partial));
   else
-    dots_kernel<VCMAX><<<dim3(nblk, nrhs, nchunk), KT, 0, st>>>(V, ldb, w, wstride, n, j, vpc, active, partial);
-  reduce_c_kernel<<<unsigned(nrhs * (j + 1)), KT, 0, st>>>(partial, nblk, j + 1, ldS, S);
+    HZ_CUDA(launch_pdl(dots_kernel<VCMAX>, dim3(nblk, nrhs, nchunk), dim3(KT), 0, st, V, ldb, w,
+                       wstride, n, j, vpc, active, partial));
+  HZ_CUDA(launch_pdl(reduce_c_kernel, dim3(unsigned(nrhs * (j + 1))), dim3(KT), 0, st, partial,
+                     nblk, j + 1, ldS, S));
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
@@ -544,19 +558,20 @@ hz_status launch_update(const double2* V, long ldb, double2* w, long wstride, lo
                         cudaStream_t st) {
   const int nblk = krylov_blocks_bps(n, nrhs, 1, tn.upd_bps);
   if (norm) {
-    update_kernel<true><<<dim3(nblk, nrhs), KT, 0, st>>>(V, ldb, w, wstride, n, j, S, ldS, sigma,
-                                                          ldsig, active, partial);
-    reduce_r_kernel<<<unsigned(nrhs), KT, 0, st>>>(partial, nblk, nrm2);
+    HZ_CUDA(launch_pdl(update_kernel<true>, dim3(nblk, nrhs), dim3(KT), 0, st, V, ldb, w, wstride,
+                       n, j, S, ldS, sigma, ldsig, active, partial));
+    HZ_CUDA(launch_pdl(reduce_r_kernel, dim3(unsigned(nrhs)), dim3(KT), 0, st, partial, nblk,
+                       nrm2));
   } else {
-    update_kernel<false><<<dim3(nblk, nrhs), KT, 0, st>>>(V, ldb, w, wstride, n, j, S, ldS, sigma,
-                                                           ldsig, active, nullptr);
+    HZ_CUDA(launch_pdl(update_kernel<false>, dim3(nblk, nrhs), dim3(KT), 0, st, V, ldb, w, wstride,
+                       n, j, S, ldS, sigma, ldsig, active, nullptr));
   }
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
 
 hz_status launch_givens(const KsDev& ks, int j, int nrhs, cudaStream_t st) {
-  givens_kernel<<<nrhs, 32, 0, st>>>(ks, j, nrhs);
+  HZ_CUDA(launch_pdl(givens_kernel, dim3(nrhs), dim3(32), 0, st, ks, j, nrhs));
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
@@ -566,11 +581,11 @@ hz_status launch_solution_update(int zprec, const void* Z, long ldb, double2* u,
                                  cudaStream_t st) {
   const int nblk = krylov_blocks(n, nrhs, 1);
   if (zprec == 0)
-    solution_update_kernel<double2><<<dim3(nblk, nrhs), KT, 0, st>>>(
-        static_cast<const double2*>(Z), ldb, u, ustride, n, y, ldy, jn);
+    HZ_CUDA(launch_pdl(solution_update_kernel<double2>, dim3(nblk, nrhs), dim3(KT), 0, st,
+                       static_cast<const double2*>(Z), ldb, u, ustride, n, y, ldy, jn));
   else
-    solution_update_kernel<float2><<<dim3(nblk, nrhs), KT, 0, st>>>(
-        static_cast<const float2*>(Z), ldb, u, ustride, n, y, ldy, jn);
+    HZ_CUDA(launch_pdl(solution_update_kernel<float2>, dim3(nblk, nrhs), dim3(KT), 0, st,
+                       static_cast<const float2*>(Z), ldb, u, ustride, n, y, ldy, jn));
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
@@ -579,7 +594,8 @@ hz_status launch_combine(const double2* V, long ldb, double2* out, long ostride,
                          const double2* y, int ldy, const double* sigma, int ldsig, const int* jn,
                          cudaStream_t st) {
   const int nblk = krylov_blocks(n, nrhs, 1);
-  combine_kernel<<<dim3(nblk, nrhs), KT, 0, st>>>(V, ldb, out, ostride, n, y, ldy, sigma, ldsig, jn);
+  HZ_CUDA(launch_pdl(combine_kernel, dim3(nblk, nrhs), dim3(KT), 0, st, V, ldb, out, ostride, n, y,
+                     ldy, sigma, ldsig, jn));
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
@@ -587,7 +603,8 @@ hz_status launch_combine(const double2* V, long ldb, double2* out, long ostride,
 hz_status launch_scale_copy(const double2* V, const double* sigma, double2* out, long n, int nrhs,
                            const int* active, cudaStream_t st) {
   const int nblk = krylov_blocks(n, nrhs, 1);
-  scale_copy_kernel<<<dim3(nblk, nrhs), KT, 0, st>>>(V, sigma, out, n, active);
+  HZ_CUDA(launch_pdl(scale_copy_kernel, dim3(nblk, nrhs), dim3(KT), 0, st, V, sigma, out, n,
+                     active));
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
@@ -595,21 +612,21 @@ hz_status launch_scale_copy(const double2* V, const double* sigma, double2* out,
 hz_status launch_axpy(double2* u, const double2* t, long stride, long n, int nrhs, const int* jn,
                       cudaStream_t st) {
   const int nblk = krylov_blocks(n, nrhs, 1);
-  axpy_kernel<<<dim3(nblk, nrhs), KT, 0, st>>>(u, t, stride, n, jn);
+  HZ_CUDA(launch_pdl(axpy_kernel, dim3(nblk, nrhs), dim3(KT), 0, st, u, t, stride, n, jn));
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
 
 hz_status launch_norm2(const double2* x, long stride, long n, int nrhs, double* partial, int nblk,
                        double* out, cudaStream_t st) {
-  norm2_kernel<<<dim3(nblk, nrhs), KT, 0, st>>>(x, stride, n, partial);
-  reduce_r_kernel<<<unsigned(nrhs), KT, 0, st>>>(partial, nblk, out);
+  HZ_CUDA(launch_pdl(norm2_kernel, dim3(nblk, nrhs), dim3(KT), 0, st, x, stride, n, partial));
+  HZ_CUDA(launch_pdl(reduce_r_kernel, dim3(unsigned(nrhs)), dim3(KT), 0, st, partial, nblk, out));
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
 
 hz_status launch_reduce_r(const double* partial, int nblk, int nq, double* out, cudaStream_t st) {
-  reduce_r_kernel<<<unsigned(nq), KT, 0, st>>>(partial, nblk, out);
+  HZ_CUDA(launch_pdl(reduce_r_kernel, dim3(unsigned(nq)), dim3(KT), 0, st, partial, nblk, out));
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }

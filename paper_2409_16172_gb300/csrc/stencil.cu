@@ -30,6 +30,7 @@ stencil_kernel(const InT* __restrict__ x, double2* __restrict__ y, const double2
                double w2, double rho_y, double rho_z, double diag, int nx, int ny, int nz, long n,
                long in_stride, long out_stride, const int* __restrict__ active,
                double* __restrict__ partial) {
+  pdl_wait();
   const int b = blockIdx.y;
   double nrm = 0.0;
   const bool on = !active || active[b];
@@ -118,13 +119,15 @@ hz_status launch_stencil(const hz_medium* m, int in_prec, const void* x, long in
   dim3 grid(unsigned(stencil_blocks(m->n)), unsigned(nrhs));
   const StencilConsts k = stencil_consts(m);
   if (in_prec == 0)
-    stencil_kernel<double2, false><<<grid, ST_THREADS, 0, st>>>(
-        static_cast<const double2*>(x), y, nullptr, m->gamma2, m->a, m->omega, k.w2, k.rho_y,
-        k.rho_z, k.diag, m->nx, m->ny, m->nz, m->n, in_stride, out_stride, active, nullptr);
+    HZ_CUDA(launch_pdl(stencil_kernel<double2, false>, dim3(grid), dim3(ST_THREADS), 0, st,
+                       static_cast<const double2*>(x), y, nullptr, m->gamma2, m->a, m->omega, k.w2,
+                       k.rho_y, k.rho_z, k.diag, m->nx, m->ny, m->nz, m->n, in_stride, out_stride,
+                       active, nullptr));
   else
-    stencil_kernel<float2, false><<<grid, ST_THREADS, 0, st>>>(
-        static_cast<const float2*>(x), y, nullptr, m->gamma2, m->a, m->omega, k.w2, k.rho_y,
-        k.rho_z, k.diag, m->nx, m->ny, m->nz, m->n, in_stride, out_stride, active, nullptr);
+    HZ_CUDA(launch_pdl(stencil_kernel<float2, false>, dim3(grid), dim3(ST_THREADS), 0, st,
+                       static_cast<const float2*>(x), y, nullptr, m->gamma2, m->a, m->omega, k.w2,
+                       k.rho_y, k.rho_z, k.diag, m->nx, m->ny, m->nz, m->n, in_stride, out_stride,
+                       active, nullptr));
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
@@ -134,9 +137,9 @@ hz_status launch_residual(const hz_medium* m, const double2* u, const double2* f
                           cudaStream_t st) {
   dim3 grid(unsigned(stencil_blocks(m->n)), unsigned(nrhs));
   const StencilConsts k = stencil_consts(m);
-  stencil_kernel<double2, true><<<grid, ST_THREADS, 0, st>>>(
-      u, r, f, m->gamma2, m->a, m->omega, k.w2, k.rho_y, k.rho_z, k.diag, m->nx, m->ny, m->nz,
-      m->n, stride, stride, active, partial);
+  HZ_CUDA(launch_pdl(stencil_kernel<double2, true>, dim3(grid), dim3(ST_THREADS), 0, st, u, r, f,
+                     m->gamma2, m->a, m->omega, k.w2, k.rho_y, k.rho_z, k.diag, m->nx, m->ny, m->nz,
+                     m->n, stride, stride, active, partial));
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }

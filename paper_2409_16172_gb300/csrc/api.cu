@@ -168,7 +168,7 @@ hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* s
                   B * K * (5.0 * dn * l2(ny) + 14.0 * dn));
     HZ_TRY(oy->line_sym_inv(prec, p->tmp, p->planes, nx, 1, nx, 0, n, m->K, nrhs, xi(tx), nullptr,
                             xi(ty), A, G, m->rowmask, 0, 1, tw(ty), tw2(ty), st, active,
-                            p->tune.syminv_kpb));
+                            p->tune.syminv_kpb, p->tune.col_pair));
   } else {
     const FftOps* oz = fft_ops(nz);
     const AxisTables& tz = m->ax[2];
@@ -183,7 +183,7 @@ hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* s
                     B * K * (5.0 * dn * l2(nz) + 14.0 * dn));
       HZ_TRY(oz->line_sym_inv(prec, p->tmp, p->planes, nx, ny, slab, nx, n, m->K, nrhs, xi(tx),
                               xi(ty), xi(tz), A, G, m->slabmask, 0, 1, tw(tz), tw2(tz), st,
-                              active, p->tune.syminv_kpb));
+                              active, p->tune.syminv_kpb, p->tune.col_pair));
     }
     {
       PhaseScope ps(st, PH_LINE, B * 2.0 * s * m->slabk_used * slab,

@@ -143,19 +143,28 @@ hz_status line_sym_inv_t(const void* vhat, void* planes, int nx, long outer, lon
                          long n, int K, int batch, const void* xi2_x, const void* xi2_o,
                          const void* xi2_l, const void* symA, const void* symG,
                          const unsigned long long* smask, long smO, long smS, const void* tw,
-                         const void* tw2, cudaStream_t st, const int* active, int kpb) {
+                         const void* tw2, cudaStream_t st, const int* active, int kpb,
+                         int pair) {
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
   // nodes per block: 1, 2 or 4
   kpb = kpb >= 4 ? 4 : (kpb >= 2 ? 2 : 1);
   if constexpr (std::is_same<R, float>::value) {
     if (tw2 && nx % 2 == 0) {
-      auto k = kpb == 4 ? line_sym_inv_pair_kernel<N, 4>
-                        : (kpb == 2 ? line_sym_inv_pair_kernel<N, 2> : line_sym_inv_pair_kernel<N, 1>);
-      HZ_TRY(smem_attr(k, C::col_pair_smem()));
-      const int ntile = (nx / 2 + C::TB - 1) / C::TB;
+      // pair > 1: half-size blocks
+      const bool half = pair > 1;
+      constexpr int TB = C::TB, TH = C::TB_HALF;
+      auto k = half ? (kpb == 4 ? line_sym_inv_pair_kernel<N, 4, TH>
+                                : (kpb == 2 ? line_sym_inv_pair_kernel<N, 2, TH>
+                                            : line_sym_inv_pair_kernel<N, 1, TH>))
+                    : (kpb == 4 ? line_sym_inv_pair_kernel<N, 4, TB>
+                                : (kpb == 2 ? line_sym_inv_pair_kernel<N, 2, TB>
+                                            : line_sym_inv_pair_kernel<N, 1, TB>));
+      const int tb = half ? TH : TB;
+      HZ_TRY(smem_attr(k, C::col_pair_smem(tb)));
+      const int ntile = (nx / 2 + tb - 1) / tb;
       dim3 grid(unsigned(ntile * outer), unsigned((K + kpb - 1) / kpb), unsigned(batch));
-      HZ_CUDA(launch_pdl(k, dim3(grid), dim3(C::COL_THREADS), C::col_pair_smem(), st,
+      HZ_CUDA(launch_pdl(k, dim3(grid), dim3(tb * C::TPL), C::col_pair_smem(tb), st,
                          static_cast<const float2*>(vhat), static_cast<float2*>(planes), nx, ntile,
                          S, ostride, n, K, static_cast<const float*>(xi2_x),
                          static_cast<const float*>(xi2_o), static_cast<const float*>(xi2_l),
@@ -184,14 +193,14 @@ hz_status line_sym_inv(int prec, const void* vhat, void* planes, int nx, long ou
                        long ostride, long n, int K, int batch, const void* xi2_x,
                        const void* xi2_o, const void* xi2_l, const void* symA, const void* symG,
                        const unsigned long long* smask, long smO, long smS, const void* tw,
-                       const void* tw2, cudaStream_t st, const int* active, int kpb) {
+                       const void* tw2, cudaStream_t st, const int* active, int kpb, int pair) {
   return prec == 0
              ? line_sym_inv_t<double>(vhat, planes, nx, outer, S, ostride, n, K, batch, xi2_x,
                                       xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, nullptr, st,
-                                      active, kpb)
+                                      active, kpb, 0)
              : line_sym_inv_t<float>(vhat, planes, nx, outer, S, ostride, n, K, batch, xi2_x,
                                      xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, tw2, st,
-                                     active, kpb);
+                                     active, kpb, pair);
 }
 
 const FftOps ops = {N, row_fwd, row_inv_acc, line_pass, line_sym_inv};

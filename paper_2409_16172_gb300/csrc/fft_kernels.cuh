@@ -3,19 +3,25 @@
 //   row_fwd       forward FFT along x of the input vector (c128 in, scaled by
 //                 the Krylov normalisation, rounded to the working precision)
 //   line_pass     forward or inverse FFT along a strided axis (y, and z in 3D)
-//   line_sym_inv  last axis, one block per (column tile, node k): read vhat,
-//                 multiply by q_k(|xi|^2) = 1 / (w^2 + i w a_k - gamma_k^2 |xi|^2)
-//                 (Eqn. 021, recomputed, never stored), inverse FFT along the
-//                 axis, write plane k
+//   line_sym_inv  last axis, one block per (column tile, group of 1/2/4 nodes):
+//                 read vhat, multiply by q_k(|xi|^2) =
+//                 1 / (w^2 + i w a_k - gamma_k^2 |xi|^2) (Eqn. 021, recomputed,
+//                 never stored), inverse FFT along the axis, write plane k on
+//                 the rows / slabs that use node k; complex64 also with two
+//                 columns per thread in packed f32x2 arithmetic
 //   row_inv_acc   inverse FFT along x of every plane a row needs, then the
 //                 weighted sum z = (1/n) sum_k w_k(x) plane_k(x) (Eqn. 405:
-//                 two non-zero hat weights per point)
+//                 two non-zero hat weights per point); for few rows, an
+//                 in-place inverse of every used (row, node) line and a gather
 //
 // Layout: vectors [rhs][z][y][x] (x fastest); planes [rhs][k][z][y][x].
-// Every kernel stages its lines through padded shared memory and runs the
-// Stockham engine of fft_engine.cuh; global loads and stores are coalesced
-// along x (rows directly, strided axes in tiles of TB adjacent columns whose
-// lines are interleaved in shared memory).
+// Every kernel reads its inputs straight into registers in the transform's
+// first-stage order, exchanges through padded shared memory between stages
+// (Stockham engine of fft_engine.cuh) and writes from registers after the
+// last stage; global accesses are coalesced along x (rows directly, strided
+// axes in tiles of TB adjacent columns whose lines are interleaved in shared
+// memory).  Every kernel begins with pdl_wait() (programmatic dependent
+// launch).
 #pragma once
 #include "fft_engine.cuh"
 #include "hz_internal.h"
@@ -54,7 +60,8 @@ template <typename R, int N> struct LineCfg {
     return stage_offset(lines) + size_t(lines) * 2 * N * VB;
   }
   static constexpr size_t col_smem() { return size_t(TB) * padded_len(N) * VB; }
-  static constexpr size_t col_pair_smem() { return size_t(TB) * padded_len(N) * 16; }
+  static constexpr size_t col_pair_smem(int tb = TB) { return size_t(tb) * padded_len(N) * 16; }
+  static constexpr int TB_HALF = TB > 1 ? TB / 2 : 1;
 };
 
 // 16-byte asynchronous global -> shared copies (L2 only), in groups.
@@ -463,9 +470,12 @@ line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
 // The complex64 symbol pass with two adjacent columns per thread (x, x + 1;
 // nx even), their values paired in f32x2 registers (PV): the same arithmetic
 // per column as line_sym_inv_kernel, in packed FP32 instructions, 16-byte
-// global accesses, and tw2 = the (re, re, im, im) twiddle table.
-template <int N, int KPB>
-__global__ void __launch_bounds__(LineCfg<float, N>::COL_THREADS, KPB == 1 ? 2 : 1)
+// global accesses, and tw2 = the (re, re, im, im) twiddle table.  TB: column
+// pairs per block (the scalar kernel's TB, or half of it: the same registers
+// per thread, smaller blocks).
+template <int N, int KPB, int TB>
+__global__ void __launch_bounds__(TB * LineCfg<float, N>::TPL,
+                                  KPB == 1 ? 2 * LineCfg<float, N>::TB / TB : 1)
 line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ planes, int nx,
                          int ntile, long S, long ostride, long n, int K,
                          const float* __restrict__ xi2_x, const float* __restrict__ xi2_o,
@@ -474,7 +484,6 @@ line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ p
                          const unsigned long long* __restrict__ smask, long smO, long smS,
                          const float4* __restrict__ tw2, const int* __restrict__ active) {
   pdl_wait();
-  constexpr int TB = LineCfg<float, N>::TB;
   using F = LineFFT<float, N, +1, TB, false, typename LineCfg<float, N>::CP, PV>;
   constexpr int E = F::E;
   static_assert(KPB == 1 || KPB == 2 || KPB == 4, "nodes per block");

@@ -177,13 +177,13 @@ struct FftOps {
                          cudaStream_t st, const int* active, int per_rhs);
   // last axis: symbol multiply of the spectrum and inverse FFT, one plane per k;
   // tw2 (complex64 only, nullable): the paired twiddle table, selects the
-  // two-columns-per-thread kernel when nx is even
+  // two-columns-per-thread kernel when nx is even; pair > 1 halves its blocks
   hz_status (*line_sym_inv)(int prec, const void* vhat, void* planes, int nx, long outer, long S,
                             long ostride, long n, int K, int batch, const void* xi2_x,
                             const void* xi2_o, const void* xi2_l, const void* symA,
                             const void* symG, const unsigned long long* smask, long smO,
                             long smS, const void* tw, const void* tw2, cudaStream_t st,
-                            const int* active, int kpb);
+                            const int* active, int kpb, int pair);
 };
 
 const FftOps* fft_ops(int N);
@@ -220,7 +220,8 @@ struct Tune {
   int upd_bps = 4;
   int syminv_kpb = 1;
   int rowinv_mode = 0;  // FftOps::row_inv_acc mode
-  int col_pair = 1;     // complex64 symbol pass: two columns per thread
+  int col_pair = 1;     // complex64 symbol pass: two columns per thread (2: in
+                        // half-size blocks)
 };
 }
 

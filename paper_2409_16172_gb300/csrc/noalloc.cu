@@ -91,7 +91,7 @@ extern "C" hz_status hz_apply_preconditioner_noalloc(const hz_medium* med, const
   int launches = 2;
   if (med->dim == 2) {
     HZ_TRY(oy->line_sym_inv(prec, tmp, planes, nx, 1, nx, 0, n, med->K, nrhs, xi(tx), nullptr, xi(ty),
-                            A, G, med->rowmask, 0, 1, tw(ty), tw2(ty), st, nullptr, 1));
+                            A, G, med->rowmask, 0, 1, tw(ty), tw2(ty), st, nullptr, 1, 1));
     launches += 1;
   } else {
     const FftOps* oz = fft_ops(nz);
@@ -99,7 +99,7 @@ extern "C" hz_status hz_apply_preconditioner_noalloc(const hz_medium* med, const
     HZ_TRY(oz->line_pass(prec, -1, tmp, nx, ny, slab, nx, n, nrhs, nullptr, med->K, tw(tz), st,
                          nullptr, 1));
     HZ_TRY(oz->line_sym_inv(prec, tmp, planes, nx, ny, slab, nx, n, med->K, nrhs, xi(tx), xi(ty),
-                            xi(tz), A, G, med->slabmask, 0, 1, tw(tz), tw2(tz), st, nullptr, 1));
+                            xi(tz), A, G, med->slabmask, 0, 1, tw(tz), tw2(tz), st, nullptr, 1, 1));
     HZ_TRY(oy->line_pass(prec, +1, planes, nx, nz, nx, slab, n, nrhs * med->K, med->slabmask, med->K,
                          tw(ty), st, nullptr, med->K));
     launches += 3;

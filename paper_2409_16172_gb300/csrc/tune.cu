@@ -73,7 +73,7 @@ extern "C" hz_status hz_plan_set_tune(hz_plan* plan, const hz_tune_report* r) {
   const bool ok = (r->dots_vc == 2 || r->dots_vc == 4 || r->dots_vc == 8) && r->dots_bps >= 1 &&
                   r->dots_bps <= 4 && r->upd_bps >= 1 && r->upd_bps <= 8 &&
                   (r->syminv_kpb == 1 || r->syminv_kpb == 2 || r->syminv_kpb == 4) &&
-                  r->rowinv_mode >= 0 && r->rowinv_mode <= 2 && (r->col_pair == 0 || r->col_pair == 1);
+                  r->rowinv_mode >= 0 && r->rowinv_mode <= 2 && r->col_pair >= 0 && r->col_pair <= 2;
   if (!ok) return set_error(HZ_ERR_INVALID_ARG, "launch shape out of range");
   plan->tune.dots_vc = r->dots_vc;
   plan->tune.dots_bps = r->dots_bps;
@@ -175,8 +175,8 @@ extern "C" hz_status hz_plan_autotune(hz_plan* plan, void* stream, hz_tune_repor
   tbest = 1e30f;
   const int prec = p->opts.precision;
   void* out = p->Z;
-  for (int pair : {1, 0}) {
-    if (pair == 0 && prec == 0) continue;  // FP64 has one form
+  for (int pair : {1, 2, 0}) {
+    if (pair != 1 && prec == 0) continue;  // FP64 has one form
     for (int kpb : {1, 2, 4}) {
       if (kpb > 1 && kpb > med->K) break;
       p->tune = best;

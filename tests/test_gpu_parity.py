@@ -219,7 +219,7 @@ def test_apply_every_launch_shape(hz, shape):
     for prec, tol in ((0, 1e-10), (1, 5e-5)):
         plan = hz.Plan(med_g, precision=prec, max_nrhs=2)
         for kpb, mode, pair in ((1, 1, 1), (1, 2, 0), (2, 2, 1), (4, 1, 0), (4, 2, 1), (2, 0, 1),
-                                (1, 0, 0)):
+                                (1, 0, 0), (1, 2, 2), (2, 1, 2), (4, 0, 2)):
             plan.set_tune(syminv_kpb=kpb, rowinv_mode=mode, col_pair=pair)
             got = plan.apply_preconditioner(_dev(v), precision=prec).cpu().numpy()
             assert rel(got, ref) <= tol, (prec, kpb, mode, pair, rel(got, ref))
@@ -230,7 +230,7 @@ def test_set_tune_rejects_out_of_range(hz):
     med_g, _ = media(hz, p)
     plan = hz.Plan(med_g, precision=1)
     for bad in (dict(syminv_kpb=3), dict(rowinv_mode=3), dict(dots_vc=5), dict(upd_bps=0),
-                dict(dots_bps=5), dict(upd_bps=9), dict(col_pair=2)):
+                dict(dots_bps=5), dict(upd_bps=9), dict(col_pair=3)):
         with pytest.raises(hz.HzError):
             plan.set_tune(**bad)
 

@@ -173,7 +173,9 @@ typedef struct {
   float upd_us, upd_us_default;
   float apply_us, apply_us_default;   /* whole preconditioner apply        */
   int rowinv_mode;          /* x-inverse pass: 0 by grid size, 1 in place
-                               then a gather of the weighted sum, 2 fused  */
+                               then a gather of the weighted sum, 2 fused,
+                               3 one line per (row, node) in use, added
+                               into the cleared output                     */
   int col_pair;             /* complex64 symbol pass: 1 two columns per
                                thread in packed FP32, 2 the same in blocks
                                of half the size, 0 one column              */
@@ -183,7 +185,7 @@ hz_status hz_plan_autotune(hz_plan* plan, void* stream, hz_tune_report* report);
 
 /* Sets the plan's launch shapes from a report (e.g. one saved from an
  * earlier hz_plan_autotune): dots_vc in {2, 4, 8}, dots_bps in 1..4, upd_bps
- * in 1..8, syminv_kpb in {1, 2, 4}, rowinv_mode in {0, 1, 2}, col_pair in
+ * in 1..8, syminv_kpb in {1, 2, 4}, rowinv_mode in {0, 1, 2, 3}, col_pair in
  * {0, 1, 2}; the timing
  * fields are ignored.  HZ_ERR_INVALID_ARG for any other value. */
 hz_status hz_plan_set_tune(hz_plan* plan, const hz_tune_report* report);

@@ -153,9 +153,13 @@ hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* s
   const double rb = prec == 0 ? 8.0 : 4.0;          // interpolation record
   const double B = nrhs, K = m->K, dn = double(n);
   auto l2 = [](int N) { return std::log2(double(N)); };
+  // the scattering x-inverse pass adds into out: cleared by the x-forward pass
+  const bool scatter = p->tune.rowinv_mode == 3;
   {
-    PhaseScope ps(st, PH_ROW_FWD, B * dn * (16.0 + s), B * 5.0 * dn * l2(nx));
-    HZ_TRY(ox->row_fwd(prec, in, scale, rows, rows * nrhs, tw(tx), p->tmp, st, active));
+    PhaseScope ps(st, PH_ROW_FWD, B * dn * (16.0 + s + (scatter ? so : 0.0)),
+                  B * 5.0 * dn * l2(nx));
+    HZ_TRY(ox->row_fwd(prec, in, scale, rows, rows * nrhs, tw(tx), p->tmp, st, active,
+                       scatter ? out : nullptr, long(nx) * long(so)));
   }
   // forward FFT along every axis but x, in place on tmp
   {
@@ -197,7 +201,7 @@ hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* s
                   B * (m->rowk_used * 5.0 * nx * l2(nx) + 8.0 * dn));
     HZ_TRY(ox->row_inv_acc(prec, out_kind, p->planes, rec, m->segtab, m->nseg, m->rowmask, m->K,
                            rows, rows * nrhs, n, 1.0 / double(n), tw(tx), out, st, active,
-                           p->tune.rowinv_mode));
+                           p->tune.rowinv_mode, m->rowitems, m->nitems));
   }
   return HZ_OK;
 }

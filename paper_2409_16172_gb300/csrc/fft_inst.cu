@@ -25,7 +25,11 @@ hz_status smem_attr(K kernel, size_t bytes) {
 
 template <typename R>
 hz_status row_fwd_t(const double2* in, const double* scale, long rows_per_rhs, long nrows,
-                    const void* tw, void* out, cudaStream_t st, const int* active) {
+                    const void* tw, void* out, cudaStream_t st, const int* active, void* zero,
+                    long zero_row_bytes) {
+  if (zero && zero_row_bytes % 16 != 0) return HZ_ERR_INVALID_ARG;
+  uint4* z = static_cast<uint4*>(zero);
+  const int zc = int(zero_row_bytes / 16);
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
   // blocks of ROW_LINES lines, or one line per block when that leaves the
@@ -36,7 +40,7 @@ hz_status row_fwd_t(const double2* in, const double* scale, long rows_per_rhs, l
     HZ_TRY(smem_attr(k, C::row_smem(1)));
     HZ_CUDA(launch_pdl(k, dim3(unsigned(nrows)), dim3(C::TPL_ROW), C::row_smem(1), st, in, scale,
                        rows_per_rhs, nrows, static_cast<const V*>(tw), static_cast<V*>(out),
-                       active));
+                       active, z, zc));
     HZ_CUDA(cudaGetLastError());
     return HZ_OK;
   }
@@ -46,24 +50,43 @@ hz_status row_fwd_t(const double2* in, const double* scale, long rows_per_rhs, l
   const long blocks = (nrows + lines - 1) / lines;
   HZ_CUDA(launch_pdl(k, dim3(unsigned(blocks)), dim3(lines * C::TPL_ROW), C::row_smem(lines), st,
                      in, scale, rows_per_rhs, nrows, static_cast<const V*>(tw),
-                     static_cast<V*>(out), active));
+                     static_cast<V*>(out), active, z, zc));
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
 
 hz_status row_fwd(int prec, const double2* in, const double* scale, long rows_per_rhs, long nrows,
-                  const void* tw, void* out, cudaStream_t st, const int* active) {
-  return prec == 0 ? row_fwd_t<double>(in, scale, rows_per_rhs, nrows, tw, out, st, active)
-                   : row_fwd_t<float>(in, scale, rows_per_rhs, nrows, tw, out, st, active);
+                  const void* tw, void* out, cudaStream_t st, const int* active, void* zero,
+                  long zero_row_bytes) {
+  return prec == 0 ? row_fwd_t<double>(in, scale, rows_per_rhs, nrows, tw, out, st, active, zero,
+                                       zero_row_bytes)
+                   : row_fwd_t<float>(in, scale, rows_per_rhs, nrows, tw, out, st, active, zero,
+                                      zero_row_bytes);
 }
 
 template <typename R, typename OutT>
 hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segtab, int nseg,
                         const unsigned long long* rowmask, int K, long rows_per_rhs, long nrows,
                         long n, double inv_n, const void* tw, void* out, cudaStream_t st,
-                        const int* active, int mode) {
+                        const int* active, int mode, const unsigned long long* items,
+                        long nitems) {
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
+  if (mode == 3) {
+    // one line per (row, node) item, added into the cleared output
+    if (!items || nitems <= 0) return nitems == 0 ? HZ_OK : HZ_ERR_INVALID_ARG;
+    const long rhs = nrows / rows_per_rhs;
+    if (rhs > 65535) return HZ_ERR_INVALID_ARG;
+    auto ks = row_inv_scatter_kernel<R, N, OutT, C::ROW_LINES>;
+    HZ_TRY(smem_attr(ks, C::row_smem()));
+    dim3 grid(unsigned((nitems + C::ROW_LINES - 1) / C::ROW_LINES), unsigned(rhs));
+    HZ_CUDA(launch_pdl(ks, dim3(grid), dim3(C::ROW_THREADS), C::row_smem(), st,
+                       static_cast<const V*>(planes), static_cast<const typename RecT<R>::T*>(rec),
+                       segtab, nseg, items, nitems, K, n, R(inv_n), static_cast<const V*>(tw),
+                       static_cast<OutT*>(out), active));
+    HZ_CUDA(cudaGetLastError());
+    return HZ_OK;
+  }
   // fewer blocks of ROW_LINES rows than SMs: few rows
   const bool small = (nrows + C::ROW_LINES - 1) / C::ROW_LINES < 152L;
   if (mode == 1 || (mode == 0 && small)) {
@@ -100,15 +123,16 @@ hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segta
 hz_status row_inv_acc(int prec, int out_kind, const void* planes, const void* rec,
                       const uchar2* segtab, int nseg, const unsigned long long* rowmask, int K,
                       long rows_per_rhs, long nrows, long n, double inv_n, const void* tw,
-                      void* out, cudaStream_t st, const int* active, int mode) {
+                      void* out, cudaStream_t st, const int* active, int mode,
+                      const unsigned long long* items, long nitems) {
   if (prec == 0)
     return row_inv_acc_t<double, double2>(planes, rec, segtab, nseg, rowmask, K, rows_per_rhs,
-                                          nrows, n, inv_n, tw, out, st, active, mode);
+                                          nrows, n, inv_n, tw, out, st, active, mode, items, nitems);
   if (out_kind == 0)
     return row_inv_acc_t<float, float2>(planes, rec, segtab, nseg, rowmask, K, rows_per_rhs,
-                                        nrows, n, inv_n, tw, out, st, active, mode);
+                                        nrows, n, inv_n, tw, out, st, active, mode, items, nitems);
   return row_inv_acc_t<float, double2>(planes, rec, segtab, nseg, rowmask, K, rows_per_rhs,
-                                       nrows, n, inv_n, tw, out, st, active, mode);
+                                       nrows, n, inv_n, tw, out, st, active, mode, items, nitems);
 }
 
 template <typename R, int SIGN>

@@ -110,13 +110,16 @@ template <> struct RecT<double> { using T = double; };
 
 // ---------------------------------------------------------------------------
 // Forward FFT along x.  in: c128 rows (row gr at gr * N); scale[rhs] (or
-// NULL) multiplies the input; out: working-precision rows.
+// NULL) multiplies the input; out: working-precision rows.  zero (or NULL):
+// rows of zchunks 16-byte chunks cleared for every row transformed (the
+// output of the scattering x-inverse pass of the same apply; it may alias in).
 // ---------------------------------------------------------------------------
 template <typename R, int N, int LPB>
 __global__ void __launch_bounds__(LPB * LineCfg<R, N>::TPL_ROW)
 row_fwd_kernel(const double2* __restrict__ in, const double* __restrict__ scale,
                long rows_per_rhs, long nrows, const typename cvec<R>::T* __restrict__ tw,
-               typename cvec<R>::T* __restrict__ out, const int* __restrict__ active) {
+               typename cvec<R>::T* __restrict__ out, const int* __restrict__ active,
+               uint4* zero, int zchunks) {
   pdl_wait();
   using V = typename cvec<R>::T;
   using F = LineFFT<R, N, -1, 1, LineCfg<R, N>::WS, typename LineCfg<R, N>::RP>;
@@ -143,6 +146,12 @@ row_fwd_kernel(const double2* __restrict__ in, const double* __restrict__ scale,
     V* dst = out + row * N;
 #pragma unroll
     for (int e = 0; e < E; ++e) dst[F::out_index(t, e)] = x[e];
+    // every thread of the line has read its input (the transform's first
+    // barrier is behind the loads), so an aliased row may be cleared now
+    if (zero) {
+      uint4* z = zero + row * zchunks;
+      for (int c = t; c < zchunks; c += TPL) z[c] = make_uint4(0u, 0u, 0u, 0u);
+    }
   }
 }
 
@@ -343,6 +352,75 @@ weighted_gather_kernel(const typename cvec<R>::T* __restrict__ planes,
     o.x = acc.x * inv_n;
     o.y = acc.y * inv_n;
     out[i] = o;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The same pass with one line per (row, node) item: items[i] = (row << 8) | k
+// lists every pair of rowmask in use (grid.x: item blocks, grid.y: rhs).  A
+// line inverse-transforms plane k along its row and adds w_k(x) / n times the
+// result into out (Eqn. 405), which the apply cleared beforehand.  Each point
+// receives at most two additions (its nodes k_lo and k_hi) onto an exact zero;
+// floating-point addition commutes, so the sum does not depend on which
+// arrives first.  Many independent short lines keep more warps resident than
+// the fused kernel, whose row loops hold the accumulator in registers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void add_out(float2* p, float x, float y) {
+  atomicAdd(p, make_float2(x, y));
+}
+__device__ __forceinline__ void add_out(double2* p, double x, double y) {
+  atomicAdd(&p->x, x);
+  atomicAdd(&p->y, y);
+}
+
+template <typename R, int N, typename OutT, int LPB>
+__global__ void __launch_bounds__(LPB * LineCfg<R, N>::TPL_ROW)
+row_inv_scatter_kernel(const typename cvec<R>::T* __restrict__ planes,
+                       const typename RecT<R>::T* __restrict__ rec,
+                       const uchar2* __restrict__ segtab, int nseg,
+                       const unsigned long long* __restrict__ items, long nitems, int K, long n,
+                       R inv_n, const typename cvec<R>::T* __restrict__ tw, OutT* out,
+                       const int* __restrict__ active) {
+  pdl_wait();
+  using V = typename cvec<R>::T;
+  using F = LineFFT<R, N, +1, 1, LineCfg<R, N>::WS, typename LineCfg<R, N>::RP>;
+  constexpr int TPL = F::TPL, E = F::E;
+  const long rhs = blockIdx.y;
+  if (active && !active[rhs]) return;  // the whole block
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sm = reinterpret_cast<V*>(smem_raw);
+  __shared__ uchar2 seg_s[HZ_MAX_SEG];
+  for (int i = threadIdx.x; i < nseg; i += blockDim.x) seg_s[i] = segtab[i];
+  const int li = threadIdx.x / TPL, t = threadIdx.x % TPL;
+  const long it = long(blockIdx.x) * LPB + li;
+  const bool valid = it < nitems;
+  const unsigned long long item = valid ? items[it] : 0ull;
+  const long row = long(item >> 8);
+  const int kc = int(item & 0xFFull);
+  const V* src = planes + (rhs * K + kc) * n + row * N;
+  V x[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) x[e] = valid ? src[F::stage0_index(t, e)] : cmk<V>(R(0), R(0));
+  __syncthreads();  // seg_s
+  F::run_regs(sm + li * padded_len(N), t, x, tw);
+  if (valid) {
+    const typename RecT<R>::T* rr = rec + row * N;
+    OutT* dst = out + rhs * n + row * N;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int p = F::out_index(t, e);
+      int seg;
+      R tf;
+      decode_rec(rr[p], seg, tf);
+      const uchar2 kk = seg_s[seg];
+      R w = R(0);
+      if (kk.x == kc) w += R(1) - tf;
+      if (kk.y == kc) w += tf;
+      if (w != R(0)) {
+        w *= inv_n;
+        add_out(dst + p, w * x[e].x, w * x[e].y);
+      }
+    }
   }
 }
 

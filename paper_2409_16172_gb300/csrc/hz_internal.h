@@ -140,6 +140,8 @@ struct hz_medium {
   uint32_t* rec32 = nullptr;        // per point segment:8 | t:24 (complex64 path)
   unsigned long long* rowmask = nullptr;   // per x-row: nodes with a non-zero weight
   unsigned long long* slabmask = nullptr;  // 3D: per z-slab OR of its rows
+  unsigned long long* rowitems = nullptr;  // (row << 8) | k for every set bit of rowmask, row-major
+  long nitems = 0;
   uchar2* segtab = nullptr;
   double2* symA64 = nullptr;        // w^2 + i w a_k
   double2* symG64 = nullptr;        // gamma_k^2
@@ -160,16 +162,20 @@ struct FftOps {
   int N;
   // forward FFT along x, c128 input (optionally scaled per rhs)
   // active (nullable): per-rhs flags; work of retired right-hand sides is skipped
+  // zero (nullable): rows of zero_row_bytes bytes (row gr at gr * zero_row_bytes)
+  // set to 0 for every row transformed, after its input has been read
   hz_status (*row_fwd)(int prec, const double2* in, const double* scale, long rows_per_rhs,
-                       long nrows, const void* tw, void* out, cudaStream_t st, const int* active);
+                       long nrows, const void* tw, void* out, cudaStream_t st, const int* active,
+                       void* zero, long zero_row_bytes);
   // inverse FFT along x of the K planes + weighted sum; out_kind 0: c64, 1: c128
   // mode 0: by size, 1: in-place inverse then gather (planes overwritten),
-  // 2: fused inverse + weighted sum
+  // 2: fused inverse + weighted sum, 3: one line per (row, node) item of
+  // items[0 .. nitems) adding its weighted line into out, which must be zero
   hz_status (*row_inv_acc)(int prec, int out_kind, const void* planes, const void* rec,
                            const uchar2* segtab, int nseg, const unsigned long long* rowmask,
                            int K, long rows_per_rhs, long nrows, long n, double inv_n,
                            const void* tw, void* out, cudaStream_t st, const int* active,
-                           int mode);
+                           int mode, const unsigned long long* items, long nitems);
   // FFT along a strided axis, in place; sign -1 forward, +1 inverse
   hz_status (*line_pass)(int prec, int sign, void* data, int nx, long outer, long S,
                          long ostride, long bstride, int batch,
@@ -219,7 +225,7 @@ struct Tune {
   int dots_vc = 8;
   int upd_bps = 4;
   int syminv_kpb = 1;
-  int rowinv_mode = 0;  // FftOps::row_inv_acc mode
+  int rowinv_mode = 0;  // FftOps::row_inv_acc mode (0..3)
   int col_pair = 1;     // complex64 symbol pass: two columns per thread (2: in
                         // half-size blocks)
 };

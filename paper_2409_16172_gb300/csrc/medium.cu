@@ -395,6 +395,15 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
     for (auto v : sm) su += __builtin_popcountll(v);
     m->rowk_used = ru;
     m->slabk_used = su;
+    // the (row, node) pairs in use, for the scattering x-inverse pass
+    std::vector<unsigned long long> items;
+    items.reserve(size_t(ru));
+    for (long r = 0; r < nrows; ++r)
+      for (unsigned long long b = rm[r]; b; b &= b - 1)
+        items.push_back((static_cast<unsigned long long>(r) << 8) |
+                        static_cast<unsigned long long>(__builtin_ctzll(b)));
+    m->nitems = long(items.size());
+    if ((st = upload(m->arena, &m->rowitems, items, cs)) != HZ_OK) return fail(st);
   }
 
   // symbol constants A_k = w^2 + i w a_k, G_k = gamma_k^2

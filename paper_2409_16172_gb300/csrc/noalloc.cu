@@ -86,7 +86,7 @@ extern "C" hz_status hz_apply_preconditioner_noalloc(const hz_medium* med, const
   const long rows = n / nx;
   const long slab = long(nx) * ny;
   HZ_TRY(ox->row_fwd(prec, static_cast<const double2*>(x), nullptr, rows, rows * nrhs, tw(tx), tmp, st,
-                     nullptr));
+                     nullptr, nullptr, 0));
   HZ_TRY(oy->line_pass(prec, -1, tmp, nx, nz, nx, slab, n, nrhs, nullptr, med->K, tw(ty), st, nullptr, 1));
   int launches = 2;
   if (med->dim == 2) {
@@ -105,7 +105,7 @@ extern "C" hz_status hz_apply_preconditioner_noalloc(const hz_medium* med, const
     launches += 3;
   }
   HZ_TRY(ox->row_inv_acc(prec, 1, planes, rec, med->segtab, med->nseg, med->rowmask, med->K, rows,
-                         rows * nrhs, n, 1.0 / double(n), tw(tx), y, st, nullptr, 0));
+                         rows * nrhs, n, 1.0 / double(n), tw(tx), y, st, nullptr, 0, nullptr, 0));
   count_launches(launches + 1);
   return HZ_OK;
 }

@@ -73,7 +73,7 @@ extern "C" hz_status hz_plan_set_tune(hz_plan* plan, const hz_tune_report* r) {
   const bool ok = (r->dots_vc == 2 || r->dots_vc == 4 || r->dots_vc == 8) && r->dots_bps >= 1 &&
                   r->dots_bps <= 4 && r->upd_bps >= 1 && r->upd_bps <= 8 &&
                   (r->syminv_kpb == 1 || r->syminv_kpb == 2 || r->syminv_kpb == 4) &&
-                  r->rowinv_mode >= 0 && r->rowinv_mode <= 2 && r->col_pair >= 0 && r->col_pair <= 2;
+                  r->rowinv_mode >= 0 && r->rowinv_mode <= 3 && r->col_pair >= 0 && r->col_pair <= 2;
   if (!ok) return set_error(HZ_ERR_INVALID_ARG, "launch shape out of range");
   plan->tune.dots_vc = r->dots_vc;
   plan->tune.dots_bps = r->dots_bps;
@@ -193,9 +193,9 @@ extern "C" hz_status hz_plan_autotune(hz_plan* plan, void* stream, hz_tune_repor
       }
     }
   }
-  // x-inverse pass: fused weighted sum vs in place + gather (grids with
-  // few rows always take the second)
-  for (int mode : {2, 1}) {
+  // x-inverse pass: fused weighted sum, in place + gather, or one line per
+  // (row, node) added into the cleared output
+  for (int mode : {2, 1, 3}) {
     p->tune = best;
     p->tune.rowinv_mode = mode;
     const float ms = tm.best_ms([&] {

@@ -209,9 +209,10 @@ def test_gmres_3d_matches_oracle(hz, shape):
 @pytest.mark.parametrize("shape", [(64, 32), (128, 128), (48, 192), (8, 2048), (12, 48, 8),
                                    (24, 16, 32)])
 def test_apply_every_launch_shape(hz, shape):
-    """Every symbol-pass node grouping, one or two columns per thread, and
-    both x-inverse forms (fused weighted sum; in place + gather) give the
-    oracle's apply, in both precisions and with two right-hand sides."""
+    """Every symbol-pass node grouping, one or two columns per thread (full or
+    half-size blocks), and every x-inverse form (fused weighted sum; in place
+    + gather; one line per (row, node) added into the cleared output) give
+    the oracle's apply, in both precisions and with two right-hand sides."""
     p = S.small_problem(shape, 14, M=6, Mt=3, width=2)
     med_g, med_o = media(hz, p)
     v = S.random_field(np.random.Generator(np.random.PCG64(15)), shape, 2)
@@ -219,7 +220,8 @@ def test_apply_every_launch_shape(hz, shape):
     for prec, tol in ((0, 1e-10), (1, 5e-5)):
         plan = hz.Plan(med_g, precision=prec, max_nrhs=2)
         for kpb, mode, pair in ((1, 1, 1), (1, 2, 0), (2, 2, 1), (4, 1, 0), (4, 2, 1), (2, 0, 1),
-                                (1, 0, 0), (1, 2, 2), (2, 1, 2), (4, 0, 2)):
+                                (1, 0, 0), (1, 2, 2), (2, 1, 2), (4, 0, 2), (1, 3, 1), (2, 3, 0),
+                                (4, 3, 2)):
             plan.set_tune(syminv_kpb=kpb, rowinv_mode=mode, col_pair=pair)
             got = plan.apply_preconditioner(_dev(v), precision=prec).cpu().numpy()
             assert rel(got, ref) <= tol, (prec, kpb, mode, pair, rel(got, ref))
@@ -229,7 +231,7 @@ def test_set_tune_rejects_out_of_range(hz):
     p = S.small_problem((16, 16), 3, M=4, Mt=2, width=2)
     med_g, _ = media(hz, p)
     plan = hz.Plan(med_g, precision=1)
-    for bad in (dict(syminv_kpb=3), dict(rowinv_mode=3), dict(dots_vc=5), dict(upd_bps=0),
+    for bad in (dict(syminv_kpb=3), dict(rowinv_mode=4), dict(dots_vc=5), dict(upd_bps=0),
                 dict(dots_bps=5), dict(upd_bps=9), dict(col_pair=3)):
         with pytest.raises(hz.HzError):
             plan.set_tune(**bad)

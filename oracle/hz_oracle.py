@@ -16,6 +16,9 @@ the order the paper states them, with no blocking or fusion:
   * operator            Q_M v = sum_m phi_m(c(x)) IFT(q(c_m,.) FT v) (Eqn. 103)
   * complex wave speed  gamma = c (1 - i zeta)                     (Eqn. Complex_wave_speed)
   * layer interpolation real hats x zeta hats                      (Eqn. 405 / 403)
+  * extensions the paper names as future work (Section 6): piecewise
+    quadratic Lagrange bases in c, and bivariate interpolation in (c, a)
+    with a independent of c (tensor products with hats in a)
   * discretisation      periodic 2nd-order central differences and
                         the FFT on the same grid                   (Section 5, Eqn. MainDiscrete)
   * solver              restarted GMRES, matrix-free               (Section 5, "GMRES implementation")
@@ -32,6 +35,12 @@ Readings of places where the paper is silent:
   * Layer nodes are c_o (1 - i zeta_m), zeta_m = m zeta_max / Mt, m = 1..Mt;
     zeta_0 = 0 is the real node c_o.  Im(gamma) <= 0 (the '1 + i zeta_max'
     printed in Section 4.4 is read as a typo for 1 - i zeta_max).
+  * Quadratic Lagrange basis (basis = 1): M odd, elements of two consecutive
+    intervals [c_2e, c_2e+2], each segment of the two-segment split holding
+    an even number of intervals; layer points keep the hats in zeta.
+  * Bivariate interpolation (Ma >= 2): Ma damping nodes equispaced on
+    [min a, max a]; node (s, j) carries gamma_s and damping a_j + alpha w;
+    weights are products of the speed weights and hats in a.
   * DFT: unnormalised forward with e^{-2 pi i jk/N}, 1/n on the inverse;
     this is the discrete form of the symmetric pair in Eqn. FT.
 
@@ -159,6 +168,9 @@ class Nodes:
     c_real    the M_eff real nodes, increasing
     zeta_nodes zeta_0 = 0 < zeta_1 < ... < zeta_Mt
     m_o       index of c_o among the real nodes (-1 when there is no layer)
+    a_nodes   damping nodes of the bivariate form (one entry otherwise);
+              node k = s * Ma + j has speed node s and damping node j
+    basis     0: piecewise-linear hats in c; 1: piecewise quadratic Lagrange
     """
     gamma: np.ndarray
     a: np.ndarray
@@ -166,10 +178,22 @@ class Nodes:
     zeta_nodes: np.ndarray
     m_o: int
     omega: float
+    a_nodes: np.ndarray = field(default_factory=lambda: np.zeros(1))
+    basis: int = 0
+    alpha: float = 0.05
 
     @property
     def K(self) -> int:
         return len(self.gamma)
+
+    @property
+    def Ma(self) -> int:
+        return len(self.a_nodes)
+
+    @property
+    def Ks(self) -> int:
+        """Number of speed nodes (real and layer)."""
+        return self.K // self.Ma
 
     @property
     def M(self) -> int:
@@ -180,7 +204,8 @@ class Nodes:
         return len(self.zeta_nodes) - 1
 
 
-def real_nodes(c_lo: float, c_hi: float, M: int, c_o: float | None) -> np.ndarray:
+def real_nodes(c_lo: float, c_hi: float, M: int, c_o: float | None,
+               basis: int = 0) -> np.ndarray:
     """Equispaced real nodes with c_1 = c_lo and c_M = c_hi (Lemma 3).
 
     If c_o is given it must be a node (Section 4.4): when it lies strictly
@@ -189,6 +214,10 @@ def real_nodes(c_lo: float, c_hi: float, M: int, c_o: float | None) -> np.ndarra
     1, M-2) intervals.  M = 1 gives the single node c_o (or c_lo), i.e. the
     Q_1 preconditioner of Eqn. OneInterpPoint.  A range narrower than
     1e-12 c_hi also collapses to one node.
+
+    basis = 1 (quadratic elements of two intervals) needs M odd, and the
+    split gives each segment an even number of intervals:
+    s1 = clamp(2 round((M-1)(c_o-c_lo)/(2(c_hi-c_lo))), 2, M-3).
     """
     if M < 1:
         raise ValueError("M must be >= 1")
@@ -196,11 +225,17 @@ def real_nodes(c_lo: float, c_hi: float, M: int, c_o: float | None) -> np.ndarra
         return np.array([c_o if c_o is not None else c_lo], dtype=np.float64)
     if c_hi - c_lo <= 1e-12 * c_hi:
         return np.array([c_lo], dtype=np.float64)
+    if basis == 1 and M % 2 == 0:
+        raise ValueError("the quadratic basis needs an odd number of real nodes")
     if c_o is not None and c_lo < c_o < c_hi:
-        if M < 3:
-            raise ValueError("c_o strictly inside the speed range needs M >= 3")
-        s1 = int(math.floor((M - 1) * (c_o - c_lo) / (c_hi - c_lo) + 0.5))
-        s1 = min(max(s1, 1), M - 2)
+        if M < (5 if basis == 1 else 3):
+            raise ValueError("c_o strictly inside the speed range needs more nodes")
+        if basis == 1:
+            s1 = 2 * int(math.floor((M - 1) * (c_o - c_lo) / (2.0 * (c_hi - c_lo)) + 0.5))
+            s1 = min(max(s1, 2), M - 3)
+        else:
+            s1 = int(math.floor((M - 1) * (c_o - c_lo) / (c_hi - c_lo) + 0.5))
+            s1 = min(max(s1, 1), M - 2)
         s2 = (M - 1) - s1
         left = [c_lo + (c_o - c_lo) * i / s1 for i in range(s1)]
         right = [c_o + (c_hi - c_o) * i / s2 for i in range(s2)]
@@ -209,15 +244,30 @@ def real_nodes(c_lo: float, c_hi: float, M: int, c_o: float | None) -> np.ndarra
                     dtype=np.float64)
 
 
+def damping_nodes(a_lo: float, a_hi: float, Ma: int) -> np.ndarray:
+    """Ma equispaced damping nodes on [a_lo, a_hi] (the second variable of
+    the bivariate form); a range narrower than 1e-12 max(|a_hi|, 1)
+    collapses to one node."""
+    if Ma < 1:
+        raise ValueError("Ma must be >= 1")
+    if Ma == 1 or a_hi - a_lo <= 1e-12 * max(abs(a_hi), 1.0):
+        return np.array([a_lo], dtype=np.float64)
+    return np.array([a_lo + (a_hi - a_lo) * j / (Ma - 1) for j in range(Ma - 1)] + [a_hi],
+                    dtype=np.float64)
+
+
 def build_nodes(c, zeta, omega: float, M: int, Mt: int, c_o: float,
                 zeta_max: float | None = None, alpha: float = 0.05,
-                a_node: float = 0.0) -> Nodes:
+                a_node: float = 0.0, a=None, Ma: int = 1, basis: int = 0) -> Nodes:
     """Node table of Section 4.1 / 4.4 for a given medium.
 
     Real nodes span [min c, max c] (c_o included when there is a layer);
     layer nodes are c_o (1 - i zeta_m), zeta_m = m zeta_max / Mt.
-    zeta_max defaults to max(zeta).  Every node symbol uses the damping
-    a_k = a_node + alpha * omega.
+    zeta_max defaults to max(zeta).  With Ma <= 1 every node symbol uses the
+    damping a_k = a_node + alpha * omega.  With Ma >= 2 the damping a(x) is
+    a second interpolation variable: node (s, j) (k = s Ma + j) uses speed
+    node s and the damping a_j + alpha * omega, a_j equispaced on
+    [min a, max a].
     """
     c = np.asarray(c, np.float64)
     zeta = np.asarray(zeta, np.float64)
@@ -225,7 +275,7 @@ def build_nodes(c, zeta, omega: float, M: int, Mt: int, c_o: float,
     c_lo, c_hi = float(c.min()), float(c.max())
     if has_layer:
         c_lo, c_hi = min(c_lo, c_o), max(c_hi, c_o)
-    cr = real_nodes(c_lo, c_hi, M, c_o if (has_layer or M == 1) else None)
+    cr = real_nodes(c_lo, c_hi, M, c_o if (has_layer or M == 1) else None, basis)
     m_o = -1
     if has_layer:
         hit = np.nonzero(cr == c_o)[0]
@@ -238,13 +288,21 @@ def build_nodes(c, zeta, omega: float, M: int, Mt: int, c_o: float,
         zn = np.array([0.0] + [m * zmax / Mt for m in range(1, Mt)] + [zmax])
     else:
         zn = np.array([0.0])
-    gam = [complex(x) for x in cr] + [c_o * (1.0 - 1j * z) for z in zn[1:]]
-    a = np.full(len(gam), a_node + alpha * omega, dtype=np.float64)
-    return Nodes(np.array(gam, np.complex128), a, cr, zn, m_o, float(omega))
+    gam_s = [complex(x) for x in cr] + [c_o * (1.0 - 1j * z) for z in zn[1:]]
+    if Ma >= 2:
+        av = np.zeros_like(c) if a is None else np.asarray(a, np.float64)
+        an = damping_nodes(float(av.min()), float(av.max()), Ma)
+    else:
+        an = np.array([a_node], dtype=np.float64)
+    gam = np.array([g for g in gam_s for _ in an], np.complex128)
+    ak = np.array([aj + alpha * omega for _ in gam_s for aj in an], np.float64)
+    return Nodes(gam, ak, cr, zn, m_o, float(omega), an, int(basis), float(alpha))
 
 
 def hat_weights(c, zeta, nodes: Nodes) -> np.ndarray:
-    """Dense weights W[k, x] of Eqn. 405 with piecewise-linear hats.
+    """Dense speed weights W[s, x] of Eqn. 405 (s over the Ks speed nodes):
+    piecewise-linear hats, or with nodes.basis == 1 quadratic Lagrange
+    polynomials on the real elements (layer points keep hats in zeta).
 
     Points with zeta = 0 get the real hats phi_m(c(x)) on the real nodes.
     Points with zeta > 0 (where c = c_o) get phi_0(Im gamma) on node m_o and
@@ -255,12 +313,25 @@ def hat_weights(c, zeta, nodes: Nodes) -> np.ndarray:
     c = np.asarray(c, np.float64)
     zeta = np.asarray(zeta, np.float64)
     cf, zf = c.ravel(), zeta.ravel()
-    W = np.zeros((nodes.K, cf.size), dtype=np.float64)
+    W = np.zeros((nodes.Ks, cf.size), dtype=np.float64)
     real = np.nonzero(zf == 0)[0]
     cr = nodes.c_real
     M = len(cr)
     if M == 1:
         W[0, real] = 1.0
+    elif len(real) and nodes.basis == 1:
+        # element e spans the nodes 2e, 2e+1, 2e+2; Lagrange polynomials of
+        # degree 2 through them
+        cv = cf[real]
+        i = np.clip(np.searchsorted(cr, cv, side="right") - 1, 0, M - 2)
+        e = np.minimum(i // 2, (M - 1) // 2 - 1)
+        if np.any(cv < cr[0] - 1e-12 * cr[-1]) or np.any(cv > cr[-1] * (1 + 1e-12)):
+            raise ValueError("wave speed outside the node range")
+        n0, n1, n2 = 2 * e, 2 * e + 1, 2 * e + 2
+        c0, c1, c2 = cr[n0], cr[n1], cr[n2]
+        np.add.at(W, (n0, real), (cv - c1) * (cv - c2) / ((c0 - c1) * (c0 - c2)))
+        np.add.at(W, (n1, real), (cv - c0) * (cv - c2) / ((c1 - c0) * (c1 - c2)))
+        np.add.at(W, (n2, real), (cv - c0) * (cv - c1) / ((c2 - c0) * (c2 - c1)))
     elif len(real):
         cv = cf[real]
         i = np.clip(np.searchsorted(cr, cv, side="right") - 1, 0, M - 2)
@@ -283,7 +354,38 @@ def hat_weights(c, zeta, nodes: Nodes) -> np.ndarray:
         node_of = np.array([nodes.m_o] + [M + m - 1 for m in range(1, Mt + 1)])
         np.add.at(W, (node_of[i], lay), 1.0 - t)
         np.add.at(W, (node_of[i + 1], lay), t)
-    return W.reshape((nodes.K,) + c.shape)
+    return W.reshape((nodes.Ks,) + c.shape)
+
+
+def damping_weights(a, nodes: Nodes) -> np.ndarray:
+    """Dense hats Wa[j, x] of a(x) on the damping nodes (all ones for a
+    single damping node)."""
+    av = np.asarray(a, np.float64).ravel()
+    an = nodes.a_nodes
+    Wa = np.zeros((len(an), av.size), dtype=np.float64)
+    if len(an) == 1:
+        Wa[0] = 1.0
+    else:
+        j = np.clip(np.searchsorted(an, av, side="right") - 1, 0, len(an) - 2)
+        t = (av - an[j]) / (an[j + 1] - an[j])
+        if np.any(t < -1e-12) or np.any(t > 1 + 1e-12):
+            raise ValueError("damping outside the node range")
+        idx = np.arange(av.size)
+        np.add.at(Wa, (j, idx), 1.0 - t)
+        np.add.at(Wa, (j + 1, idx), t)
+    return Wa.reshape((len(an),) + np.shape(a))
+
+
+def interp_weights(c, zeta, a, nodes: Nodes) -> np.ndarray:
+    """Weights W[k, x] of node k = s Ma + j: speed weight of node s times the
+    damping hat of node j (the tensor-product form of Eqn. 405 in (c, a))."""
+    Ws = hat_weights(c, zeta, nodes)
+    Wa = damping_weights(a, nodes)
+    W = np.zeros((nodes.K,) + np.shape(c), dtype=np.float64)
+    for s_ in range(nodes.Ks):
+        for j in range(nodes.Ma):
+            W[s_ * nodes.Ma + j] = Ws[s_] * Wa[j]
+    return W
 
 
 def node_symbol(gamma_k: complex, a_k: float, omega: float, xi2: np.ndarray) -> np.ndarray:
@@ -320,14 +422,15 @@ class Medium:
 
 def make_medium(c, zeta=None, a=None, omega: float = 1.0, M: int = 8, Mt: int = 0,
                 c_o: float = 1.0, zeta_max: float | None = None, alpha: float = 0.05,
-                a_node: float = 0.0, symbol_kind: int = 0, L: float = 1.0) -> Medium:
+                a_node: float = 0.0, symbol_kind: int = 0, L: float = 1.0, Ma: int = 1,
+                basis: int = 0) -> Medium:
     """Validate a medium and build its node table and weights."""
     c = np.asarray(c, np.float64)
     zeta = np.zeros_like(c) if zeta is None else np.asarray(zeta, np.float64)
     a = np.zeros_like(c) if a is None else np.asarray(a, np.float64)
     validate_medium(c, zeta, c_o)
-    nodes = build_nodes(c, zeta, omega, M, Mt, c_o, zeta_max, alpha, a_node)
-    W = hat_weights(c, zeta, nodes)
+    nodes = build_nodes(c, zeta, omega, M, Mt, c_o, zeta_max, alpha, a_node, a, Ma, basis)
+    W = interp_weights(c, zeta, a, nodes)
     return Medium(c, zeta, a, float(omega), float(L), nodes, W, symbol_kind,
                   xi2_grid(c.shape, L, symbol_kind))
 
@@ -371,12 +474,16 @@ def apply_pdo_direct(symbol_at_point, v: np.ndarray, L: float = 1.0,
 
 def exact_symbol_at_point(med: Medium):
     """q_{-2}(gamma(x), xi) with the point's own complex speed (Eqn. Precond,
-    the un-interpolated preconditioner Q)."""
+    the un-interpolated preconditioner Q); in the bivariate form also with
+    the point's own damping a(x) + alpha * omega."""
     g = complex_speed(med.c, med.zeta).ravel()
-    damp = med.nodes.a[0]
+    if med.nodes.Ma >= 2:
+        damp = med.a.ravel() + med.nodes.alpha * med.omega
+    else:
+        damp = np.full(g.size, med.nodes.a[0])
 
     def f(p, xi2):
-        return 1.0 / (med.omega ** 2 + 1j * med.omega * damp - g[p] ** 2 * xi2)
+        return 1.0 / (med.omega ** 2 + 1j * med.omega * damp[p] - g[p] ** 2 * xi2)
     return f
 
 

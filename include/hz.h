@@ -68,7 +68,23 @@ typedef struct {
  *   a_node     see alpha (the paper's a(c) assumption, Section 4, with one
  *              value for every node).
  *   symbol_kind 0: |xi|^2 = sum (2 pi k / L)^2 (Eqn. 021);
- *               1: the finite-difference symbol sum (4/h^2) sin^2(pi k / N). */
+ *               1: the finite-difference symbol sum (4/h^2) sin^2(pi k / N).
+ *   Ma         0 or 1: the damping of every node symbol is a_node + alpha w
+ *              (a follows c, Eqn. Intro02).  >= 2: bivariate interpolation in
+ *              (c, a), the extension Section 6 names for damping that does
+ *              not follow the wave speed: Ma damping nodes a_j equispaced on
+ *              [min a, max a] (one node when a is constant or NULL), node
+ *              k = s Ma + j with speed node s and damping a_j + alpha w, and
+ *              weights = speed weight x hat in a (up to 4 per point).
+ *              K = (M + Mt) Ma must stay <= 64.
+ *   basis      0: piecewise-linear hats in c (Eqn. 405); 1: piecewise
+ *              quadratic Lagrange polynomials on elements of two intervals
+ *              (the higher-order basis of Section 6; M odd, and with c_o
+ *              inside the range each of its two segments gets an even
+ *              number of intervals).  Layer points keep the hats in zeta.
+ *              basis 1 is univariate only (Ma <= 1).
+ * Fields added later (Ma, basis) read as 0 when a caller zero-fills the
+ * struct, which keeps the univariate piecewise-linear method.           */
 typedef struct {
   int M;
   int Mt;
@@ -77,6 +93,8 @@ typedef struct {
   double alpha;
   double a_node;
   int symbol_kind;
+  int Ma;
+  int basis;
 } hz_interp;
 
 /* Solver options.

@@ -201,7 +201,8 @@ hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* s
                   B * (m->rowk_used * 5.0 * nx * l2(nx) + 8.0 * dn));
     HZ_TRY(ox->row_inv_acc(prec, out_kind, p->planes, rec, m->segtab, m->nseg, m->rowmask, m->K,
                            rows, rows * nrhs, n, 1.0 / double(n), tw(tx), out, st, active,
-                           p->tune.rowinv_mode, m->rowitems, m->nitems));
+                           p->tune.rowinv_mode, m->rowitems, m->nitems, m->gnode,
+                           prec == 0 ? (const void*)m->gw64 : (const void*)m->gw32));
   }
   return HZ_OK;
 }

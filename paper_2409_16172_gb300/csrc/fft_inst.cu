@@ -69,21 +69,41 @@ hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segta
                         const unsigned long long* rowmask, int K, long rows_per_rhs, long nrows,
                         long n, double inv_n, const void* tw, void* out, cudaStream_t st,
                         const int* active, int mode, const unsigned long long* items,
-                        long nitems) {
+                        long nitems, const uchar4* gnode, const void* gw) {
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
+  using GW = typename GwT<R>::T;
+  if (gnode && mode != 3) {
+    // per-point (node, weight) records: lines in place, then the gather
+    auto ki = row_inv_inplace_kernel<R, N, C::ROW_LINES>;
+    HZ_TRY(smem_attr(ki, C::row_smem()));
+    dim3 grid(unsigned((nrows + C::ROW_LINES - 1) / C::ROW_LINES), unsigned(K));
+    HZ_CUDA(launch_pdl(ki, dim3(grid), dim3(C::ROW_THREADS), C::row_smem(), st,
+                       static_cast<V*>(const_cast<void*>(planes)), rowmask, K, rows_per_rhs, nrows,
+                       n, static_cast<const V*>(tw), active));
+    HZ_CUDA(cudaGetLastError());
+    const long total = nrows * N;
+    const long gblocks = std::min<long>((total + 255) / 256, 152L * 16);
+    HZ_CUDA(launch_pdl(weighted_gather4_kernel<R, OutT>, dim3(unsigned(gblocks)), dim3(256), 0, st,
+                       static_cast<const V*>(planes), gnode, static_cast<const GW*>(gw), K, n,
+                       total, R(inv_n), static_cast<OutT*>(out), active));
+    HZ_CUDA(cudaGetLastError());
+    count_launches(1);  // the phase counts one
+    return HZ_OK;
+  }
   if (mode == 3) {
     // one line per (row, node) item, added into the cleared output
     if (!items || nitems <= 0) return nitems == 0 ? HZ_OK : HZ_ERR_INVALID_ARG;
     const long rhs = nrows / rows_per_rhs;
     if (rhs > 65535) return HZ_ERR_INVALID_ARG;
-    auto ks = row_inv_scatter_kernel<R, N, OutT, C::ROW_LINES>;
+    auto ks = gnode ? row_inv_scatter_kernel<R, N, OutT, C::ROW_LINES, true>
+                    : row_inv_scatter_kernel<R, N, OutT, C::ROW_LINES, false>;
     HZ_TRY(smem_attr(ks, C::row_smem()));
     dim3 grid(unsigned((nitems + C::ROW_LINES - 1) / C::ROW_LINES), unsigned(rhs));
     HZ_CUDA(launch_pdl(ks, dim3(grid), dim3(C::ROW_THREADS), C::row_smem(), st,
                        static_cast<const V*>(planes), static_cast<const typename RecT<R>::T*>(rec),
                        segtab, nseg, items, nitems, K, n, R(inv_n), static_cast<const V*>(tw),
-                       static_cast<OutT*>(out), active));
+                       static_cast<OutT*>(out), active, gnode, static_cast<const GW*>(gw)));
     HZ_CUDA(cudaGetLastError());
     return HZ_OK;
   }
@@ -124,15 +144,16 @@ hz_status row_inv_acc(int prec, int out_kind, const void* planes, const void* re
                       const uchar2* segtab, int nseg, const unsigned long long* rowmask, int K,
                       long rows_per_rhs, long nrows, long n, double inv_n, const void* tw,
                       void* out, cudaStream_t st, const int* active, int mode,
-                      const unsigned long long* items, long nitems) {
+                      const unsigned long long* items, long nitems, const uchar4* gnode,
+                      const void* gw) {
   if (prec == 0)
     return row_inv_acc_t<double, double2>(planes, rec, segtab, nseg, rowmask, K, rows_per_rhs,
-                                          nrows, n, inv_n, tw, out, st, active, mode, items, nitems);
+                                          nrows, n, inv_n, tw, out, st, active, mode, items, nitems, gnode, gw);
   if (out_kind == 0)
     return row_inv_acc_t<float, float2>(planes, rec, segtab, nseg, rowmask, K, rows_per_rhs,
-                                        nrows, n, inv_n, tw, out, st, active, mode, items, nitems);
+                                        nrows, n, inv_n, tw, out, st, active, mode, items, nitems, gnode, gw);
   return row_inv_acc_t<float, double2>(planes, rec, segtab, nseg, rowmask, K, rows_per_rhs,
-                                       nrows, n, inv_n, tw, out, st, active, mode, items, nitems);
+                                       nrows, n, inv_n, tw, out, st, active, mode, items, nitems, gnode, gw);
 }
 
 template <typename R, int SIGN>

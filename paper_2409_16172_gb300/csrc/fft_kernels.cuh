@@ -108,6 +108,21 @@ template <typename R> struct RecT;
 template <> struct RecT<float> { using T = uint32_t; };
 template <> struct RecT<double> { using T = double; };
 
+// Per-point (node, weight) records of the bivariate and quadratic forms:
+// gnode[p] holds up to four node indices (0xFF: unused slot) and gw their
+// weights, one float4 (complex64 path) or two double2 (complex128) per point.
+template <typename R> struct GwT;
+template <> struct GwT<float> { using T = float4; };
+template <> struct GwT<double> { using T = double2; };
+__device__ __forceinline__ void load_gw(const float4* gw, long p, float (&w)[4]) {
+  const float4 v = gw[p];
+  w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+}
+__device__ __forceinline__ void load_gw(const double2* gw, long p, double (&w)[4]) {
+  const double2 u = gw[2 * p], v = gw[2 * p + 1];
+  w[0] = u.x; w[1] = u.y; w[2] = v.x; w[3] = v.y;
+}
+
 // ---------------------------------------------------------------------------
 // Forward FFT along x.  in: c128 rows (row gr at gr * N); scale[rhs] (or
 // NULL) multiplies the input; out: working-precision rows.  zero (or NULL):
@@ -355,6 +370,41 @@ weighted_gather_kernel(const typename cvec<R>::T* __restrict__ planes,
   }
 }
 
+// The gather for per-point (node, weight) records: z = (1/n) sum over the
+// point's used slots of w_slot plane_node (slots in increasing node order).
+template <typename R, typename OutT>
+__global__ void __launch_bounds__(256)
+weighted_gather4_kernel(const typename cvec<R>::T* __restrict__ planes,
+                        const uchar4* __restrict__ gnode, const typename GwT<R>::T* __restrict__ gw,
+                        int K, long n, long total, R inv_n, OutT* __restrict__ out,
+                        const int* __restrict__ active) {
+  pdl_wait();
+  using V = typename cvec<R>::T;
+  for (long i = long(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+       i += long(gridDim.x) * blockDim.x) {
+    const long rhs = i / n, e = i - rhs * n;
+    if (active && !active[rhs]) continue;
+    const uchar4 nd = gnode[e];
+    R w[4];
+    load_gw(gw, e, w);
+    const unsigned char ks[4] = {nd.x, nd.y, nd.z, nd.w};
+    const V* pl = planes + rhs * K * n + e;
+    R ax = R(0), ay = R(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (ks[j] != 0xFF) {
+        const V a = pl[long(ks[j]) * n];
+        ax = fma(w[j], a.x, ax);
+        ay = fma(w[j], a.y, ay);
+      }
+    }
+    OutT o;
+    o.x = ax * inv_n;
+    o.y = ay * inv_n;
+    out[i] = o;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // The same pass with one line per (row, node) item: items[i] = (row << 8) | k
 // lists every pair of rowmask in use (grid.x: item blocks, grid.y: rhs).  A
@@ -373,14 +423,19 @@ __device__ __forceinline__ void add_out(double2* p, double x, double y) {
   atomicAdd(&p->y, y);
 }
 
-template <typename R, int N, typename OutT, int LPB>
+// GEN: the weights come from the per-point (node, weight) records gnode / gw.
+// A point then receives up to four additions; with three or more the
+// rounding of the sum depends on their arrival order, so results can differ
+// between runs by rounding (the gather form does not).
+template <typename R, int N, typename OutT, int LPB, bool GEN>
 __global__ void __launch_bounds__(LPB * LineCfg<R, N>::TPL_ROW)
 row_inv_scatter_kernel(const typename cvec<R>::T* __restrict__ planes,
                        const typename RecT<R>::T* __restrict__ rec,
                        const uchar2* __restrict__ segtab, int nseg,
                        const unsigned long long* __restrict__ items, long nitems, int K, long n,
                        R inv_n, const typename cvec<R>::T* __restrict__ tw, OutT* out,
-                       const int* __restrict__ active) {
+                       const int* __restrict__ active, const uchar4* __restrict__ gnode,
+                       const typename GwT<R>::T* __restrict__ gw) {
   pdl_wait();
   using V = typename cvec<R>::T;
   using F = LineFFT<R, N, +1, 1, LineCfg<R, N>::WS, typename LineCfg<R, N>::RP>;
@@ -409,13 +464,23 @@ row_inv_scatter_kernel(const typename cvec<R>::T* __restrict__ planes,
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int p = F::out_index(t, e);
-      int seg;
-      R tf;
-      decode_rec(rr[p], seg, tf);
-      const uchar2 kk = seg_s[seg];
       R w = R(0);
-      if (kk.x == kc) w += R(1) - tf;
-      if (kk.y == kc) w += tf;
+      if constexpr (GEN) {
+        const uchar4 nd = gnode[row * N + p];
+        R ws[4];
+        load_gw(gw, row * N + p, ws);
+        if (nd.x == kc) w += ws[0];
+        if (nd.y == kc) w += ws[1];
+        if (nd.z == kc) w += ws[2];
+        if (nd.w == kc) w += ws[3];
+      } else {
+        int seg;
+        R tf;
+        decode_rec(rr[p], seg, tf);
+        const uchar2 kk = seg_s[seg];
+        if (kk.x == kc) w += R(1) - tf;
+        if (kk.y == kc) w += tf;
+      }
       if (w != R(0)) {
         w *= inv_n;
         add_out(dst + p, w * x[e].x, w * x[e].y);

@@ -132,6 +132,12 @@ struct hz_medium {
   std::vector<double> gamma_re, gamma_im, a_k, c_real, zeta_nodes;
   int nseg = 0;
   std::vector<uchar2> segtab_h;
+  // bivariate (c, a) interpolation and the quadratic basis: Ma damping nodes
+  // (node k = s * Ma + j), and per-point (node, weight) records instead of
+  // the (segment, t) record
+  int Ma = 1, basis = 0;
+  bool generic = false;
+  std::vector<double> a_nodes;
   // device data
   hz::DevArena arena;
   double2* gamma2 = nullptr;        // per point gamma^2 / h_x^2 (Eqn. Complex_wave_speed squared)
@@ -140,6 +146,9 @@ struct hz_medium {
   uint32_t* rec32 = nullptr;        // per point segment:8 | t:24 (complex64 path)
   unsigned long long* rowmask = nullptr;   // per x-row: nodes with a non-zero weight
   unsigned long long* slabmask = nullptr;  // 3D: per z-slab OR of its rows
+  uchar4* gnode = nullptr;          // generic: up to 4 nodes per point (0xFF: unused)
+  float4* gw32 = nullptr;           // generic: their weights (complex64 path)
+  double2* gw64 = nullptr;          // generic: their weights, two double2 per point
   unsigned long long* rowitems = nullptr;  // (row << 8) | k for every set bit of rowmask, row-major
   long nitems = 0;
   uchar2* segtab = nullptr;
@@ -170,12 +179,16 @@ struct FftOps {
   // inverse FFT along x of the K planes + weighted sum; out_kind 0: c64, 1: c128
   // mode 0: by size, 1: in-place inverse then gather (planes overwritten),
   // 2: fused inverse + weighted sum, 3: one line per (row, node) item of
-  // items[0 .. nitems) adding its weighted line into out, which must be zero
+  // items[0 .. nitems) adding its weighted line into out, which must be zero.
+  // gnode (nullable): per-point (node, weight) records gnode / gw (float4 or
+  // two double2 per point) replace rec / segtab; mode 3 then scatters and
+  // every other mode transforms in place and gathers
   hz_status (*row_inv_acc)(int prec, int out_kind, const void* planes, const void* rec,
                            const uchar2* segtab, int nseg, const unsigned long long* rowmask,
                            int K, long rows_per_rhs, long nrows, long n, double inv_n,
                            const void* tw, void* out, cudaStream_t st, const int* active,
-                           int mode, const unsigned long long* items, long nitems);
+                           int mode, const unsigned long long* items, long nitems,
+                           const uchar4* gnode, const void* gw);
   // FFT along a strided axis, in place; sign -1 forward, +1 inverse
   hz_status (*line_pass)(int prec, int sign, void* data, int nx, long outer, long S,
                          long ostride, long bstride, int batch,

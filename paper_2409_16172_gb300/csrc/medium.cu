@@ -17,7 +17,7 @@ namespace {
 constexpr int VAL_THREADS = 256;
 
 struct ValPartial {
-  double cmin, cmax, zmax;
+  double cmin, cmax, zmax, amin, amax;
   unsigned long long bad_c, bad_zeta, bad_layer, bad_a;
 };
 
@@ -27,7 +27,7 @@ struct ValPartial {
 __global__ void validate_kernel(const double* __restrict__ c, const double* __restrict__ zeta,
                                 const double* __restrict__ a, long n, double c_o,
                                 ValPartial* __restrict__ part) {
-  double cmin = INFINITY, cmax = -INFINITY, zmax = 0.0;
+  double cmin = INFINITY, cmax = -INFINITY, zmax = 0.0, amin = INFINITY, amax = -INFINITY;
   unsigned long long bc = 0, bz = 0, bl = 0, ba = 0;
   for (long i = blockIdx.x * long(blockDim.x) + threadIdx.x; i < n; i += long(gridDim.x) * blockDim.x) {
     const double ci = c[i];
@@ -41,10 +41,17 @@ __global__ void validate_kernel(const double* __restrict__ c, const double* __re
     if (!(zi >= 0.0) || !isfinite(zi)) ++bz;
     else zmax = fmax(zmax, zi);
     if (zi > 0.0 && fabs(ci - c_o) > 1e-12 * c_o) ++bl;
-    if (a && !isfinite(a[i])) ++ba;
+    if (a) {
+      if (!isfinite(a[i])) {
+        ++ba;
+      } else {
+        amin = fmin(amin, a[i]);
+        amax = fmax(amax, a[i]);
+      }
+    }
   }
   __shared__ ValPartial sh[VAL_THREADS];
-  sh[threadIdx.x] = ValPartial{cmin, cmax, zmax, bc, bz, bl, ba};
+  sh[threadIdx.x] = ValPartial{cmin, cmax, zmax, amin, amax, bc, bz, bl, ba};
   __syncthreads();
   for (int s = VAL_THREADS / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
@@ -53,6 +60,8 @@ __global__ void validate_kernel(const double* __restrict__ c, const double* __re
       p.cmin = fmin(p.cmin, q.cmin);
       p.cmax = fmax(p.cmax, q.cmax);
       p.zmax = fmax(p.zmax, q.zmax);
+      p.amin = fmin(p.amin, q.amin);
+      p.amax = fmax(p.amax, q.amax);
       p.bad_c += q.bad_c;
       p.bad_zeta += q.bad_zeta;
       p.bad_layer += q.bad_layer;
@@ -66,7 +75,8 @@ __global__ void validate_kernel(const double* __restrict__ c, const double* __re
 struct NodeDev {
   double c_real[HZ_MAX_K];
   double zeta_nodes[HZ_MAX_K + 1];
-  int M, Mt;
+  double a_nodes[HZ_MAX_K];
+  int M, Mt, Ma, basis;
   uchar2 seg[HZ_MAX_SEG];
 };
 
@@ -112,6 +122,104 @@ __global__ void record_kernel(const double* __restrict__ c, const double* __rest
     row = i / nx;
   }
   // OR the bits of the warp's points that share a row, then one atomic each
+  const unsigned full = __activemask();
+  const long row0 = __shfl_sync(full, row, 0);
+  const bool same = __all_sync(full, row == row0);
+  if (same && row0 >= 0) {
+    const unsigned lo = __reduce_or_sync(full, unsigned(bits & 0xFFFFFFFFull));
+    const unsigned hi = __reduce_or_sync(full, unsigned(bits >> 32));
+    if ((threadIdx.x & 31) == 0) atomicOr(&rowmask[row0], (unsigned long long)lo | ((unsigned long long)hi << 32));
+  } else if (row >= 0 && bits) {
+    atomicOr(&rowmask[row], bits);
+  }
+}
+
+// Per point, for the bivariate and quadratic forms: the non-zero weights of
+// node k = s * Ma + j as (node, weight) pairs, speed weight of node s times
+// the hat of a(x) on damping node j.  Speed weights: hats in zeta on the
+// layer segment where zeta > 0 (Eqn. 405), else hats in c (basis 0) or the
+// degree-2 Lagrange polynomials of the element [c_2e, c_2e+2] containing c
+// (basis 1).  Also gamma^2 and the row mask bits of the nodes used.
+__global__ void gen_record_kernel(const double* __restrict__ c, const double* __restrict__ zeta,
+                                  const double* __restrict__ a, long n, int nx, NodeDev nd,
+                                  uchar4* __restrict__ gnode, float4* __restrict__ gw32,
+                                  double2* __restrict__ gw64, double2* __restrict__ gamma2,
+                                  double ih2x, unsigned long long* __restrict__ rowmask) {
+  const long i = blockIdx.x * long(blockDim.x) + threadIdx.x;
+  unsigned long long bits = 0ull;
+  long row = -1;
+  if (i < n) {
+    const double ci = c[i];
+    const double zi = zeta ? zeta[i] : 0.0;
+    const double ai = a ? a[i] : 0.0;
+    int sk[3] = {0, 0, 0};
+    double sw[3] = {0.0, 0.0, 0.0};
+    int ns = 0;
+    if (zi > 0.0) {
+      int m = 0;
+      while (m + 1 < nd.Mt && zi >= nd.zeta_nodes[m + 1]) ++m;
+      double t = (zi - nd.zeta_nodes[m]) / (nd.zeta_nodes[m + 1] - nd.zeta_nodes[m]);
+      t = fmin(fmax(t, 0.0), 1.0);
+      const uchar2 kk = nd.seg[nd.M + m];
+      sk[0] = kk.x; sw[0] = 1.0 - t;
+      sk[1] = kk.y; sw[1] = t;
+      ns = 2;
+    } else if (nd.M == 1) {
+      sk[0] = 0; sw[0] = 1.0;
+      ns = 1;
+    } else {
+      int m = 0;
+      while (m + 2 < nd.M && ci >= nd.c_real[m + 1]) ++m;
+      if (nd.basis == 1) {
+        const int e = min(m / 2, (nd.M - 1) / 2 - 1);
+        const double c0 = nd.c_real[2 * e], c1 = nd.c_real[2 * e + 1], c2 = nd.c_real[2 * e + 2];
+        sk[0] = 2 * e;     sw[0] = (ci - c1) * (ci - c2) / ((c0 - c1) * (c0 - c2));
+        sk[1] = 2 * e + 1; sw[1] = (ci - c0) * (ci - c2) / ((c1 - c0) * (c1 - c2));
+        sk[2] = 2 * e + 2; sw[2] = (ci - c0) * (ci - c1) / ((c2 - c0) * (c2 - c1));
+        ns = 3;
+      } else {
+        double t = (ci - nd.c_real[m]) / (nd.c_real[m + 1] - nd.c_real[m]);
+        t = fmin(fmax(t, 0.0), 1.0);
+        sk[0] = m;     sw[0] = 1.0 - t;
+        sk[1] = m + 1; sw[1] = t;
+        ns = 2;
+      }
+    }
+    int dk[2] = {0, 0};
+    double dw[2] = {1.0, 0.0};
+    int na = 1;
+    if (nd.Ma > 1) {
+      int j = 0;
+      while (j + 2 < nd.Ma && ai >= nd.a_nodes[j + 1]) ++j;
+      double t = (ai - nd.a_nodes[j]) / (nd.a_nodes[j + 1] - nd.a_nodes[j]);
+      t = fmin(fmax(t, 0.0), 1.0);
+      dk[0] = j;     dw[0] = 1.0 - t;
+      dk[1] = j + 1; dw[1] = t;
+      na = 2;
+    }
+    unsigned char kn[4] = {0xFF, 0xFF, 0xFF, 0xFF};
+    double wv[4] = {0.0, 0.0, 0.0, 0.0};
+    int used = 0;
+    for (int s = 0; s < ns; ++s) {
+      for (int d = 0; d < na; ++d) {
+        const double w = sw[s] * dw[d];
+        if (w != 0.0 && used < 4) {
+          const int k = sk[s] * nd.Ma + dk[d];
+          kn[used] = (unsigned char)k;
+          wv[used] = w;
+          bits |= 1ull << k;
+          ++used;
+        }
+      }
+    }
+    gnode[i] = make_uchar4(kn[0], kn[1], kn[2], kn[3]);
+    gw32[i] = make_float4(float(wv[0]), float(wv[1]), float(wv[2]), float(wv[3]));
+    gw64[2 * i] = make_double2(wv[0], wv[1]);
+    gw64[2 * i + 1] = make_double2(wv[2], wv[3]);
+    const double c2 = ci * ci;
+    gamma2[i] = make_double2(c2 * (1.0 - zi * zi) * ih2x, -2.0 * c2 * zi * ih2x);
+    row = i / nx;
+  }
   const unsigned full = __activemask();
   const long row0 = __shfl_sync(full, row, 0);
   const bool same = __all_sync(full, row == row0);
@@ -181,7 +289,10 @@ hz_status upload(DevArena& ar, T** d, const std::vector<T>& h, cudaStream_t cs) 
 // the background speed c_o is a node (Section 4.4): a c_o strictly inside
 // the range splits it into two equispaced segments of s1 and M-1-s1
 // intervals, s1 = clamp(round((M-1)(c_o-c_lo)/(c_hi-c_lo)), 1, M-2).
-hz_status real_nodes(double c_lo, double c_hi, int M, bool force_co, double c_o,
+// basis 1 (quadratic elements of two intervals): M odd, and the split gives
+// each segment an even number of intervals,
+// s1 = clamp(2 round((M-1)(c_o-c_lo)/(2(c_hi-c_lo))), 2, M-3).
+hz_status real_nodes(double c_lo, double c_hi, int M, bool force_co, double c_o, int basis,
                      std::vector<double>& out) {
   out.clear();
   if (M == 1) {
@@ -192,10 +303,19 @@ hz_status real_nodes(double c_lo, double c_hi, int M, bool force_co, double c_o,
     out.push_back(c_lo);
     return HZ_OK;
   }
+  if (basis == 1 && M % 2 == 0)
+    return set_error(HZ_ERR_INVALID_ARG, "the quadratic basis needs an odd number of real nodes");
   if (force_co && c_lo < c_o && c_o < c_hi) {
-    if (M < 3) return set_error(HZ_ERR_MEDIUM, "c_o inside (c_min, c_max) needs M >= 3");
-    int s1 = int(std::floor((M - 1) * (c_o - c_lo) / (c_hi - c_lo) + 0.5));
-    s1 = std::min(std::max(s1, 1), M - 2);
+    if (M < (basis == 1 ? 5 : 3))
+      return set_error(HZ_ERR_MEDIUM, "c_o inside (c_min, c_max) needs more real nodes");
+    int s1;
+    if (basis == 1) {
+      s1 = 2 * int(std::floor((M - 1) * (c_o - c_lo) / (2.0 * (c_hi - c_lo)) + 0.5));
+      s1 = std::min(std::max(s1, 2), M - 3);
+    } else {
+      s1 = int(std::floor((M - 1) * (c_o - c_lo) / (c_hi - c_lo) + 0.5));
+      s1 = std::min(std::max(s1, 1), M - 2);
+    }
     const int s2 = (M - 1) - s1;
     for (int i = 0; i < s1; ++i) out.push_back(c_lo + (c_o - c_lo) * i / s1);
     for (int i = 0; i < s2; ++i) out.push_back(c_o + (c_hi - c_o) * i / s2);
@@ -247,6 +367,12 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
   if (!(interp->c_o > 0) || interp->alpha < 0 || interp->a_node < 0 ||
       (interp->symbol_kind != 0 && interp->symbol_kind != 1))
     return set_error(HZ_ERR_INVALID_ARG, "bad interpolation options");
+  if (interp->Ma < 0 || (interp->basis != 0 && interp->basis != 1) ||
+      (interp->basis == 1 && interp->Ma > 1) ||
+      (interp->M + interp->Mt) * std::max(interp->Ma, 1) > HZ_MAX_K)
+    return set_error(HZ_ERR_INVALID_ARG,
+                     "need Ma >= 0, basis 0 or 1 (1 only with Ma <= 1), (M + Mt) Ma <= %d",
+                     HZ_MAX_K);
 
   hz_medium* m = new hz_medium();
   m->dim = grid->dim;
@@ -293,12 +419,14 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
   ce = cudaMemcpyAsync(hp.data(), dpart, vblocks * sizeof(ValPartial), cudaMemcpyDeviceToHost, cs);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(cs);
   if (ce != cudaSuccess) return fail(cuda_error(ce, "validate"));
-  double cmin = INFINITY, cmax = -INFINITY, zmax = 0;
+  double cmin = INFINITY, cmax = -INFINITY, zmax = 0, amin = INFINITY, amax = -INFINITY;
   unsigned long long bc = 0, bz = 0, bl = 0, ba = 0;
   for (const auto& p : hp) {
     cmin = std::min(cmin, p.cmin);
     cmax = std::max(cmax, p.cmax);
     zmax = std::max(zmax, p.zmax);
+    amin = std::min(amin, p.amin);
+    amax = std::max(amax, p.amax);
     bc += p.bad_c; bz += p.bad_zeta; bl += p.bad_layer; ba += p.bad_a;
   }
   if (bc) return fail(set_error(HZ_ERR_MEDIUM, "%llu points with c <= 0 or not finite", bc));
@@ -317,7 +445,8 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
     c_lo = std::min(c_lo, interp->c_o);
     c_hi = std::max(c_hi, interp->c_o);
   }
-  if ((st = real_nodes(c_lo, c_hi, interp->M, layer || interp->M == 1, interp->c_o, m->c_real)) != HZ_OK)
+  if ((st = real_nodes(c_lo, c_hi, interp->M, layer || interp->M == 1, interp->c_o, interp->basis,
+                       m->c_real)) != HZ_OK)
     return fail(st);
   m->M = int(m->c_real.size());
   m->m_o = -1;
@@ -333,18 +462,37 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
     m->zeta_max = zm;
   }
   m->Mt = int(m->zeta_nodes.size()) - 1;
-  m->K = m->M + m->Mt;
+  const int Ks = m->M + m->Mt;  // speed nodes
+  // damping nodes: bivariate form only (Ma >= 2), equispaced on [min a, max a]
+  m->a_nodes.clear();
+  if (interp->Ma >= 2) {
+    const double lo = a ? amin : 0.0, hi = a ? amax : 0.0;
+    if (hi - lo <= 1e-12 * std::max(std::fabs(hi), 1.0)) {
+      m->a_nodes.push_back(lo);
+    } else {
+      for (int j = 0; j < interp->Ma - 1; ++j) m->a_nodes.push_back(lo + (hi - lo) * j / (interp->Ma - 1));
+      m->a_nodes.push_back(hi);
+    }
+  } else {
+    m->a_nodes.push_back(interp->a_node);
+  }
+  m->Ma = int(m->a_nodes.size());
+  m->basis = interp->basis;
+  m->generic = m->Ma > 1 || (m->basis == 1 && m->M > 1);
+  m->K = Ks * m->Ma;
   m->gamma_re.clear();
   m->gamma_im.clear();
-  for (double cr : m->c_real) {
-    m->gamma_re.push_back(cr);
-    m->gamma_im.push_back(0.0);
+  m->a_k.clear();
+  for (int s = 0; s < Ks; ++s) {
+    // gamma = c_s for real nodes, c_o (1 - i zeta_m) for layer nodes
+    const double gr = s < m->M ? m->c_real[s] : interp->c_o;
+    const double gi = s < m->M ? 0.0 : -interp->c_o * m->zeta_nodes[s - m->M + 1];
+    for (int j = 0; j < m->Ma; ++j) {
+      m->gamma_re.push_back(gr);
+      m->gamma_im.push_back(gi);
+      m->a_k.push_back(m->a_nodes[j] + interp->alpha * omega);
+    }
   }
-  for (int i = 1; i <= m->Mt; ++i) {  // gamma = c_o (1 - i zeta_m)
-    m->gamma_re.push_back(interp->c_o);
-    m->gamma_im.push_back(-interp->c_o * m->zeta_nodes[i]);
-  }
-  m->a_k.assign(m->K, interp->a_node + interp->alpha * omega);
 
   // segment table: real segments, end entry, layer segments, end entry
   m->segtab_h.clear();
@@ -355,7 +503,7 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
     node_of[0] = m->m_o;
     for (int i = 1; i <= m->Mt; ++i) node_of[i] = m->M + i - 1;
     for (int i = 0; i < m->Mt; ++i) m->segtab_h.push_back(make_uchar2(node_of[i], node_of[i + 1]));
-    m->segtab_h.push_back(make_uchar2(m->K - 1, m->K - 1));
+    m->segtab_h.push_back(make_uchar2(Ks - 1, Ks - 1));
   }
   m->nseg = int(m->segtab_h.size());
 
@@ -363,6 +511,9 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
   memset(&nd, 0, sizeof(nd));
   nd.M = m->M;
   nd.Mt = m->Mt;
+  nd.Ma = m->Ma;
+  nd.basis = m->basis;
+  for (int j = 0; j < m->Ma; ++j) nd.a_nodes[j] = m->a_nodes[j];
   for (int i = 0; i < m->M; ++i) nd.c_real[i] = m->c_real[i];
   for (int i = 0; i <= m->Mt; ++i) nd.zeta_nodes[i] = m->zeta_nodes[i];
   for (int i = 0; i < m->nseg; ++i) nd.seg[i] = m->segtab_h[i];
@@ -373,12 +524,21 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
   if (st == HZ_OK) st = m->arena.alloc(&m->gamma2, n);
   if (st == HZ_OK) st = m->arena.alloc(&m->rowmask, nrows);
   if (st == HZ_OK) st = m->arena.alloc(&m->slabmask, m->nz);
+  if (st == HZ_OK && m->generic) st = m->arena.alloc(&m->gnode, n);
+  if (st == HZ_OK && m->generic) st = m->arena.alloc(&m->gw32, n);
+  if (st == HZ_OK && m->generic) st = m->arena.alloc(&m->gw64, 2 * n);
   if (st != HZ_OK) return fail(st);
   ce = cudaMemsetAsync(m->rowmask, 0, nrows * sizeof(unsigned long long), cs);
   if (ce != cudaSuccess) return fail(cuda_error(ce, "memset"));
   const double hx = m->L / m->nx;
-  record_kernel<<<unsigned((n + 255) / 256), 256, 0, cs>>>(dc, dz, n, m->nx, nd, m->rec64, m->rec32,
-                                                          m->gamma2, 1.0 / (hx * hx), m->rowmask);
+  if (m->generic) {
+    gen_record_kernel<<<unsigned((n + 255) / 256), 256, 0, cs>>>(dc, dz, m->a, n, m->nx, nd, m->gnode,
+                                                                m->gw32, m->gw64, m->gamma2,
+                                                                1.0 / (hx * hx), m->rowmask);
+  } else {
+    record_kernel<<<unsigned((n + 255) / 256), 256, 0, cs>>>(dc, dz, n, m->nx, nd, m->rec64, m->rec32,
+                                                            m->gamma2, 1.0 / (hx * hx), m->rowmask);
+  }
   slab_kernel<<<(m->nz + 127) / 128, 128, 0, cs>>>(m->rowmask, m->ny, m->nz, m->slabmask);
   count_launches(2);
   ce = cudaGetLastError();

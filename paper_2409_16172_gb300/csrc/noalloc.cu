@@ -105,7 +105,8 @@ extern "C" hz_status hz_apply_preconditioner_noalloc(const hz_medium* med, const
     launches += 3;
   }
   HZ_TRY(ox->row_inv_acc(prec, 1, planes, rec, med->segtab, med->nseg, med->rowmask, med->K, rows,
-                         rows * nrhs, n, 1.0 / double(n), tw(tx), y, st, nullptr, 0, nullptr, 0));
+                         rows * nrhs, n, 1.0 / double(n), tw(tx), y, st, nullptr, 0, nullptr, 0, med->gnode,
+                         prec == 0 ? (const void*)med->gw64 : (const void*)med->gw32));
   count_launches(launches + 1);
   return HZ_OK;
 }

@@ -58,11 +58,14 @@ size_t fft_partial_bytes(long n, int B, int m) {
 extern "C" size_t hz_request_footprint(const hz_grid* g, const hz_interp* it,
                                        const hz_solver_opts* o, int nrhs, int has_a) {
   const long n = long(g->n[0]) * g->n[1] * (g->dim == 3 ? g->n[2] : 1);
-  const int K = it->M + it->Mt;
+  const int Ka = it->Ma > 1 ? it->Ma : 1;
+  const int K = (it->M + it->Mt) * Ka;
+  const bool generic = Ka > 1 || it->basis == 1;  // per-point (node, weight) records
   const int m = o->restart;
   const size_t B = size_t(nrhs);
   const size_t es = o->precision == 0 ? 16 : 8;
-  size_t med = size_t(n) * (16 + 8 + 4 + (has_a ? 8 : 0) + 16) + size_t(n / g->n[0] + 1) * 16 + (1 << 20);
+  size_t med = size_t(n) * (16 + 8 + 4 + (has_a ? 8 : 0) + 16 + (generic ? 52 : 0)) +
+               size_t(n / g->n[0] + 1) * 16 * (generic ? 4 : 1) + (1 << 20);
   size_t plan = B * n * 16                      // tmp
                 + B * K * n * es                // planes
                 + size_t(m + 1) * B * n * 16    // V

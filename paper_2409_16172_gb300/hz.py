@@ -41,7 +41,8 @@ class hz_grid(C.Structure):
 
 class hz_interp(C.Structure):
     _fields_ = [("M", C.c_int), ("Mt", C.c_int), ("c_o", C.c_double), ("zeta_max", C.c_double),
-                ("alpha", C.c_double), ("a_node", C.c_double), ("symbol_kind", C.c_int)]
+                ("alpha", C.c_double), ("a_node", C.c_double), ("symbol_kind", C.c_int),
+                ("Ma", C.c_int), ("basis", C.c_int)]
 
 
 class hz_solver_opts(C.Structure):
@@ -204,7 +205,8 @@ class Medium:
 
     def __init__(self, c, zeta=None, a=None, *, omega: float, M: int, Mt: int = 0,
                  c_o: float = 1.0, zeta_max: float = 0.0, alpha: float = 0.15,
-                 a_node: float = 0.0, symbol_kind: int = 0, L: float = 1.0):
+                 a_node: float = 0.0, symbol_kind: int = 0, L: float = 1.0, Ma: int = 0,
+                 basis: int = 0):
         c = np.ascontiguousarray(c, dtype=np.float64)
         self.shape = c.shape
         if c.ndim not in (2, 3):
@@ -220,7 +222,7 @@ class Medium:
         for i in range(3):
             g.n[i] = dims[i]
         g.L = L
-        it = hz_interp(M, Mt, c_o, zeta_max, alpha, a_node, symbol_kind)
+        it = hz_interp(M, Mt, c_o, zeta_max, alpha, a_node, symbol_kind, Ma, basis)
         h = _vp()
         check(lib.hz_create_medium(C.byref(g), _dptr(c), _dptr(zeta), _dptr(a), float(omega),
                                    C.byref(it), C.byref(h)))

@@ -110,7 +110,7 @@ class Problem:
 
     @property
     def K(self) -> int:
-        return self.M + self.Mt
+        return (self.M + self.Mt) * max(int(self.meta.get("Ma", 1)), 1)
 
 
 def point_sources(rng, shape, width: int, nrhs: int) -> np.ndarray:
@@ -297,9 +297,11 @@ def random_field(rng, shape, nrhs: int | None = None) -> np.ndarray:
 
 def small_problem(shape, seed: int, *, M: int = 4, Mt: int = 2, width: int = 2,
                   contrast: float = 0.5, ppw: float = 6.0, zeta_max: float = DEFAULT_ZETA_MAX,
-                  a_const: float | None = None) -> Problem:
+                  a_const: float | None = None, damping: tuple | None = None) -> Problem:
     """A small smooth random medium for parity tests at any (ragged) shape:
-    a few bumps of relative height `contrast`, a `width`-cell layer."""
+    a few bumps of relative height `contrast`, a `width`-cell layer.
+    damping = (lo, hi): a(x) = omega (lo + (hi - lo) b(x)), b an independent
+    bump field scaled to [0, 1] (damping that does not follow c)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     shape = tuple(shape)
     X = coords(shape)
@@ -316,6 +318,44 @@ def small_problem(shape, seed: int, *, M: int = 4, Mt: int = 2, width: int = 2,
         c, zeta = raw, np.zeros(shape)
     omega = omega_for_ppw(float(c.min()), min(shape), ppw)
     a = None if a_const is None else np.full(shape, float(a_const))
+    if damping is not None:
+        b = damping_field(rng, shape)
+        a = omega * (damping[0] + (damping[1] - damping[0]) * b)
     f = random_field(rng, shape, 1)
     return Problem(f"small-{'x'.join(map(str, shape))}", shape, c, zeta, a, omega, 1.0, M, Mt,
                    f, 30, 1e-6, 0, width)
+
+
+def damping_field(rng, shape, n_bumps: int = 4) -> np.ndarray:
+    """An independent smooth field in [0, 1]: Gaussian bumps (sigma
+    U[0.08, 0.25], amplitude U[0.3, 1]) at uniform centres, min-max scaled."""
+    X = coords(shape)
+    b = np.zeros(shape)
+    for _ in range(n_bumps):
+        ctr = rng.uniform(-0.4, 0.4, size=len(shape))
+        s = rng.uniform(0.08, 0.25)
+        d2 = sum((X[ax] - ctr[ax]) ** 2 for ax in range(len(shape)))
+        b = b + rng.uniform(0.3, 1.0) * np.exp(-d2 / (2 * s * s))
+    return (b - b.min()) / max(b.max() - b.min(), 1e-30)
+
+
+def damping_problem(N: int = 1024, seed: int = 16179, *, Ma: int = 3,
+                    damping: tuple = (0.02, 0.2), width: int = 32, ppw: float = 8.0,
+                    M: int = 12, Mt: int = 4, nrhs: int = 1) -> Problem:
+    """The 2D bumps + gradient medium of the 1024^2 workload at side N, with a
+    damping field a(x) = omega (lo + (hi - lo) b(x)) that does not follow c
+    (b: damping_field from the same seeded stream after c and f), for the
+    bivariate (c, a) interpolation; FGMRES(40), complex64 preconditioner."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = (N, N)
+    raw = bumps(rng, shape, 20, lambda r: r.uniform(0, 1), lambda r: r.uniform(0.02, 0.1),
+                width)
+    X = coords(shape)
+    raw = raw + 0.5 * (X[1] + 0.5)
+    raw = 1.0 + (raw - raw.min()) / (raw.max() - raw.min())
+    c, zeta = finish_medium(raw, width, DEFAULT_ZETA_MAX)
+    omega = omega_for_ppw(float(c.min()), N, ppw)
+    f = point_sources(rng, shape, width, nrhs)
+    a = omega * (damping[0] + (damping[1] - damping[0]) * damping_field(rng, shape, 8))
+    return Problem(f"2d-{N}-bumps20-grad-damping-Ma{Ma}", shape, c, zeta, a, omega, 1.0, M, Mt,
+                   f, 40, 1e-6, 1, width, meta=dict(Ma=Ma, damping=damping))

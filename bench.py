@@ -548,6 +548,89 @@ def run_example1(args):
     print(json.dumps(out), flush=True)
 
 
+def run_interp(args):
+    """The interpolation forms Section 6 proposes, against the paper's
+    piecewise-linear univariate Q_M, by FGMRES(40) steps to 1e-6 and solve
+    time: (a) 2D media whose damping a(x) (omega [0.02, 0.2] and omega
+    [0.005, 0.05]) does not follow c, preconditioned univariately (every node
+    at the mean damping) and bivariately with Ma = 2, 3 (and 4) damping nodes,
+    with the node damping regularised by alpha omega (alpha = 0.1) and not
+    (alpha = 0; a > 0 everywhere); (b) the 1024^2 workload's medium with hats
+    vs quadratic Lagrange polynomials in c."""
+    import torch
+    from paper_2409_16172_gb300 import build, synth as S
+    build.build()
+    from paper_2409_16172_gb300 import hz
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(0)
+    sampler.start()
+
+    def one(p, alpha=ALPHA, **mopt):
+        med = hz.Medium(p.c, p.zeta, p.a, omega=p.omega, M=mopt.pop("M", p.M), Mt=p.Mt,
+                        c_o=p.c_o, alpha=alpha, **mopt)
+        K = med.info()["K"]
+        plan = hz.Plan(med, precision=1, restart=p.restart, tol=p.tol, graphs=True)
+        plan.autotune()
+        f = torch.from_numpy(np.ascontiguousarray(p.f[0])).cuda()
+        u = torch.zeros_like(f)
+        plan.solve(f, u, stream=stream)  # warm-up (graph capture)
+        times = []
+        for _ in range(max(1, args.steps)):
+            u.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st = plan.solve(f, u, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        apply_us = time_apply(plan, p, stream)
+        ms = float(np.median(times))
+        out = {"K": K, "iters": st[0]["iters"], "converged": bool(st[0]["converged"]),
+               "rel_true_resid": st[0]["rel_true_resid"], "ms_per_solve": ms,
+               "solves_per_s": 1e3 / ms, "apply_us": apply_us}
+        del plan, med
+        return out
+
+    N = args.int_n
+    biv = {}
+    for damping in ((0.02, 0.2), (0.005, 0.05)):
+        pd = S.damping_problem(N=N, damping=damping)
+        for alpha in (ALPHA, 0.0):
+            tag = f"a/w in {list(damping)}, alpha={alpha}"
+            biv[f"{tag}: univariate (a_k = mean a + alpha w)"] = one(
+                pd, alpha=alpha, a_node=float(pd.a.mean()))
+            for Ma in ((2, 3, 4) if alpha > 0 and damping[0] == 0.02 else (2, 3)):
+                biv[f"{tag}: bivariate Ma={Ma}"] = one(pd, alpha=alpha, Ma=Ma)
+    pc = S.config2() if N == 1024 else S.damping_problem(N=N)
+    if N != 1024:
+        pc.a = None
+    basis = {}
+    for M in (6, 8, 12):
+        basis[f"linear M={M}"] = one(pc, M=M)
+    for M in (5, 7, 11, 13):
+        basis[f"quadratic M={M}"] = one(pc, M=M, basis=1)
+    clocks = sampler.stop()
+    tag = "a/w in [0.005, 0.05], alpha=0.0"
+    u_it = biv[f"{tag}: univariate (a_k = mean a + alpha w)"]["iters"]
+    b_it = biv[f"{tag}: bivariate Ma=3"]["iters"]
+    out = {"metric": "FGMRES(40) steps to 1e-6: univariate Q_M / bivariate (c, a) Q_M with "
+                     "Ma = 3, damping a(x) in omega [0.005, 0.05] independent of c, alpha = 0",
+           "value": u_it / max(b_it, 1), "unit": "ratio of steps", "n_gpus": 1,
+           "steps": args.steps, "warmup": 1,
+           "ms_per_step": biv[f"{tag}: bivariate Ma=3"]["ms_per_solve"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": pd.name, "grid": list(pd.shape), "omega": pd.omega,
+                      "damping_over_omega": [[0.02, 0.2], [0.005, 0.05]], "M": pd.M, "Mt": pd.Mt,
+                      "restart": pd.restart, "alpha": ALPHA,
+                      "basis_study_medium": pc.name},
+           "bivariate": biv, "basis": basis, "clocks": clocks}
+    print(json.dumps(out), flush=True)
+
+
 def fit_beta(Ns, T_rows, d=2):
     """Order beta of T ~ M N^(d beta) log N as the paper's Table 1 computes
     it: slope / d of a least-squares line through (log N, log T) for each row
@@ -725,7 +808,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", choices=["cfg2", "cfg1", "cfg3", "cfg4", "serving", "example1",
-                                           "spectrum", "complexity"],
+                                           "spectrum", "complexity", "interp"],
                     default="cfg2", help="cfg2 (default): the 2D 1024^2 K=16 workload")
     ap.add_argument("--requests", type=int, default=30, help="serving: number of requests")
     ap.add_argument("--ex1-n", type=int, default=2048, help="example1: grid side N")
@@ -733,6 +816,7 @@ def main():
                     help="spectrum: grid sides N")
     ap.add_argument("--cx-n", type=int, nargs="+", default=[256, 512, 1024, 2048],
                     help="complexity: grid sides N")
+    ap.add_argument("--int-n", type=int, default=1024, help="interp: grid side N")
     ap.add_argument("--rate", type=float, default=4.0, help="serving: arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent requests")
     ap.add_argument("--cpu-iters", type=int, default=6, help="Arnoldi steps in the CPU sample")
@@ -763,6 +847,9 @@ def main():
         return
     if args.workload == "complexity":
         run_complexity(args)
+        return
+    if args.workload == "interp":
+        run_interp(args)
         return
     p = getattr(S, WORKLOADS[args.workload][0])()
     if args.impl == "reference":

@@ -245,7 +245,7 @@ def test_autotune_choices_are_valid_and_cached(hz):
     assert r["cached"] == 0
     assert r["dots_bps"] in (1, 2, 3, 4) and r["dots_vc"] in (2, 4, 8)
     assert r["upd_bps"] in (2, 4, 6, 8) and r["syminv_kpb"] in (1, 2, 4)
-    assert r["rowinv_mode"] in (0, 1, 2)
+    assert r["rowinv_mode"] in (0, 1, 2, 3) and r["col_pair"] in (0, 1, 2)
     assert 0 < r["dots_us"] <= r["dots_us_default"] * 1.0001
     u, st = plan.solve(np.ascontiguousarray(p.f))
     for b in range(2):

@@ -153,14 +153,19 @@ hz_status hz_set_allocator(void* (*alloc)(size_t bytes, void* ctx),
  * copied; the call returns after the medium is ready.  Axis lengths: 8, 12,
  * 16, 24, 32, 48, 64, 96, 128, 192, 256, 512, 1024, 2048 (z <= 1024); fewer
  * than 2^31 points.
- * Errors: HZ_ERR_INVALID_ARG (grid, options), HZ_ERR_MEDIUM (c <= 0, zeta < 0,
- * NaN, c != c_o in the layer, too few nodes), HZ_ERR_OOM, HZ_ERR_CUDA. */
+ * With interp->Ma >= 2 or interp->basis == 1 the per-point record is up to
+ * four (node, weight) pairs (52 bytes per point) instead of (segment, t).
+ * Errors: HZ_ERR_INVALID_ARG (grid, options: Ma < 0, basis not 0/1, basis 1
+ * with Ma >= 2 or an even M, (M + Mt) Ma > 64), HZ_ERR_MEDIUM (c <= 0,
+ * zeta < 0, NaN, c != c_o in the layer, too few nodes), HZ_ERR_OOM,
+ * HZ_ERR_CUDA. */
 hz_status hz_create_medium(const hz_grid* grid, const double* c, const double* zeta,
                            const double* a, double omega, const hz_interp* interp,
                            hz_medium** out);
 
 /* Node table of a medium: K = number of symbol planes, M real nodes, Mt layer
- * nodes; gamma_re/gamma_im/a_k receive K values each (may be NULL);
+ * nodes (K = (M + Mt) Ma, node k = s Ma + j in the bivariate form);
+ * gamma_re/gamma_im/a_k receive K values each (may be NULL);
  * c_min/c_max over the grid. */
 hz_status hz_medium_info(const hz_medium* med, int* K, int* M, int* Mt, double* gamma_re,
                          double* gamma_im, double* a_k, double* c_min, double* c_max);
@@ -178,9 +183,10 @@ hz_status hz_plan_create(hz_medium* med, const hz_solver_opts* opts, int max_nrh
  * launch shapes).  Times candidate launch shapes of the kernels that dominate
  * a solve on the plan's own buffers with CUDA events on `stream`: blocks per
  * SM and vectors per block of the CGS2 dot kernel, blocks per SM of the CGS2
- * update, nodes per block of the last-axis symbol pass, and whether the
- * x-inverse pass accumulates the weighted sum as it goes or transforms the
- * planes in place and gathers the sum afterwards.  The choice is stored
+ * update, nodes per block and columns per thread of the last-axis symbol
+ * pass, and whether the x-inverse pass accumulates the weighted sum as it
+ * goes, transforms the planes in place and gathers the sum afterwards, or
+ * transforms each (row, node) line on its own and adds it into the output.  The choice is stored
  * in the plan and cached per (grid, K, max_nrhs, restart, precision) for the
  * process; later plans with the same key reuse it without timing.
  * Synchronous; overwrites the plan's work arrays (call before solving). */

@@ -471,6 +471,11 @@ struct LineFFT {
   }
   static constexpr int PS = max_rad() >= 32 ? 5 : PAD_SHIFT;
   __device__ static __forceinline__ int pad(int i) { return i + (i >> PS); }
+  // For i >= 0 and a step m that is a multiple of 2^PS, pad(i + r m) =
+  // pad(i) + r padstep(m): the addresses of a stage's elements are then one
+  // per-thread base plus compile-time offsets.
+  static constexpr bool affine(int m) { return m % (1 << PS) == 0; }
+  static constexpr int padstep(int m) { return m + (m >> PS); }
   static_assert(!WS || TPL <= 32, "warp-synchronous lines need TPL <= 32");
 
   // lanes of the warp that exist: a block smaller than a warp holds lanes
@@ -490,8 +495,15 @@ struct LineFFT {
   }
 
   __device__ static __forceinline__ void load_stage0(const V* line, int t, V (&x)[E]) {
+    if constexpr (affine(TPL) && affine(N / R0)) {
+      const int pt = pad(t);
 #pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = line[pad(stage0_index(t, e)) * LS];
+      for (int e = 0; e < E; ++e)
+        x[e] = line[(pt + (e / R0) * padstep(TPL) + (e % R0) * padstep(N / R0)) * LS];
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e) x[e] = line[pad(stage0_index(t, e)) * LS];
+    }
   }
 
   template <int STAGE, int NS, bool KEEP>
@@ -502,8 +514,14 @@ struct LineFFT {
 #pragma unroll
         for (int b = 0; b < E / RAD; ++b) {
           const int j = t + b * TPL;
+          if constexpr (affine(N / RAD)) {
+            const int pj = affine(TPL) ? pad(t) + b * padstep(TPL) : pad(j);
 #pragma unroll
-          for (int r = 0; r < RAD; ++r) x[b * RAD + r] = line[pad(j + r * (N / RAD)) * LS];
+            for (int r = 0; r < RAD; ++r) x[b * RAD + r] = line[(pj + r * padstep(N / RAD)) * LS];
+          } else {
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) x[b * RAD + r] = line[pad(j + r * (N / RAD)) * LS];
+          }
         }
         sync();
       }
@@ -520,8 +538,14 @@ struct LineFFT {
         dftR<RAD, S>(&x[b * RAD]);
         if constexpr (!(KEEP && STAGE == P::NST - 1)) {
           const int d = (j / NS) * NS * RAD + k;
+          if constexpr (affine(NS)) {
+            const int pd = pad(d);
 #pragma unroll
-          for (int r = 0; r < RAD; ++r) line[pad(d + r * NS) * LS] = x[b * RAD + r];
+            for (int r = 0; r < RAD; ++r) line[(pd + r * padstep(NS)) * LS] = x[b * RAD + r];
+          } else {
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) line[pad(d + r * NS) * LS] = x[b * RAD + r];
+          }
         }
       }
       if constexpr (!(KEEP && STAGE == P::NST - 1)) sync();

@@ -603,7 +603,7 @@ line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
       V* dst = planes + (rhs * K + k) * n + off;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        if ((mb[(e * KPB) / 32] >> ((e * KPB) % 32 + kk)) & 1u) dst[F::out_index(t, e) * int(S)] = v[e];
+        if ((mb[(e * KPB) / 32] >> ((e * KPB) % 32 + (KPB == 1 ? 0 : kk))) & 1u) dst[F::out_index(t, e) * int(S)] = v[e];
       }
     }
   }
@@ -690,7 +690,7 @@ line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ p
       float2* dst = planes + (rhs * K + k) * n + off;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        if ((mb[(e * KPB) / 32] >> ((e * KPB) % 32 + kk)) & 1u)
+        if ((mb[(e * KPB) / 32] >> ((e * KPB) % 32 + (KPB == 1 ? 0 : kk))) & 1u)
           *reinterpret_cast<float4*>(dst + F::out_index(t, e) * int(S)) =
               make_float4(f2_lo(v[e].x), f2_lo(v[e].y), f2_hi(v[e].x), f2_hi(v[e].y));
       }

@@ -618,7 +618,9 @@ line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
 // per thread, smaller blocks).
 template <int N, int KPB, int TB>
 __global__ void __launch_bounds__(TB * LineCfg<float, N>::TPL,
-                                  KPB == 1 ? 2 * LineCfg<float, N>::TB / TB : 1)
+                                  KPB == 1 ? (TB * LineCfg<float, N>::TPL >= 512
+                                                  ? 1 : 512 / (TB * LineCfg<float, N>::TPL))
+                                           : 1)
 line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ planes, int nx,
                          int ntile, long S, long ostride, long n, int K,
                          const float* __restrict__ xi2_x, const float* __restrict__ xi2_o,

@@ -415,6 +415,10 @@ template <typename R, int N> struct ColPlan { using P = FftPlan<N>; };
 // complex64 columns of 512: three stages (16, 16, 2) instead of four radix-8
 // stages, one shared-memory exchange fewer
 template <> struct ColPlan<float, 512> { using P = FftPlanW<512>; };
+// The paired complex64 symbol pass: the column plan, except two radix-32
+// stages (32 pairs per thread) for 1024.
+template <typename R, int N> struct PairPlan { using P = typename ColPlan<R, N>::P; };
+template <> struct PairPlan<float, 1024> { using P = FftPlanW<1024>; };
 
 // FP64 lines up to 256 points: radix-4 (and 2, 3) stages with 4 or 12
 // elements per thread.  An FP64 instruction occupies a sub-partition's FP64

@@ -198,18 +198,17 @@ hz_status line_sym_inv_t(const void* vhat, void* planes, int nx, long outer, lon
     if (tw2 && nx % 2 == 0) {
       // pair > 1: half-size blocks
       const bool half = pair > 1;
-      constexpr int TB = C::TB, TH = C::TB_HALF;
-      auto k = half ? (kpb == 4 ? line_sym_inv_pair_kernel<N, 4, TH>
-                                : (kpb == 2 ? line_sym_inv_pair_kernel<N, 2, TH>
-                                            : line_sym_inv_pair_kernel<N, 1, TH>))
-                    : (kpb == 4 ? line_sym_inv_pair_kernel<N, 4, TB>
-                                : (kpb == 2 ? line_sym_inv_pair_kernel<N, 2, TB>
-                                            : line_sym_inv_pair_kernel<N, 1, TB>));
-      const int tb = half ? TH : TB;
+      constexpr int T1 = C::template tb_p<1>(), T1H = C::template tb_p_half<1>();
+      constexpr int Tn = C::template tb_p<2>(), TnH = C::template tb_p_half<2>();
+      auto k = kpb == 1 ? (half ? line_sym_inv_pair_kernel<N, 1, T1H> : line_sym_inv_pair_kernel<N, 1, T1>)
+             : kpb == 2 ? (half ? line_sym_inv_pair_kernel<N, 2, TnH> : line_sym_inv_pair_kernel<N, 2, Tn>)
+                        : (half ? line_sym_inv_pair_kernel<N, 4, TnH> : line_sym_inv_pair_kernel<N, 4, Tn>);
+      const int tb = kpb == 1 ? (half ? T1H : T1) : (half ? TnH : Tn);
+      const int tpl = kpb == 1 ? C::template tpl_p<1>() : C::template tpl_p<2>();
       HZ_TRY(smem_attr(k, C::col_pair_smem(tb)));
       const int ntile = (nx / 2 + tb - 1) / tb;
       dim3 grid(unsigned(ntile * outer), unsigned((K + kpb - 1) / kpb), unsigned(batch));
-      HZ_CUDA(launch_pdl(k, dim3(grid), dim3(tb * C::TPL), C::col_pair_smem(tb), st,
+      HZ_CUDA(launch_pdl(k, dim3(grid), dim3(tb * tpl), C::col_pair_smem(tb), st,
                          static_cast<const float2*>(vhat), static_cast<float2*>(planes), nx, ntile,
                          S, ostride, n, K, static_cast<const float*>(xi2_x),
                          static_cast<const float*>(xi2_o), static_cast<const float*>(xi2_l),

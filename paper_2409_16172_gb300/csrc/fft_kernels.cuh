@@ -26,6 +26,8 @@
 #include "fft_engine.cuh"
 #include "hz_internal.h"
 
+#include <type_traits>
+
 namespace hz {
 
 // Launch shapes.  Row kernels: ROW_THREADS threads, ROW_THREADS / TPL lines.
@@ -60,8 +62,25 @@ template <typename R, int N> struct LineCfg {
     return stage_offset(lines) + size_t(lines) * 2 * N * VB;
   }
   static constexpr size_t col_smem() { return size_t(TB) * padded_len(N) * VB; }
-  static constexpr size_t col_pair_smem(int tb = TB) { return size_t(tb) * padded_len(N) * 16; }
-  static constexpr int TB_HALF = TB > 1 ? TB / 2 : 1;
+  static constexpr size_t col_pair_smem(int tb) { return size_t(tb) * padded_len(N) * 16; }
+  // the paired complex64 symbol pass: its own plan (two radix-32 stages for
+  // columns of 1024), TB_P column pairs per block (>= 128 threads), or half
+  // as many; one-node blocks aim at 512 resident threads per SM, or at three
+  // blocks when a thread holds 32 pairs
+  // (blocks of several nodes keep the spectrum across nodes and use the
+  // column plan)
+  template <int KPB>
+  using PPK = typename std::conditional<KPB == 1, typename PairPlan<R, N>::P, CP>::type;
+  template <int KPB> static constexpr int tpl_p() { return N / PPK<KPB>::E; }
+  template <int KPB> static constexpr int tb_p() {
+    return tpl_p<KPB>() == TPL ? TB : (tpl_p<KPB>() >= 128 ? 1 : 128 / tpl_p<KPB>());
+  }
+  template <int KPB> static constexpr int tb_p_half() { return tb_p<KPB>() > 1 ? tb_p<KPB>() / 2 : 1; }
+  template <int KPB> static constexpr int pair_min_blocks(int tb) {
+    return KPB > 1 ? 1
+                   : (PPK<KPB>::E >= 32 ? (tb * tpl_p<KPB>() >= 384 ? 1 : 384 / (tb * tpl_p<KPB>()))
+                                        : (tb * tpl_p<KPB>() >= 512 ? 1 : 512 / (tb * tpl_p<KPB>())));
+  }
 };
 
 // 16-byte asynchronous global -> shared copies (L2 only), in groups.
@@ -617,10 +636,8 @@ line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
 // pairs per block (the scalar kernel's TB, or half of it: the same registers
 // per thread, smaller blocks).
 template <int N, int KPB, int TB>
-__global__ void __launch_bounds__(TB * LineCfg<float, N>::TPL,
-                                  KPB == 1 ? (TB * LineCfg<float, N>::TPL >= 512
-                                                  ? 1 : 512 / (TB * LineCfg<float, N>::TPL))
-                                           : 1)
+__global__ void __launch_bounds__(TB * LineCfg<float, N>::template tpl_p<KPB>(),
+                                  LineCfg<float, N>::template pair_min_blocks<KPB>(TB))
 line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ planes, int nx,
                          int ntile, long S, long ostride, long n, int K,
                          const float* __restrict__ xi2_x, const float* __restrict__ xi2_o,
@@ -629,7 +646,7 @@ line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ p
                          const unsigned long long* __restrict__ smask, long smO, long smS,
                          const float4* __restrict__ tw2, const int* __restrict__ active) {
   pdl_wait();
-  using F = LineFFT<float, N, +1, TB, false, typename LineCfg<float, N>::CP, PV>;
+  using F = LineFFT<float, N, +1, TB, false, typename LineCfg<float, N>::template PPK<KPB>, PV>;
   constexpr int E = F::E;
   static_assert(KPB == 1 || KPB == 2 || KPB == 4, "nodes per block");
   if (active && !active[blockIdx.z]) return;
@@ -647,18 +664,6 @@ line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ p
   const float2* src = vhat + rhs * n + off;
   const float so = xi2_o ? xi2_o[o] : 0.0f;
   const float sx0 = (valid ? xi2_x[x] : 0.0f) + so, sx1 = (valid ? xi2_x[x + 1] : 0.0f) + so;
-  PV spec[E];
-  f2 s2[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int p = F::stage0_index(t, e);
-    const float4 a = valid ? *reinterpret_cast<const float4*>(src + p * int(S))
-                           : make_float4(0.f, 0.f, 0.f, 0.f);
-    spec[e].x = f2_make(a.x, a.z);
-    spec[e].y = f2_make(a.y, a.w);
-    const float xl = xi2_l[p];
-    s2[e] = f2_make(sx0 + xl, sx1 + xl);
-  }
   constexpr int MW = (E * KPB + 31) / 32;
   uint32_t mb[MW];
 #pragma unroll
@@ -669,33 +674,67 @@ line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ p
     const uint32_t bits = uint32_t(smask[o * smO + p * int(smS)] >> k0) & ((1u << KPB) - 1u);
     mb[(e * KPB) / 32] |= bits << ((e * KPB) % 32);
   }
-#pragma unroll 1
-  for (int k = k0; k < k1; ++k) {
-    const float2 A = symA[k], G = symG[k];
+  // vhat q_k = vhat conj(den) / |den|^2,  den = A - G |xi|^2
+  auto symbol = [](const PV& sp, f2 s2, f2 AX, f2 AY, f2 NGX, f2 NGY) {
+    PV den;
+    den.x = fma2(NGX, s2, AX);
+    den.y = fma2(NGY, s2, AY);
+    const f2 nrm = fma2(den.x, den.x, den.y * den.y);
+    const f2 inv = f2_make(recip(f2_lo(nrm)), recip(f2_hi(nrm)));
+    const PV q = cmulc(sp, den);
+    PV r;
+    r.x = q.x * inv;
+    r.y = q.y * inv;
+    return r;
+  };
+  auto store = [&](int k, int kk, PV (&v)[E]) {
+    if (!valid) return;
+    float2* dst = planes + (rhs * K + k) * n + off;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if ((mb[(e * KPB) / 32] >> ((e * KPB) % 32 + (KPB == 1 ? 0 : kk))) & 1u)
+        *reinterpret_cast<float4*>(dst + F::out_index(t, e) * int(S)) =
+            make_float4(f2_lo(v[e].x), f2_lo(v[e].y), f2_hi(v[e].x), f2_hi(v[e].y));
+    }
+  };
+  auto load = [&](int e, PV& sp, f2& s2) {
+    const int p = F::stage0_index(t, e);
+    const float4 a = valid ? *reinterpret_cast<const float4*>(src + p * int(S))
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+    sp.x = f2_make(a.x, a.z);
+    sp.y = f2_make(a.y, a.w);
+    const float xl = xi2_l[p];
+    s2 = f2_make(sx0 + xl, sx1 + xl);
+  };
+  if constexpr (KPB == 1) {
+    // one node: the symbol product straight from the loads (no copy of the
+    // spectrum kept across nodes)
+    const float2 A = symA[k0], G = symG[k0];
     const f2 AX = f2_splat(A.x), AY = f2_splat(A.y), NGX = f2_splat(-G.x), NGY = f2_splat(-G.y);
-    const int kk = k - k0;
     PV v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      // vhat q_k = vhat conj(den) / |den|^2,  den = A - G |xi|^2
-      PV den;
-      den.x = fma2(NGX, s2[e], AX);
-      den.y = fma2(NGY, s2[e], AY);
-      const f2 nrm = fma2(den.x, den.x, den.y * den.y);
-      const f2 inv = f2_make(recip(f2_lo(nrm)), recip(f2_hi(nrm)));
-      const PV q = cmulc(spec[e], den);
-      v[e].x = q.x * inv;
-      v[e].y = q.y * inv;
+      PV sp;
+      f2 s2;
+      load(e, sp, s2);
+      v[e] = symbol(sp, s2, AX, AY, NGX, NGY);
     }
     F::run_regs(sm + col, t, v, tw2);
-    if (valid) {
-      float2* dst = planes + (rhs * K + k) * n + off;
+    store(k0, 0, v);
+  } else {
+    PV spec[E];
+    f2 s2[E];
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        if ((mb[(e * KPB) / 32] >> ((e * KPB) % 32 + (KPB == 1 ? 0 : kk))) & 1u)
-          *reinterpret_cast<float4*>(dst + F::out_index(t, e) * int(S)) =
-              make_float4(f2_lo(v[e].x), f2_lo(v[e].y), f2_hi(v[e].x), f2_hi(v[e].y));
-      }
+    for (int e = 0; e < E; ++e) load(e, spec[e], s2[e]);
+#pragma unroll 1
+    for (int k = k0; k < k1; ++k) {
+      const float2 A = symA[k], G = symG[k];
+      const f2 AX = f2_splat(A.x), AY = f2_splat(A.y), NGX = f2_splat(-G.x), NGY = f2_splat(-G.y);
+      PV v[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = symbol(spec[e], s2[e], AX, AY, NGX, NGY);
+      F::run_regs(sm + col, t, v, tw2);
+      store(k, k - k0, v);
     }
   }
 }

@@ -207,7 +207,7 @@ def test_gmres_3d_matches_oracle(hz, shape):
 
 
 @pytest.mark.parametrize("shape", [(64, 32), (128, 128), (48, 192), (8, 2048), (12, 48, 8),
-                                   (24, 16, 32)])
+                                   (24, 16, 32), (1024, 24), (512, 48)])
 def test_apply_every_launch_shape(hz, shape):
     """Every symbol-pass node grouping, one or two columns per thread (full or
     half-size blocks), and every x-inverse form (fused weighted sum; in place

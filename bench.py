@@ -209,6 +209,9 @@ def run_reference(args, p):
     print(json.dumps(out), flush=True)
 
 
+# DRAM traffic / algorithmic bytes of the CGS2 dot kernel in one ncu capture
+# (1024^2, Arnoldi step j = 13: 261.8 MB read + write, 16 n (j + 2) = 251.7 MB)
+DOTS_TRAFFIC_RATIO = 261.8 / 251.7
 FP64_DFMA_PER_CLK_PER_SM = 2  # sm_103 (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak)
 
 
@@ -408,12 +411,16 @@ def run_gpu(args, p, name):
     fp64_phases = {"cgs2_dots", "cgs2_update", "stencil", "residual", "solution_update", "norm"}
     if kname in fp64_phases:
         achieved = d["flops"] / d["ms"] / 1e9  # TFLOP/s
+        avg_bytes = d["bytes"] / d["launches"]
+        traffic = DOTS_TRAFFIC_RATIO * avg_bytes if kname == "cgs2_dots" else None
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
-                "traffic_note": "per-launch DRAM bytes vary with the Arnoldi step j (the launches "
-                                "averaged here run j = 0..39); one ncu capture at 1024^2, j = 12: "
-                                "190 MB read + write per dot launch against 218 MB algorithmic "
-                                "(profiles/kernels_2d1024_K16_ncu_full.md)",
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": traffic,
+                "traffic_note": "bytes per launch: the DRAM read + write of one ncu-captured dot "
+                                "launch (1024^2, j = 13: 261.8 MB against 251.7 MB algorithmic, "
+                                "profiles/kernels_2d1024_K16_ncu_full.md) scaled to the average "
+                                "algorithmic bytes per launch of this phase (the launches run "
+                                "j = 0..m-1, and the phase's partial-sum launches count as "
+                                "launches)",
                 "peak_source": f"FP64: {FP64_DFMA_PER_CLK_PER_SM} DFMA/clk/SM x 2 flops x "
                                f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz "
                                f"(in-library FMA probe {fp64_probe / 1e3:.3f} TFLOP/s)",

@@ -416,11 +416,10 @@ def run_gpu(args, p, name):
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": traffic,
                 "traffic_note": "bytes per launch: the DRAM read + write of one ncu-captured dot "
-                                "launch (1024^2, j = 13: 262.4 MB against 251.7 MB algorithmic, "
-                                "profiles/kernels_2d1024_K16_ncu_full.md) scaled to the average "
-                                "algorithmic bytes per launch of this phase (the launches run "
-                                "j = 0..m-1, and the phase's partial-sum launches count as "
-                                "launches)",
+                                "launch (1024^2, j = 13: 262.4 MB against 251.7 MB algorithmic) "
+                                "scaled to the average algorithmic bytes per launch of this phase "
+                                "(the launches run j = 0..m-1, and the phase's partial-sum "
+                                "launches count as launches)",
                 "peak_source": f"FP64: {FP64_DFMA_PER_CLK_PER_SM} DFMA/clk/SM x 2 flops x "
                                f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz "
                                f"(in-library FMA probe {fp64_probe / 1e3:.3f} TFLOP/s)",

@@ -378,9 +378,10 @@ def _grid_of(shape, L=1.0):
     return g
 
 
-def request_footprint(shape, M, Mt, precision=1, restart=40, nrhs=1, has_a=False) -> int:
+def request_footprint(shape, M, Mt, precision=1, restart=40, nrhs=1, has_a=False, Ma=0,
+                      basis=0) -> int:
     g = _grid_of(tuple(shape))
-    it = hz_interp(M, Mt, 1.0, 0.0, 0.15, 0.0, 0)
+    it = hz_interp(M, Mt, 1.0, 0.0, 0.15, 0.0, 0, Ma, basis)
     o = hz_solver_opts(precision, restart, 1e-6, 4000, 0, 0)
     return int(lib.hz_request_footprint(C.byref(g), C.byref(it), C.byref(o), nrhs, 1 if has_a else 0))
 
@@ -399,7 +400,8 @@ class Server:
     def submit(self, c, f, *, omega: float, M: int, Mt: int = 0, zeta=None, a=None,
                c_o: float = 1.0, zeta_max: float = 0.0, alpha: float = 0.15, a_node: float = 0.0,
                symbol_kind: int = 0, precision: int = 1, restart: int = 40, tol: float = 1e-6,
-               maxit: int = 4000, L: float = 1.0, graphs: bool = False) -> int:
+               maxit: int = 4000, L: float = 1.0, graphs: bool = False, Ma: int = 0,
+               basis: int = 0) -> int:
         c = np.ascontiguousarray(c, dtype=np.float64)
         shape = c.shape
         f = np.ascontiguousarray(f, dtype=np.complex128)
@@ -412,7 +414,7 @@ class Server:
         r.zeta = _dptr(zeta)
         r.a = _dptr(a)
         r.omega = omega
-        r.interp = hz_interp(M, Mt, c_o, zeta_max, alpha, a_node, symbol_kind)
+        r.interp = hz_interp(M, Mt, c_o, zeta_max, alpha, a_node, symbol_kind, Ma, basis)
         r.opts = hz_solver_opts(precision, restart, tol, maxit, 1 if graphs else 0, 0)
         r.nrhs = nrhs
         r.f = _vp(f.ctypes.data)

@@ -28,3 +28,17 @@ def test_footprint_of_the_config2_workload(hz):
     n = 1024 * 1024
     assert fp >= n * (41 * 16 + 40 * 8 + 16 * 8)
     assert fp <= 1.5 * n * (41 * 16 + 40 * 8 + 16 * 8) + (64 << 20)
+
+
+def test_footprint_counts_bivariate_planes_and_records(hz):
+    """Bivariate (c, a) media hold (M + Mt) Ma planes per right-hand side and
+    a 52-byte (node, weight) record per point; the quadratic basis only the
+    record."""
+    n = 512 * 512
+    base = hz.request_footprint((512, 512), 12, 4, 1, 40, 1, has_a=True)
+    biv = hz.request_footprint((512, 512), 12, 4, 1, 40, 1, has_a=True, Ma=3)
+    assert biv - base >= n * (2 * 16 * 8 + 52)
+    quad = hz.request_footprint((512, 512), 11, 4, 1, 40, 1, has_a=True, basis=1)
+    lin = hz.request_footprint((512, 512), 11, 4, 1, 40, 1, has_a=True)
+    assert quad - lin >= n * 52
+    assert hz.request_footprint((512, 512), 12, 4, 1, 40, 1, has_a=True, Ma=1) == base

@@ -475,10 +475,18 @@ row_inv_scatter_kernel(const typename cvec<R>::T* __restrict__ planes,
   V x[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) x[e] = valid ? src[F::stage0_index(t, e)] : cmk<V>(R(0), R(0));
+  // the records of this thread's output points, loaded with the line so that
+  // no global load waits behind the transform
+  using RT = typename RecT<R>::T;
+  RT rv[GEN ? 1 : E];
+  if constexpr (!GEN) {
+    const RT* rr = rec + row * N;
+#pragma unroll
+    for (int e = 0; e < E; ++e) rv[e] = valid ? rr[F::out_index(t, e)] : RT(0);
+  }
   __syncthreads();  // seg_s
   F::run_regs(sm + li * padded_len(N), t, x, tw);
   if (valid) {
-    const typename RecT<R>::T* rr = rec + row * N;
     OutT* dst = out + rhs * n + row * N;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -495,7 +503,7 @@ row_inv_scatter_kernel(const typename cvec<R>::T* __restrict__ planes,
       } else {
         int seg;
         R tf;
-        decode_rec(rr[p], seg, tf);
+        decode_rec(rv[e], seg, tf);
         const uchar2 kk = seg_s[seg];
         if (kk.x == kc) w += R(1) - tf;
         if (kk.y == kc) w += tf;

@@ -63,12 +63,11 @@ template <typename R, int N> struct LineCfg {
   }
   static constexpr size_t col_smem() { return size_t(TB) * padded_len(N) * VB; }
   static constexpr size_t col_pair_smem(int tb) { return size_t(tb) * padded_len(N) * 16; }
-  // the paired complex64 symbol pass: its own plan (two radix-32 stages for
-  // columns of 1024), TB_P column pairs per block (>= 128 threads), or half
-  // as many; one-node blocks aim at 512 resident threads per SM, or at three
-  // blocks when a thread holds 32 pairs
-  // (blocks of several nodes keep the spectrum across nodes and use the
-  // column plan)
+  // The paired complex64 symbol pass.  One-node blocks use PairPlan (two
+  // radix-32 stages for columns of 1024), blocks of several nodes, which keep
+  // the spectrum across nodes, the column plan.  tb_p column pairs per block
+  // (>= 128 threads), or half as many; one-node blocks aim at 512 resident
+  // threads per SM, 384 when a thread holds 32 pairs.
   template <int KPB>
   using PPK = typename std::conditional<KPB == 1, typename PairPlan<R, N>::P, CP>::type;
   template <int KPB> static constexpr int tpl_p() { return N / PPK<KPB>::E; }

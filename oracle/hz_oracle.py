@@ -44,7 +44,34 @@ Readings of places where the paper is silent:
   * DFT: unnormalised forward with e^{-2 pi i jk/N}, 1/n on the inverse;
     this is the discrete form of the symmetric pair in Eqn. FT.
 
-Parity status of each function is given in its docstring.
+What pins each function (tests/test_oracle_pins.py, tests/test_oracle_extensions.py; no
+function here is "parity unpinned"):
+  dft                     numpy.fft on 1D/2D/3D shapes; delta <-> constant, plane wave -> one
+                          bin (fixes the sign), Parseval
+  xi2_axis / xi2_grid     fftfreq order; the discrete table is minus the eigenvalue of the
+                          periodic second difference
+  apply_operator          plane-wave eigenfunction with gamma = c (1 - i zeta) and a > 0
+                          (fixes the signs of zeta and of i w a); O(h^2) consistency
+  real_nodes, build_nodes equispaced nodes, c_o a node, the two-segment split (and its
+                          even-interval form for the quadratic basis)
+  hat_weights             partition of unity, <= 2 non-zeros, reproduction of gamma (hats);
+                          reproduction of 1, c, c^2 and <= 3 non-zeros (quadratic basis)
+  damping_nodes, damping_weights, interp_weights
+                          reproduction of every bilinear f(c, a), <= 4 non-zeros, collapse to
+                          the univariate form for constant a
+  node_symbol             constant medium: Q_M is the Fourier multiplier of Eqn. 021; the
+                          Lemma 3 bound with the printed second derivative
+  apply_preconditioner    plane-wave closed form; equals the direct O(n^2) Op(q_M); equals the
+                          un-interpolated Op(q) where the medium takes node values;
+                          Q_{N,M} P_N = I (discrete symbol, constant c, a > 0, alpha = 0);
+                          convergence orders 2 (hats, in c and in a) and 3 (quadratic)
+  apply_pdo_direct, exact_symbol_at_point, interpolated_symbol_at_point
+                          the constant-medium closed form and the pins above
+  assemble_dense          column by column from apply_operator, then checked through the LU
+                          solves below
+  gmres, givens           right and left forms equal dense LU; unpreconditioned GMRES too;
+                          monotone Givens estimate within a cycle; preconditioning reduces the
+                          step count; the paper's Example 1 residual gap
 """
 from __future__ import annotations
 

@@ -157,11 +157,13 @@ def job_rate(dist, world: int, units_per_rank: float, ms: float):
     return ms_max, world * units_per_rank / (ms_max / 1e3)
 
 
-def oracle_solve_sample(p, iters: int, workers: int, alpha: float = ALPHA):
-    """Bounded oracle sample: one FGMRES cycle of `iters` Arnoldi steps of the
-    same workload (oracle as it stands, FP64 numpy / scipy)."""
+def oracle_solve_sample(p, iters: int, workers: int, alpha: float = ALPHA, med=None):
+    """Bounded oracle sample: `iters` (F)GMRES Arnoldi steps of the same
+    workload (oracle as it stands, FP64 numpy / scipy); med: the oracle medium
+    if already built (its construction is not timed)."""
     import oracle as O
-    med = O.make_medium(p.c, p.zeta, None, p.omega, p.M, p.Mt, p.c_o, None, alpha)
+    if med is None:
+        med = O.make_medium(p.c, p.zeta, None, p.omega, p.M, p.Mt, p.c_o, None, alpha)
     t0 = time.perf_counter()
     _, st = O.gmres(lambda u: O.apply_operator(med, u), p.f[0],
                     lambda v: O.apply_preconditioner(med, v, workers=workers),
@@ -174,23 +176,22 @@ def run_reference(args, p):
     world, rank, local, dist = dist_setup(args.gpus)
     if rank != 0:
         return
-    import oracle as O  # noqa: F401
+    import oracle as O
     workers = os.cpu_count() or 1
+    med = O.make_medium(p.c, p.zeta, None, p.omega, p.M, p.Mt, p.c_o, None, ALPHA)
     # iterations per solve: the oracle's own full solve (run once, untimed)
     med_iters = None
     if args.ref_iters <= 0:
-        import oracle as O
-        med = O.make_medium(p.c, p.zeta, None, p.omega, p.M, p.Mt, p.c_o, None, ALPHA)
         _, st = O.gmres(lambda u: O.apply_operator(med, u), p.f[0],
                         lambda v: O.apply_preconditioner(med, v, workers=workers),
                         restart=p.restart, tol=p.tol, maxit=4000)
         med_iters = st["iters"]
     iters_per_solve = med_iters or args.ref_iters
     for _ in range(args.warmup):
-        oracle_solve_sample(p, 2, workers)
+        oracle_solve_sample(p, 2, workers, ALPHA, med)
     per_it = []
     for _ in range(args.steps):
-        dt, it = oracle_solve_sample(p, args.ref_sample, workers)
+        dt, it = oracle_solve_sample(p, args.ref_sample, workers, ALPHA, med)
         per_it.append(dt / max(it, 1))
     t_it = float(np.mean(per_it))
     value = 1.0 / (t_it * iters_per_solve)
@@ -464,14 +465,21 @@ def run_gpu(args, p, name):
 
     cpu = None
     if not args.no_cpu_baseline:
+        import oracle as O
         workers = os.cpu_count() or 1
-        its = args.cpu_iters if name != "cfg3" else min(args.cpu_iters, 2)
         pc = p
         if nrhs > 1:  # one right-hand side of the batch; the rate is per solve
             import copy
             pc = copy.copy(p)
             pc.f = p.f[:1]
-        dt, it = oracle_solve_sample(pc, its, workers, alpha)
+        med_o = O.make_medium(pc.c, pc.zeta, None, pc.omega, pc.M, pc.Mt, pc.c_o, None, alpha)
+        # a probe of 2 steps, then enough steps for about args.cpu_seconds of
+        # oracle work in all (at most 400)
+        dt, it = oracle_solve_sample(pc, 2, workers, alpha, med_o)
+        more = int(min(max(args.cpu_seconds / max(dt / max(it, 1), 1e-9) - it, 0), 400))
+        if more > 0:
+            dt2, it2 = oracle_solve_sample(pc, more, workers, alpha, med_o)
+            dt, it = dt + dt2, it + it2
         iters = int(np.mean([s["iters"] for s in stats[0]]))
         cpu = {"value": 1.0 / (dt / max(it, 1) * iters), "unit": "solves/s", "cores": workers,
                "kind": "oracle",
@@ -825,7 +833,8 @@ def main():
     ap.add_argument("--int-n", type=int, default=1024, help="interp: grid side N")
     ap.add_argument("--rate", type=float, default=4.0, help="serving: arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent requests")
-    ap.add_argument("--cpu-iters", type=int, default=6, help="Arnoldi steps in the CPU sample")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target oracle time of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--tune", default="",

@@ -473,11 +473,11 @@ def run_gpu(args, p, name):
             pc = copy.copy(p)
             pc.f = p.f[:1]
         med_o = O.make_medium(pc.c, pc.zeta, None, pc.omega, pc.M, pc.Mt, pc.c_o, None, alpha)
-        # a probe of 2 steps, then enough steps for about args.cpu_seconds of
-        # oracle work in all (at most 400)
+        # a probe of 2 steps, then samples (each stops where the oracle's
+        # solve converges) until about args.cpu_seconds of oracle work
         dt, it = oracle_solve_sample(pc, 2, workers, alpha, med_o)
-        more = int(min(max(args.cpu_seconds / max(dt / max(it, 1), 1e-9) - it, 0), 400))
-        if more > 0:
+        while dt < args.cpu_seconds and it < 2000:
+            more = int(min(max(args.cpu_seconds / max(dt / max(it, 1), 1e-9) - it, 1), 400))
             dt2, it2 = oracle_solve_sample(pc, more, workers, alpha, med_o)
             dt, it = dt + dt2, it + it2
         iters = int(np.mean([s["iters"] for s in stats[0]]))

@@ -64,8 +64,10 @@ extern "C" size_t hz_request_footprint(const hz_grid* g, const hz_interp* it,
   const int m = o->restart;
   const size_t B = size_t(nrhs);
   const size_t es = o->precision == 0 ? 16 : 8;
+  // (row masks, and at most K (row, node) items of 8 bytes per row)
+  const size_t rows = size_t(n / g->n[0]);
   size_t med = size_t(n) * (16 + 8 + 4 + (has_a ? 8 : 0) + 16 + (generic ? 52 : 0)) +
-               size_t(n / g->n[0] + 1) * 16 * (generic ? 4 : 1) + (1 << 20);
+               (rows + 1) * 16 * (generic ? 4 : 1) + rows * size_t(K) * 8 + (1 << 20);
   size_t plan = B * n * 16                      // tmp
                 + B * K * n * es                // planes
                 + size_t(m + 1) * B * n * 16    // V

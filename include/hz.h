@@ -199,7 +199,12 @@ typedef struct {
   int rowinv_mode;          /* x-inverse pass: 0 by grid size, 1 in place
                                then a gather of the weighted sum, 2 fused,
                                3 one line per (row, node) in use, added
-                               into the cleared output                     */
+                               into the cleared output (bitwise
+                               reproducible with the two-node records; with
+                               the up to four weights of Ma >= 2 or
+                               basis 1 the order of the additions can
+                               change the last bits, and the autotuner
+                               leaves this form out for such media)        */
   int col_pair;             /* complex64 symbol pass: 1 two columns per
                                thread in packed FP32, 2 the same in blocks
                                of half the size, 0 one column              */

@@ -194,8 +194,11 @@ extern "C" hz_status hz_plan_autotune(hz_plan* plan, void* stream, hz_tune_repor
     }
   }
   // x-inverse pass: fused weighted sum, in place + gather, or one line per
-  // (row, node) added into the cleared output
+  // (row, node) added into the cleared output.  The last is bitwise
+  // reproducible only with at most two additions per point, so it is not a
+  // candidate for the four-weight records of the bivariate / quadratic forms.
   for (int mode : {2, 1, 3}) {
+    if (mode == 3 && med->generic) continue;
     p->tune = best;
     p->tune.rowinv_mode = mode;
     const float ms = tm.best_ms([&] {

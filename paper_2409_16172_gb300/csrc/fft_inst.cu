@@ -98,9 +98,11 @@ hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segta
     if (rhs > 65535) return HZ_ERR_INVALID_ARG;
     auto ks = gnode ? row_inv_scatter_kernel<R, N, OutT, C::ROW_LINES, true>
                     : row_inv_scatter_kernel<R, N, OutT, C::ROW_LINES, false>;
-    HZ_TRY(smem_attr(ks, C::row_smem()));
+    // line buffers, then (two-node records) one weight table per line
+    const size_t smem = C::row_smem() + (gnode ? 0 : size_t(C::ROW_LINES) * HZ_MAX_SEG * sizeof(V));
+    HZ_TRY(smem_attr(ks, smem));
     dim3 grid(unsigned((nitems + C::ROW_LINES - 1) / C::ROW_LINES), unsigned(rhs));
-    HZ_CUDA(launch_pdl(ks, dim3(grid), dim3(C::ROW_THREADS), C::row_smem(), st,
+    HZ_CUDA(launch_pdl(ks, dim3(grid), dim3(C::ROW_THREADS), smem, st,
                        static_cast<const V*>(planes), static_cast<const typename RecT<R>::T*>(rec),
                        segtab, nseg, items, nitems, K, n, R(inv_n), static_cast<const V*>(tw),
                        static_cast<OutT*>(out), active, gnode, static_cast<const GW*>(gw)));

@@ -446,7 +446,9 @@ __device__ __forceinline__ void add_out(double2* p, double x, double y) {
 // rounding of the sum depends on their arrival order, so results can differ
 // between runs by rounding (the gather form does not).
 template <typename R, int N, typename OutT, int LPB, bool GEN>
-__global__ void __launch_bounds__(LPB * LineCfg<R, N>::TPL_ROW)
+__global__ void __launch_bounds__(LPB * LineCfg<R, N>::TPL_ROW,
+                                  sizeof(R) == 4 && LPB * LineCfg<R, N>::TPL_ROW < 512
+                                      ? 512 / (LPB * LineCfg<R, N>::TPL_ROW) : 1)
 row_inv_scatter_kernel(const typename cvec<R>::T* __restrict__ planes,
                        const typename RecT<R>::T* __restrict__ rec,
                        const uchar2* __restrict__ segtab, int nseg,
@@ -462,14 +464,24 @@ row_inv_scatter_kernel(const typename cvec<R>::T* __restrict__ planes,
   if (active && !active[rhs]) return;  // the whole block
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
-  __shared__ uchar2 seg_s[HZ_MAX_SEG];
-  for (int i = threadIdx.x; i < nseg; i += blockDim.x) seg_s[i] = segtab[i];
   const int li = threadIdx.x / TPL, t = threadIdx.x % TPL;
   const long it = long(blockIdx.x) * LPB + li;
   const bool valid = it < nitems;
   const unsigned long long item = valid ? items[it] : 0ull;
   const long row = long(item >> 8);
   const int kc = int(item & 0xFFull);
+  // the line's weight of node kc on segment s, as w = a + b t (already / n):
+  // a = [k_lo == kc], b = [k_hi == kc] - a; HZ_MAX_SEG entries per line
+  // after the lines' transform buffers
+  V* wtab = reinterpret_cast<V*>(smem_raw + LineCfg<R, N>::row_smem(LPB)) + li * HZ_MAX_SEG;
+  if constexpr (!GEN) {
+    for (int i = t; i < nseg; i += TPL) {
+      const uchar2 kk = segtab[i];
+      const R a = kk.x == kc ? R(1) : R(0);
+      const R b = (kk.y == kc ? R(1) : R(0)) - a;
+      wtab[i] = cmk<V>(a * inv_n, b * inv_n);
+    }
+  }
   const V* src = planes + (rhs * K + kc) * n + row * N;
   V x[E];
 #pragma unroll
@@ -483,7 +495,7 @@ row_inv_scatter_kernel(const typename cvec<R>::T* __restrict__ planes,
 #pragma unroll
     for (int e = 0; e < E; ++e) rv[e] = valid ? rr[F::out_index(t, e)] : RT(0);
   }
-  __syncthreads();  // seg_s
+  __syncthreads();  // wtab
   F::run_regs(sm + li * padded_len(N), t, x, tw);
   if (valid) {
     OutT* dst = out + rhs * n + row * N;
@@ -503,12 +515,11 @@ row_inv_scatter_kernel(const typename cvec<R>::T* __restrict__ planes,
         int seg;
         R tf;
         decode_rec(rv[e], seg, tf);
-        const uchar2 kk = seg_s[seg];
-        if (kk.x == kc) w += R(1) - tf;
-        if (kk.y == kc) w += tf;
+        const V ab = wtab[seg];
+        w = fma(ab.y, tf, ab.x);  // already / n
       }
       if (w != R(0)) {
-        w *= inv_n;
+        if constexpr (GEN) w *= inv_n;
         add_out(dst + p, w * x[e].x, w * x[e].y);
       }
     }

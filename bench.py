@@ -211,8 +211,8 @@ def run_reference(args, p):
 
 
 # DRAM traffic / algorithmic bytes of the CGS2 dot kernel in one ncu capture
-# (1024^2, Arnoldi step j = 13: 262.0 MB read + write, 16 n (j + 2) = 251.7 MB)
-DOTS_TRAFFIC_RATIO = 262.0 / 251.7
+# (1024^2, Arnoldi step j = 13: 262.2 MB read + write, 16 n (j + 2) = 251.7 MB)
+DOTS_TRAFFIC_RATIO = 262.2 / 251.7
 FP64_DFMA_PER_CLK_PER_SM = 2  # sm_103 (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak)
 
 
@@ -417,7 +417,7 @@ def run_gpu(args, p, name):
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": traffic,
                 "traffic_note": "bytes per launch: the DRAM read + write of one ncu-captured dot "
-                                "launch (1024^2, j = 13: 262.0 MB against 251.7 MB algorithmic) "
+                                "launch (1024^2, j = 13: 262.2 MB against 251.7 MB algorithmic) "
                                 "scaled to the average algorithmic bytes per launch of this phase "
                                 "(the launches run j = 0..m-1, and the phase's partial-sum "
                                 "launches count as launches)",

@@ -369,3 +369,36 @@ def test_synth_media_respect_layer_rule():
     for p in (S.config1(), S.small_problem((16, 12), 1)):
         O.validate_medium(p.c, p.zeta, p.c_o)
         assert p.c.min() >= 1.0 - 1e-15
+
+
+# --------------------------------------------------------------------------
+# Spectrum of the preconditioned operator (Thms. 1-2, soft)
+# --------------------------------------------------------------------------
+
+def test_dense_preconditioned_spectrum_clusters_near_one():
+    """Theorems 1-2 (soft form): on a tiny grid with the FD-consistent symbol,
+    the eigenvalues of the dense Q_M P_N gather around 1 as M grows and reach
+    those of the un-interpolated Q P_N; Q_M P_N is far better conditioned
+    than P_N."""
+    shape = (12, 12)
+    X = S.coords(shape)
+    c = 1.0 + 0.5 * (1 + np.cos(2 * np.pi * X[1])) * (1 + np.cos(2 * np.pi * X[0])) / 4
+    omega = 2 * np.pi * 12 / 6
+    a = np.full(shape, 0.3 * omega)
+    spread = {}
+    P = None
+    for M in (1, 9):
+        med = O.make_medium(c, None, a, omega, M=M, c_o=1.0, alpha=0.0, a_node=0.3 * omega,
+                            symbol_kind=1)
+        if P is None:
+            P = O.assemble_dense(lambda u: O.apply_operator(med, u), shape)
+        Q = O.assemble_dense(lambda v: O.apply_preconditioner(med, v), shape)
+        d = np.abs(np.linalg.eigvals(Q @ P) - 1)
+        spread[M] = (np.median(d), np.percentile(d, 90), np.linalg.cond(Q @ P))
+    Qx = O.assemble_dense(lambda v: O.apply_pdo_direct(O.exact_symbol_at_point(med), v,
+                                                       symbol_kind=1), shape)
+    dx = np.abs(np.linalg.eigvals(Qx @ P) - 1)
+    assert spread[9][0] <= 0.5 * spread[1][0] and spread[9][1] <= 0.5 * spread[1][1], spread
+    assert abs(spread[9][0] - np.median(dx)) <= 0.1 * np.median(dx), (spread, np.median(dx))
+    assert spread[9][0] < 0.1
+    assert spread[9][2] < np.linalg.cond(P) / 10, (spread, np.linalg.cond(P))

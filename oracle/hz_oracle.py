@@ -68,7 +68,8 @@ function here is "parity unpinned"):
   apply_pdo_direct, exact_symbol_at_point, interpolated_symbol_at_point
                           the constant-medium closed form and the pins above
   assemble_dense          column by column from apply_operator, then checked through the LU
-                          solves below
+                          solves below; the dense Q_M P_N spectrum gathers near 1 as M grows
+                          and matches the un-interpolated Q P_N (Thms. 1-2, soft)
   gmres, givens           right and left forms equal dense LU; unpreconditioned GMRES too;
                           monotone Givens estimate within a cycle; preconditioning reduces the
                           step count; the paper's Example 1 residual gap

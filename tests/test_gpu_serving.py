@@ -113,3 +113,26 @@ def test_queue_limit_and_bad_request(hz):
         srv.submit(np.ones((20, 16)), np.zeros((1, 20, 16), complex), omega=3.0, M=2)
     assert e.value.status == 1
     srv.close()
+
+
+def test_extension_requests_are_served(hz):
+    """Bivariate (c, a) and quadratic-basis requests go through the server and
+    give the result of the same request solved on its own plan."""
+    p = S.small_problem((64, 96), 8, M=5, Mt=2, width=3, damping=(0.05, 0.3))
+    f = S.random_field(np.random.Generator(np.random.PCG64(8)), p.shape, 2)
+    srv = hz.Server(max_slots=2)
+    cases = [dict(Ma=3), dict(basis=1)]
+    tickets = [srv.submit(p.c, f, omega=p.omega, M=p.M, Mt=p.Mt, zeta=p.zeta, a=p.a, alpha=0.15,
+                          restart=30, tol=1e-8, **kw) for kw in cases]
+    for kw, t in zip(cases, tickets):
+        done, u, stats, status = srv.result(t)
+        assert done and status == 0 and all(s["converged"] for s in stats)
+        med_o = O.make_medium(p.c, p.zeta, p.a, p.omega, p.M, p.Mt, 1.0, None, 0.15,
+                              Ma=max(kw.get("Ma", 1), 1), basis=kw.get("basis", 0))
+        for b in range(f.shape[0]):
+            assert rel(O.apply_operator(med_o, u[b]), f[b]) <= 1e-8
+        med = hz.Medium(p.c, p.zeta, p.a, omega=p.omega, M=p.M, Mt=p.Mt, alpha=0.15, **kw)
+        plan = hz.Plan(med, precision=1, restart=30, tol=1e-8, max_nrhs=f.shape[0])
+        u1, _ = plan.solve(np.ascontiguousarray(f))
+        assert np.array_equal(u1, u), rel(u1, u)
+    srv.close()

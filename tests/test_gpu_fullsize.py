@@ -95,3 +95,23 @@ def test_config3_plane_wave_and_solve_full_size(hz):
     u, st = plan.solve(np.ascontiguousarray(p.f[0]))
     r = rel(O.apply_operator(med_o, u), p.f[0])
     assert st[0]["converged"] and r <= 1e-6, (st, r)
+
+
+@pytest.mark.parametrize("N,d,K", [(2048, 2, (12, 4)), (192, 3, (9, 3))])
+def test_largest_and_radix3_serving_grids_plane_wave(hz, N, d, K):
+    """The serving recipe's largest 2D grid (2048^2, 3 radix-16/8 stages per
+    axis) and its radix-3 3D grid (192^3 = 3 * 64 per axis): the apply of a
+    plane wave through an autotuned plan against the per-point closed form,
+    in both precisions, on 4096 sampled points."""
+    p = S.bump_problem(N, 61 + d, d=d, n_bumps=6, amp=0.8, width=24 if d == 2 else 16,
+                       ppw=8.0, M=K[0], Mt=K[1])
+    med_g, med_o = media(hz, p, alpha=0.15)
+    plan = hz.Plan(med_g, precision=1, restart=40, tol=1e-6)
+    plan.autotune()
+    kv = (37, -101) if d == 2 else (17, -29, 41)
+    w = _plane_wave(p.shape, kv)
+    pts = np.random.Generator(np.random.PCG64(63)).integers(0, p.n, 4096)
+    exp = _plane_wave_expected(med_o, p.shape, kv, pts) * w.ravel()[pts]
+    for prec, tol in ((1, 5e-5), (0, 1e-10)):
+        got = plan.apply_preconditioner(_dev(w), precision=prec).cpu().numpy().ravel()
+        assert rel(got[pts], exp) <= tol, (N, d, prec, rel(got[pts], exp))

@@ -102,7 +102,8 @@ def test_largest_and_radix3_serving_grids_plane_wave(hz, N, d, K):
     """The serving recipe's largest 2D grid (2048^2, 3 radix-16/8 stages per
     axis) and its radix-3 3D grid (192^3 = 3 * 64 per axis): the apply of a
     plane wave through an autotuned plan against the per-point closed form,
-    in both precisions, on 4096 sampled points."""
+    in both precisions, on 4096 sampled points; then the solve, checked with
+    the oracle's operator."""
     p = S.bump_problem(N, 61 + d, d=d, n_bumps=6, amp=0.8, width=24 if d == 2 else 16,
                        ppw=8.0, M=K[0], Mt=K[1])
     med_g, med_o = media(hz, p, alpha=0.15)
@@ -115,3 +116,8 @@ def test_largest_and_radix3_serving_grids_plane_wave(hz, N, d, K):
     for prec, tol in ((1, 5e-5), (0, 1e-10)):
         got = plan.apply_preconditioner(_dev(w), precision=prec).cpu().numpy().ravel()
         assert rel(got[pts], exp) <= tol, (N, d, prec, rel(got[pts], exp))
+    # and the solve, by the oracle's own operator
+    u, st = plan.solve(np.ascontiguousarray(p.f[0]))
+    r = rel(O.apply_operator(med_o, u), p.f[0])
+    assert st[0]["converged"] and r <= 1e-6, (st, r)
+    assert abs(r - st[0]["rel_true_resid"]) <= 1e-9

@@ -1,7 +1,8 @@
 // FFT pass kernels of the preconditioner apply Q_M v (Eqn. 103 / 403):
 //
 //   row_fwd       forward FFT along x of the input vector (c128 in, scaled by
-//                 the Krylov normalisation, rounded to the working precision)
+//                 the Krylov normalisation, rounded to the working precision;
+//                 optionally clears the rows of the scattering pass's output)
 //   line_pass     forward or inverse FFT along a strided axis (y, and z in 3D)
 //   line_sym_inv  last axis, one block per (column tile, group of 1/2/4 nodes):
 //                 read vhat, multiply by q_k(|xi|^2) =
@@ -11,8 +12,11 @@
 //                 columns per thread in packed f32x2 arithmetic
 //   row_inv_acc   inverse FFT along x of every plane a row needs, then the
 //                 weighted sum z = (1/n) sum_k w_k(x) plane_k(x) (Eqn. 405:
-//                 two non-zero hat weights per point); for few rows, an
-//                 in-place inverse of every used (row, node) line and a gather
+//                 two non-zero hat weights per point); or an in-place
+//                 inverse of every used (row, node) line and a gather (also
+//                 the 4-weight gather of the bivariate / quadratic records);
+//                 or one line per used (row, node) adding its weighted
+//                 result into an output cleared by row_fwd (row_inv_scatter)
 //
 // Layout: vectors [rhs][z][y][x] (x fastest); planes [rhs][k][z][y][x].
 // Every kernel reads its inputs straight into registers in the transform's

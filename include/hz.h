@@ -128,6 +128,17 @@ typedef struct {
   double rel_true_resid;   /* ||f - P_N u|| / ||f|| in FP64 at return      */
   double rel_est_resid;    /* last Givens estimate                          */
   float ms_total;          /* wall time of the solve on the stream (events) */
+  /* Phase times of this solve call (all of its right-hand sides together),
+   * filled only while hz_profile_enable(1) is on and for launches made step
+   * by step (a captured cycle graph carries no events: with opts.graphs = 1
+   * they cover the launches outside the graph); 0 otherwise.            */
+  float ms_precond;        /* preconditioner passes: FFTs, symbol, weighted sum */
+  float ms_stencil;        /* operator P_N: Arnoldi products and residuals  */
+  float ms_arnoldi;        /* CGS2 dots and updates, Givens, norms, u update */
+  double model_bytes_precond; /* algorithmic bytes of those preconditioner
+                               passes (each input read once, each output
+                               written once; planes only on the rows / slabs
+                               that use them)                              */
 } hz_solve_stats;
 
 typedef struct hz_medium hz_medium;
@@ -172,10 +183,15 @@ hz_status hz_medium_info(const hz_medium* med, int* K, int* M, int* Mt, double* 
 
 hz_status hz_destroy_medium(hz_medium* med);
 
-/* A plan owns the workspace to apply and solve with up to max_nrhs
- * right-hand sides at once on one medium (K symbol planes per right-hand
- * side, the Krylov basis and the small Hessenberg systems). The medium must
- * outlive the plan. */
+/* A plan owns the workspace to apply Q_M (Eqn. 103 / 403: the transformed
+ * input and K symbol planes per right-hand side) and to run the restarted
+ * GMRES of Section 5 ("GMRES implementation": the Krylov basis V of m + 1
+ * c128 vectors, for precision 1 the m c64 preconditioned vectors Z of
+ * flexible GMRES, and the small Hessenberg systems) for up to max_nrhs
+ * right-hand sides at once on one medium.  The medium must outlive the plan
+ * and its device must be current.  hz_plan_bytes reports the size.
+ * Errors: HZ_ERR_INVALID_ARG (precision or no_precond not 0 / 1, restart
+ * outside 1..128, tol <= 0, maxit < 1, max_nrhs < 1), HZ_ERR_OOM. */
 hz_status hz_plan_create(hz_medium* med, const hz_solver_opts* opts, int max_nrhs,
                          hz_plan** out);
 
@@ -224,9 +240,17 @@ hz_status hz_plan_bytes(const hz_plan* plan, size_t* bytes);
 
 hz_status hz_destroy_plan(hz_plan* plan);
 
-/* y = P_N x for nrhs c128 vectors (device pointers, x != y), FP64
- * (Eqn. 001, Section 5). */
-hz_status hz_apply_operator(hz_plan* plan, const void* x, void* y, int nrhs, void* stream);
+/* y = P_N x (Eqn. 001 discretised as in Section 5: the 5-point (2D) or
+ * 7-point (3D) centred second difference, periodic, with gamma^2 of
+ * Eqn. Complex_wave_speed in the layer) for nrhs vectors, x != y, device
+ * pointers.  The arithmetic is FP64 in both precisions, as the Krylov method
+ * needs it: precision 0 reads x as c128; precision 1 reads x as c64 (the
+ * form in which flexible GMRES stores its preconditioned vectors, widened
+ * exactly to FP64).  y is always c128.  Errors: HZ_ERR_INVALID_ARG for null
+ * or aliasing pointers, nrhs outside 1..max_nrhs, precision not 0 / 1, or a
+ * current device other than the medium's. */
+hz_status hz_apply_operator(hz_plan* plan, const void* x, void* y, int nrhs, int precision,
+                            void* stream);
 
 /* y = Q_M x for nrhs c128 device vectors (x may equal y).  precision 0
  * computes in complex128, 1 in complex64 (input rounded to c64, output
@@ -249,8 +273,13 @@ hz_status hz_apply_preconditioner(hz_plan* plan, const void* x, void* y, int nrh
  *     side with K = 16 in complex128, or one 512 x 512 with K <= 15 in
  *     complex64; larger requests return HZ_ERR_INVALID_ARG with the sizes.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current, and caches it for
+ *     that device's current CUDA context; a call made after the context
+ *     was destroyed and recreated (cudaDeviceReset, primary context
+ *     released and retained again) looks the address up again.  Make the
+ *     first call on each device and context before any stream capture.
+ *   - The medium's device must be the current device
+ *     (HZ_ERR_INVALID_ARG otherwise).
  *   - All calls share the one array: calls whose work overlaps on the GPU
  *     (different streams, or several host threads) race and corrupt each
  *     other's results; serialise them.  No part of the array has to start
@@ -259,9 +288,13 @@ hz_status hz_apply_preconditioner(hz_plan* plan, const void* x, void* y, int nrh
 hz_status hz_apply_preconditioner_noalloc(const hz_medium* med, const void* x, void* y, int nrhs,
                                           int precision, void* stream);
 
-/* Solve P_N u = f for nrhs right-hand sides with restarted (F)GMRES(m):
- * CGS2 Arnoldi in FP64, complex Givens rotations, true-residual check after
- * each cycle whose estimate reached tol.  f and u are c128 arrays of
+/* Solve P_N u = f (Eqn. 001 discretised as in Section 5) for nrhs
+ * right-hand sides with the restarted GMRES of Section 5 ("GMRES
+ * implementation"; the paper preconditions from the left, this library from
+ * the right, flexibly for precision 1, so that tol applies to the true
+ * unpreconditioned residual): CGS2 Arnoldi in FP64, complex Givens
+ * rotations, true-residual check after each cycle whose estimate reached
+ * tol.  f and u are c128 arrays of
  * nrhs * n elements in device OR host memory (host buffers are staged
  * through the plan); u holds the initial guess on entry.  stats receives
  * nrhs entries (may be NULL).  Synchronous: returns when the solve is done.

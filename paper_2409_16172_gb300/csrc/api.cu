@@ -287,15 +287,31 @@ extern "C" hz_status hz_destroy_plan(hz_plan* plan) {
   return HZ_OK;
 }
 
-extern "C" hz_status hz_apply_operator(hz_plan* plan, const void* x, void* y, int nrhs, void* stream) {
+// The medium's arrays live on the device that was current when it was
+// created; every call that launches work on them must run with that device
+// current.
+hz_status hz::check_device(const hz_medium* med) {
+  int dev = 0;
+  HZ_CUDA(cudaGetDevice(&dev));
+  if (dev != med->device)
+    return set_error(HZ_ERR_INVALID_ARG, "the medium lives on device %d but device %d is current",
+                     med->device, dev);
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_apply_operator(hz_plan* plan, const void* x, void* y, int nrhs,
+                                       int precision, void* stream) {
   if (!plan || !x || !y) return set_error(HZ_ERR_INVALID_ARG, "null argument");
   if (nrhs < 1 || nrhs > plan->max_nrhs) return set_error(HZ_ERR_INVALID_ARG, "nrhs out of range");
+  if (precision != 0 && precision != 1) return set_error(HZ_ERR_INVALID_ARG, "precision must be 0 or 1");
   if (x == y) return set_error(HZ_ERR_INVALID_ARG, "x and y must not alias");
+  HZ_TRY(check_device(plan->med));
   const long n = plan->med->n;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  PhaseScope ps(st, PH_STENCIL, double(nrhs) * n * (48.0 + (plan->med->a ? 8.0 : 0.0)),
+  const double sin = precision == 0 ? 16.0 : 8.0;
+  PhaseScope ps(st, PH_STENCIL, double(nrhs) * n * (sin + 32.0 + (plan->med->a ? 8.0 : 0.0)),
                 double(nrhs) * n * (plan->med->dim == 3 ? 30.0 : 26.0));
-  return launch_stencil(plan->med, 0, x, n, static_cast<double2*>(y), n, nrhs, nullptr, st);
+  return launch_stencil(plan->med, precision, x, n, static_cast<double2*>(y), n, nrhs, nullptr, st);
 }
 
 extern "C" hz_status hz_apply_preconditioner(hz_plan* plan, const void* x, void* y, int nrhs,
@@ -303,6 +319,7 @@ extern "C" hz_status hz_apply_preconditioner(hz_plan* plan, const void* x, void*
   if (!plan || !x || !y) return set_error(HZ_ERR_INVALID_ARG, "null argument");
   if (nrhs < 1 || nrhs > plan->max_nrhs) return set_error(HZ_ERR_INVALID_ARG, "nrhs out of range");
   if (precision != 0 && precision != 1) return set_error(HZ_ERR_INVALID_ARG, "precision must be 0 or 1");
+  HZ_TRY(check_device(plan->med));
   return precond_apply(plan, precision, static_cast<const double2*>(x), nullptr, nrhs, y, 1,
                        static_cast<cudaStream_t>(stream), nullptr);
 }

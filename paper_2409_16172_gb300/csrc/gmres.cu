@@ -120,8 +120,24 @@ hz_status gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs, hz_
   const double tol = p->opts.tol;
   const long ldb = B;  // basis vector i of rhs b at V + (i * B + b) * n
 
+  HZ_TRY(check_device(med));
   HZ_TRY(solve_ws_create(p));
   SolveWs& w = *p->ws;
+  // per-solve phase times (only while profiling is on; nothing is timed
+  // inside a captured graph)
+  SolveSink sink;
+  struct SinkGuard {
+    SolveSink* s;
+    bool on;
+    void finish() {
+      if (!on) return;
+      set_solve_sink(nullptr);
+      resolve_solve_sink(s);
+      on = false;
+    }
+    ~SinkGuard() { finish(); }
+  } sink_guard{&sink, profiling()};
+  if (sink_guard.on) set_solve_sink(&sink);
   KsDev& ks = w.ks;
   (void)tol;
   HZ_CUDA(cudaEventRecord(w.t0, st));
@@ -381,6 +397,14 @@ hz_status gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs, hz_
   HZ_CUDA(cudaEventSynchronize(w.t1));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, w.t0, w.t1);
+  sink_guard.finish();
+  const float ms_pre = float(sink.ms[PH_ROW_FWD] + sink.ms[PH_LINE] + sink.ms[PH_SYMINV] +
+                             sink.ms[PH_ROW_INV]);
+  const float ms_op = float(sink.ms[PH_STENCIL] + sink.ms[PH_RESID]);
+  const float ms_arn = float(sink.ms[PH_DOTS] + sink.ms[PH_UPDATE] + sink.ms[PH_GIVENS] +
+                             sink.ms[PH_NORM] + sink.ms[PH_SOLUPD]);
+  const double pre_bytes = sink.bytes[PH_ROW_FWD] + sink.bytes[PH_LINE] + sink.bytes[PH_SYMINV] +
+                           sink.bytes[PH_ROW_INV];
   hz_status ret = HZ_OK;
   for (int b = 0; b < nrhs; ++b) {
     if (stats) {
@@ -391,6 +415,10 @@ hz_status gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs, hz_
       stats[b].rel_true_resid = rel[b];
       stats[b].rel_est_resid = est[b];
       stats[b].ms_total = ms;
+      stats[b].ms_precond = ms_pre;
+      stats[b].ms_stencil = ms_op;
+      stats[b].ms_arnoldi = ms_arn;
+      stats[b].model_bytes_precond = pre_bytes;
     }
     if (!conv[b]) {
       const hz_status sb = status[b] == HZ_OK ? HZ_ERR_NOT_CONVERGED : hz_status(status[b]);

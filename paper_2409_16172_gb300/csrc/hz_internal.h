@@ -121,6 +121,7 @@ __device__ __forceinline__ double f2d_bits(float f) {
 }  // namespace hz
 
 struct hz_medium {
+  int device = 0;  // CUDA device that holds the medium's arrays (current at create time)
   int dim = 2;
   int nx = 0, ny = 1, nz = 1;
   long n = 0;
@@ -214,6 +215,16 @@ enum Phase {
 };
 void count_launches(int k);
 bool profiling();
+// Per-solve sums of the phases timed while a SolveSink is installed on the
+// calling thread (profiling on, launches outside graph capture).
+struct SolveSink {
+  double ms[PH_COUNT] = {};
+  double bytes[PH_COUNT] = {};
+};
+void set_solve_sink(SolveSink* sink);   // thread-local; nullptr to remove
+void resolve_solve_sink(SolveSink* sink);  // waits for and adds this sink's events
+// HZ_ERR_INVALID_ARG unless the medium's device is the current one
+hz_status check_device(const hz_medium* med);
 // Records an event pair around the launches made while it is alive.
 struct PhaseScope {
   PhaseScope(cudaStream_t st, Phase ph, double bytes, double flops, int launches = 1);
@@ -223,6 +234,7 @@ struct PhaseScope {
   double bytes, flops;
   int launches;
   int slot = -1;
+  SolveSink* sink = nullptr;
 };
 
 }  // namespace hz

@@ -374,7 +374,13 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
                      "need Ma >= 0, basis 0 or 1 (1 only with Ma <= 1), (M + Mt) Ma <= %d",
                      HZ_MAX_K);
 
+  int dev = 0;
+  {
+    const cudaError_t de = cudaGetDevice(&dev);
+    if (de != cudaSuccess) return cuda_error(de, "cudaGetDevice");
+  }
   hz_medium* m = new hz_medium();
+  m->device = dev;
   m->dim = grid->dim;
   m->nx = grid->n[0];
   m->ny = grid->n[1];

@@ -10,6 +10,8 @@
 // fixed size, so the call itself allocates nothing.  The array is part of the
 // library's device image: every GPU that loads the library holds it until the
 // process exits.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "hz_internal.h"
@@ -21,10 +23,53 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
+// The array's device address belongs to the CUDA context that loaded the
+// library's module on that device.  A context can be destroyed and a new one
+// created on the same device (cudaDeviceReset, or the primary context
+// released and retained again); the new context holds its own copy of the
+// array at an address that may differ.  So the cached address is keyed on the
+// context's unique id (cuCtxGetId, never reused within a process), not on the
+// device ordinal alone, and is looked up again when the id changes.
+struct ScratchSlot {
+  unsigned long long ctx_id = 0;  // 0: nothing cached
+  void* ptr = nullptr;
+};
 std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
+ScratchSlot g_slot[kMaxDevices];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Id of the calling thread's current context (after cudaGetDevice has made
+// the device's primary context current if there was none).
+hz_status current_context_id(unsigned long long* id) {
+  if (!g_ctx_current || !g_ctx_id) {
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    const cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000,
+                                                           cudaEnableDefault, &q1);
+    const cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000,
+                                                           cudaEnableDefault, &q2);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || q1 != cudaDriverEntryPointSuccess ||
+        q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return hz::set_error(HZ_ERR_CUDA, "driver entry points cuCtxGetCurrent / cuCtxGetId not found");
+    g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    g_ctx_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx)
+    return hz::set_error(HZ_ERR_CUDA, "no current CUDA context");
+  unsigned long long cid = 0;
+  if (g_ctx_id(ctx, &cid) != CUDA_SUCCESS || cid == 0)
+    return hz::set_error(HZ_ERR_CUDA, "cuCtxGetId failed");
+  *id = cid;
+  return HZ_OK;
+}
 
 }  // namespace
 
@@ -45,21 +90,29 @@ extern "C" hz_status hz_apply_preconditioner_noalloc(const hz_medium* med, const
                      "the static limit is %zu bytes",
                      need, es, kScratchBytes);
 
-  // Set-up, once per device with that device current: the host-side name of
-  // the array is not a device address; ask the runtime for it.
+  // Set-up, once per device and context with that device current: the
+  // host-side name of the array is not a device address; ask the runtime
+  // for it, and ask again when the context has changed.
   int dev = 0;
   HZ_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return set_error(HZ_ERR_INVALID_ARG, "device id %d too large", dev);
+  if (dev != med->device)
+    return set_error(HZ_ERR_INVALID_ARG, "the medium lives on device %d but device %d is current",
+                     med->device, dev);
   void* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    unsigned long long cid = 0;
+    HZ_TRY(current_context_id(&cid));
+    ScratchSlot& slot = g_slot[dev];
+    if (slot.ctx_id != cid || !slot.ptr) {
       void* p = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(scratch)");
-      g_scratch_ptr[dev] = p;
+      slot.ctx_id = cid;
+      slot.ptr = p;
     }
-    scratch = g_scratch_ptr[dev];
+    scratch = slot.ptr;
   }
   unsigned char* base = static_cast<unsigned char*>(scratch);
   void* tmp = base;

@@ -20,6 +20,7 @@ struct Pending {
   double bytes, flops;
   int launches;
   bool live;
+  SolveSink* sink;
 };
 
 struct Acc {
@@ -33,11 +34,14 @@ std::mutex g_mu;
 std::vector<Pending> g_pend;
 std::vector<int> g_free_slots;
 Acc g_acc[PH_COUNT];
+thread_local SolveSink* g_tls_sink = nullptr;
 
-void resolve_locked() {
+// only: resolve only the entries of this sink (nullptr: every entry)
+void resolve_locked(SolveSink* only = nullptr) {
   for (size_t i = 0; i < g_pend.size(); ++i) {
     Pending& p = g_pend[i];
     if (!p.live) continue;
+    if (only && p.sink != only) continue;
     float ms = 0.f;
     if (cudaEventSynchronize(p.e1) == cudaSuccess && cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) {
       Acc& a = g_acc[p.ph];
@@ -45,6 +49,10 @@ void resolve_locked() {
       a.ms += ms;
       a.bytes += p.bytes;
       a.flops += p.flops;
+      if (p.sink) {
+        p.sink->ms[p.ph] += ms;
+        p.sink->bytes[p.ph] += p.bytes;
+      }
     } else {
       cudaGetLastError();
     }
@@ -72,6 +80,14 @@ void count_launches(int k) {
 }
 bool profiling() { return g_on.load(std::memory_order_relaxed); }
 
+void set_solve_sink(SolveSink* sink) { g_tls_sink = sink; }
+
+void resolve_solve_sink(SolveSink* sink) {
+  if (!sink) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  resolve_locked(sink);
+}
+
 PhaseScope::PhaseScope(cudaStream_t s, Phase p, double b, double f, int l)
     : st(s), ph(p), bytes(b), flops(f), launches(l) {
   count_launches(l);
@@ -94,6 +110,7 @@ PhaseScope::PhaseScope(cudaStream_t s, Phase p, double b, double f, int l)
   }
   slot = g_free_slots.back();
   g_free_slots.pop_back();
+  sink = g_tls_sink;
   cudaEventRecord(g_pend[slot].e0, st);
 }
 
@@ -106,6 +123,7 @@ PhaseScope::~PhaseScope() {
   p.bytes = bytes;
   p.flops = flops;
   p.launches = launches;
+  p.sink = sink;
   p.live = true;
 }
 

@@ -53,7 +53,9 @@ class hz_solver_opts(C.Structure):
 class hz_solve_stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("status", C.c_int),
                 ("converged", C.c_int), ("rel_true_resid", C.c_double),
-                ("rel_est_resid", C.c_double), ("ms_total", C.c_float)]
+                ("rel_est_resid", C.c_double), ("ms_total", C.c_float),
+                ("ms_precond", C.c_float), ("ms_stencil", C.c_float), ("ms_arnoldi", C.c_float),
+                ("model_bytes_precond", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -100,7 +102,7 @@ _SIGS = {
     "hz_plan_create": (C.c_int, [_vp, C.POINTER(hz_solver_opts), C.c_int, C.POINTER(_vp)]),
     "hz_plan_bytes": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
     "hz_destroy_plan": (C.c_int, [_vp]),
-    "hz_apply_operator": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
+    "hz_apply_operator": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
     "hz_apply_preconditioner": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
     "hz_gmres_solve": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(hz_solve_stats), _vp]),
     "hz_gmres_solve_history": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(hz_solve_stats),
@@ -307,12 +309,18 @@ class Plan:
         return b.value
 
     def apply_operator(self, x, out=None, stream=None):
+        """y = P_N x in FP64 (hz_apply_operator).  x: complex128 CUDA tensor
+        (precision 0) or complex64 (precision 1, widened exactly); the result
+        is complex128."""
         import torch
-        _check_dev(x, "x")
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.is_contiguous()
+                and x.dtype in (torch.complex128, torch.complex64)):
+            raise TypeError("x must be a contiguous complex128 or complex64 CUDA tensor")
+        prec = 0 if x.dtype == torch.complex128 else 1
         nrhs = x.numel() // self.medium.n
-        out = torch.empty_like(x) if out is None else out
+        out = torch.empty(x.shape, dtype=torch.complex128, device=x.device) if out is None else out
         _check_dev(out, "out")
-        check(lib.hz_apply_operator(self._h, _vp(x.data_ptr()), _vp(out.data_ptr()), nrhs,
+        check(lib.hz_apply_operator(self._h, _vp(x.data_ptr()), _vp(out.data_ptr()), nrhs, prec,
                                     _stream(stream)))
         return out
 

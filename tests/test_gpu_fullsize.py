@@ -10,7 +10,7 @@ import pytest
 import oracle as O
 from paper_2409_16172_gb300 import synth as S
 
-from gpu_util import hz_module, media, rel
+from gpu_util import hz_module, media, rel, within
 
 pytestmark = pytest.mark.gpu
 
@@ -54,14 +54,14 @@ def test_config2_apply_and_solve_full_size(hz):
     v = S.random_field(np.random.Generator(np.random.PCG64(31)), p.shape)
     ref = O.apply_preconditioner(med_o, v)
     got = plan.apply_preconditioner(_dev(v), precision=1).cpu().numpy()
-    assert rel(got, ref) <= 5e-5, rel(got, ref)
+    assert within(rel(got, ref), 1, "cfg2"), rel(got, ref)
     # plane wave through the same plan
     kv = (37, -101)
     w = _plane_wave(p.shape, kv)
     got = plan.apply_preconditioner(_dev(w), precision=1).cpu().numpy().ravel()
     pts = np.random.Generator(np.random.PCG64(32)).integers(0, p.n, 4096)
     exp = _plane_wave_expected(med_o, p.shape, kv, pts) * w.ravel()[pts]
-    assert rel(got[pts], exp) <= 5e-5
+    assert within(rel(got[pts], exp), 1, "cfg2"), rel(got[pts], exp)
     # the solve the benchmark times; residual by the oracle's operator
     u, st = plan.solve(np.ascontiguousarray(p.f[0]))
     r = rel(O.apply_operator(med_o, u), p.f[0])
@@ -78,7 +78,29 @@ def test_config4_batched_apply_sampled_rhs(hz):
     v = S.random_field(np.random.Generator(np.random.PCG64(33)), p.shape, nrhs)
     got = plan.apply_preconditioner(_dev(v), precision=1).cpu().numpy()
     for b in (0, nrhs // 2, nrhs - 1):
-        assert rel(got[b], O.apply_preconditioner(med_o, v[b])) <= 5e-5
+        e = rel(got[b], O.apply_preconditioner(med_o, v[b]))
+        assert within(e, 1, "cfg4"), (b, e)
+
+
+def test_config4_batched_solve_every_rhs(hz):
+    """The 512^2 x 64 batched FGMRES(40) solve the benchmark times (autotuned
+    plan, captured cycle graphs, all 64 right-hand sides in lock step):
+    every right-hand side's true residual, computed by the oracle's own
+    operator from the returned solution, meets the tolerance and agrees with
+    the residual the library reports."""
+    p = S.config4()
+    med_g, med_o = media(hz, p, alpha=0.15)
+    nrhs = p.f.shape[0]
+    plan = hz.Plan(med_g, precision=1, restart=p.restart, tol=p.tol, max_nrhs=nrhs, graphs=True)
+    plan.autotune()
+    f = _dev(p.f)
+    u, st = plan.solve(f)
+    u = u.cpu().numpy()
+    assert len(st) == nrhs
+    for b in range(nrhs):
+        r = rel(O.apply_operator(med_o, u[b]), p.f[b])
+        assert st[b]["converged"] and r <= p.tol, (b, st[b], r)
+        assert abs(r - st[b]["rel_true_resid"]) <= 1e-9, (b, r, st[b]["rel_true_resid"])
 
 
 def test_config3_plane_wave_and_solve_full_size(hz):
@@ -91,7 +113,7 @@ def test_config3_plane_wave_and_solve_full_size(hz):
     got = plan.apply_preconditioner(_dev(w), precision=1).cpu().numpy().ravel()
     pts = np.random.Generator(np.random.PCG64(34)).integers(0, p.n, 4096)
     exp = _plane_wave_expected(med_o, p.shape, kv, pts) * w.ravel()[pts]
-    assert rel(got[pts], exp) <= 5e-5
+    assert within(rel(got[pts], exp), 1, "cfg3"), rel(got[pts], exp)
     u, st = plan.solve(np.ascontiguousarray(p.f[0]))
     r = rel(O.apply_operator(med_o, u), p.f[0])
     assert st[0]["converged"] and r <= 1e-6, (st, r)
@@ -113,9 +135,9 @@ def test_largest_and_radix3_serving_grids_plane_wave(hz, N, d, K):
     w = _plane_wave(p.shape, kv)
     pts = np.random.Generator(np.random.PCG64(63)).integers(0, p.n, 4096)
     exp = _plane_wave_expected(med_o, p.shape, kv, pts) * w.ravel()[pts]
-    for prec, tol in ((1, 5e-5), (0, 1e-10)):
+    for prec in (1, 0):
         got = plan.apply_preconditioner(_dev(w), precision=prec).cpu().numpy().ravel()
-        assert rel(got[pts], exp) <= tol, (N, d, prec, rel(got[pts], exp))
+        assert within(rel(got[pts], exp), prec, f"grid{N}"), (N, d, prec, rel(got[pts], exp))
     # and the solve, by the oracle's own operator
     u, st = plan.solve(np.ascontiguousarray(p.f[0]))
     r = rel(O.apply_operator(med_o, u), p.f[0])

@@ -13,7 +13,7 @@ import pytest
 import oracle as O
 from paper_2409_16172_gb300 import synth as S
 
-from gpu_util import hz_module, media, rel
+from gpu_util import hz_module, media, rel, within
 
 pytestmark = pytest.mark.gpu
 
@@ -51,12 +51,12 @@ def test_apply_matches_oracle(hz, shape, form):
     np.testing.assert_allclose(info["a"], med_o.nodes.a, rtol=1e-15, atol=0)
     v = S.random_field(np.random.Generator(np.random.PCG64(22)), shape, 2)
     ref = np.stack([O.apply_preconditioner(med_o, v[b]) for b in range(2)])
-    for prec, tol in ((0, 1e-10), (1, 5e-5)):
+    for prec in (0, 1):
         plan = hz.Plan(med_g, precision=prec, max_nrhs=2)
         for mode in (0, 1, 3):
             plan.set_tune(rowinv_mode=mode)
             got = plan.apply_preconditioner(_dev(v), precision=prec).cpu().numpy()
-            assert rel(got, ref) <= tol, (form, prec, mode, rel(got, ref))
+            assert within(rel(got, ref), prec, "interp_small"), (form, prec, mode, rel(got, ref))
 
 
 def test_bad_extension_options_are_refused(hz):
@@ -100,9 +100,9 @@ def test_full_size_apply_plane_wave(hz, form):
     w = _plane_wave(p.shape, kv)
     pts = np.random.Generator(np.random.PCG64(32)).integers(0, p.n, 4096)
     exp = _plane_wave_expected(med_o, p.shape, kv, pts) * w.ravel()[pts]
-    for prec, tol in ((1, 5e-5), (0, 1e-10)):
+    for prec in (1, 0):
         got = plan.apply_preconditioner(_dev(w), precision=prec).cpu().numpy().ravel()
-        assert rel(got[pts], exp) <= tol, (form, prec, rel(got[pts], exp))
+        assert within(rel(got[pts], exp), prec, "interp_full"), (form, prec, rel(got[pts], exp))
 
 
 @pytest.mark.parametrize("mopt", [dict(Ma=3), dict(M=7, basis=1)])
@@ -126,7 +126,7 @@ def test_noalloc_apply_on_bivariate_medium(hz):
     med, _ = media(hz, p, oracle=False, Ma=3)
     plan = hz.Plan(med, precision=1)
     x = _dev(S.random_field(np.random.Generator(np.random.PCG64(6)), p.shape, 1))
-    for prec, tol in ((0, 1e-10), (1, 5e-5)):
+    for prec in (0, 1):
         y = torch.zeros_like(x)
         s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
         st = hz.lib.hz_apply_preconditioner_noalloc(med.handle, ctypes.c_void_p(x.data_ptr()),
@@ -134,4 +134,4 @@ def test_noalloc_apply_on_bivariate_medium(hz):
         assert st == 0
         ref = plan.apply_preconditioner(x, precision=prec)
         torch.cuda.synchronize()
-        assert rel(y.cpu().numpy(), ref.cpu().numpy()) <= tol
+        assert within(rel(y.cpu().numpy(), ref.cpu().numpy()), prec, "same_path")

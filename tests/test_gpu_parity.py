@@ -1,15 +1,16 @@
 """Parity of the CUDA path against the CPU oracle, element by element, on
 seeded synthetic media (several tiles, ragged tails, 2D and 3D), through the
 C ABI.  Tolerances: 1e-10 relative (2-norm) for the FP64 apply, operator and
-solve pieces; 5e-5 for the complex64 preconditioner apply (FP32 rounding,
-~eps32 log2(n), amplified near |xi| = omega / c_k by at most 1/alpha)."""
+solve pieces; for the complex64 preconditioner apply the stated per-family
+bound of gpu_util.C64_BOUND (FP32 rounding, ~eps32 log2(n), amplified near
+|xi| = omega / c_k by at most 1/alpha)."""
 import numpy as np
 import pytest
 
 import oracle as O
 from paper_2409_16172_gb300 import synth as S
 
-from gpu_util import hz_module, media, rel
+from gpu_util import hz_module, media, rel, within
 
 pytestmark = pytest.mark.gpu
 
@@ -67,7 +68,7 @@ def test_apply_preconditioner_c64(hz, shape):
     v = S.random_field(np.random.Generator(np.random.PCG64(6)), shape)
     ref = O.apply_preconditioner(med_o, v)
     got = plan.apply_preconditioner(_dev(v), precision=1).cpu().numpy()
-    assert rel(got, ref) <= 5e-5, rel(got, ref)
+    assert within(rel(got, ref), 1, "small"), rel(got, ref)
 
 
 @pytest.mark.parametrize("shape", [(16, 16), (24, 48), (8, 12, 16)])
@@ -93,6 +94,14 @@ def test_apply_operator(hz, shape):
     ref = np.stack([O.apply_operator(med_o, v[b]) for b in range(3)])
     got = plan.apply_operator(_dev(v)).cpu().numpy()
     assert rel(got, ref) <= 1e-12, rel(got, ref)
+    # precision 1: complex64 input (as flexible GMRES stores Z), FP64
+    # arithmetic; the reference is the oracle's operator on the same
+    # complex64-rounded values, so only FP64 rounding separates them
+    v32 = v.astype(np.complex64)
+    ref32 = np.stack([O.apply_operator(med_o, v32[b].astype(np.complex128)) for b in range(3)])
+    got32 = plan.apply_operator(_dev(v32)).cpu().numpy()
+    assert got32.dtype == np.complex128
+    assert rel(got32, ref32) <= 1e-12, rel(got32, ref32)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -108,6 +117,36 @@ def test_gmres_small_matches_dense_and_oracle(hz, prec):
     A = O.assemble_dense(lambda x: O.apply_operator(med_o, x), p.shape)
     x_lu = np.linalg.solve(A, p.f[0].ravel()).reshape(p.shape)
     assert rel(u, x_lu) <= 1e-7
+
+
+def test_solve_stats_phase_times(hz):
+    """hz_solve_stats carries the solve's own phase times and the
+    preconditioner's algorithmic bytes while profiling is on (step by step),
+    and zeros otherwise; the phases fit inside the solve's wall time."""
+    p = S.small_problem((64, 96), 16, M=5, Mt=3, width=3)
+    med, _ = media(hz, p, oracle=False)
+    K = med.info()["K"]
+    n = p.n
+    plan = hz.Plan(med, precision=1, restart=20, tol=1e-8, maxit=2000)
+    u, st = plan.solve(_dev(p.f[0]))
+    assert st[0]["converged"]
+    assert st[0]["ms_precond"] == 0 and st[0]["ms_arnoldi"] == 0
+    assert st[0]["model_bytes_precond"] == 0
+    hz.profile_enable(True)
+    try:
+        u, st = plan.solve(_dev(p.f[0]))
+    finally:
+        hz.profile_enable(False)
+        hz.profile_read(reset=True)
+    s = st[0]
+    assert s["converged"]
+    assert s["ms_precond"] > 0 and s["ms_stencil"] > 0 and s["ms_arnoldi"] > 0
+    assert s["ms_precond"] + s["ms_stencil"] + s["ms_arnoldi"] <= s["ms_total"] * 1.01
+    # one complex64 apply per Arnoldi step: between the input and output
+    # alone (24 B/pt) and the fixed model with every plane (plus the output
+    # cleared by the scattering form)
+    per_apply = s["model_bytes_precond"] / s["iters"]
+    assert 24 * n <= per_apply <= n * ((4 + 2 * K) * 8 + 4 + 32), (per_apply, n, K)
 
 
 def test_gmres_config1_fp64(hz):
@@ -217,14 +256,14 @@ def test_apply_every_launch_shape(hz, shape):
     med_g, med_o = media(hz, p)
     v = S.random_field(np.random.Generator(np.random.PCG64(15)), shape, 2)
     ref = np.stack([O.apply_preconditioner(med_o, v[b]) for b in range(2)])
-    for prec, tol in ((0, 1e-10), (1, 5e-5)):
+    for prec in (0, 1):
         plan = hz.Plan(med_g, precision=prec, max_nrhs=2)
         for kpb, mode, pair in ((1, 1, 1), (1, 2, 0), (2, 2, 1), (4, 1, 0), (4, 2, 1), (2, 0, 1),
                                 (1, 0, 0), (1, 2, 2), (2, 1, 2), (4, 0, 2), (1, 3, 1), (2, 3, 0),
                                 (4, 3, 2)):
             plan.set_tune(syminv_kpb=kpb, rowinv_mode=mode, col_pair=pair)
             got = plan.apply_preconditioner(_dev(v), precision=prec).cpu().numpy()
-            assert rel(got, ref) <= tol, (prec, kpb, mode, pair, rel(got, ref))
+            assert within(rel(got, ref), prec, "small"), (prec, kpb, mode, pair, rel(got, ref))
 
 
 def test_set_tune_rejects_out_of_range(hz):
@@ -278,4 +317,4 @@ def test_scattering_x_inverse_is_bitwise_reproducible(hz):
         alone = plan.apply_preconditioner(_dev(v[1:2]), precision=prec).cpu().numpy()
         assert np.array_equal(alone[0], outs[0][1])
         ref = O.apply_preconditioner(med_o, v[0])
-        assert rel(outs[0][0], ref) <= (1e-10 if prec == 0 else 5e-5)
+        assert within(rel(outs[0][0], ref), prec, "small")

@@ -15,7 +15,9 @@
  *   - Grid: dim 2 or 3, n[0] = Nx (fastest), n[1] = Ny, n[2] = Nz; unit box of
  *     side L with spacing h = L / N per axis; every axis periodic.  Supported
  *     axis lengths: 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 512, 1024,
- *     2048 (2048 only along x and y).
+ *     2048, and with a factor 5 (the grids of the paper's Section 5): 20,
+ *     40, 60, 120, 180, 240, 360, 480, 720, 960, 1440, 1920, 2400, 2880,
+ *     3600, 4800; z at most 1024.
  *   - Complex vectors are interleaved (re, im).  "c128" = two doubles, "c64" =
  *     two floats.  Several right-hand sides are stored one after another with
  *     stride n = Nx Ny Nz elements.
@@ -162,7 +164,8 @@ hz_status hz_set_allocator(void* (*alloc)(size_t bytes, void* ctx),
  * indexed [z][y][x].  c: wave speed (> 0); zeta: layer profile (>= 0, NULL =
  * no layer); a: operator damping of Eqn. 001 (NULL = 0).  The arrays are
  * copied; the call returns after the medium is ready.  Axis lengths: 8, 12,
- * 16, 24, 32, 48, 64, 96, 128, 192, 256, 512, 1024, 2048 (z <= 1024); fewer
+ * 16, 24, 32, 48, 64, 96, 128, 192, 256, 512, 1024, 2048 and the lengths with
+ * a factor 5 listed at the top of this file (z <= 1024); fewer
  * than 2^31 points.
  * With interp->Ma >= 2 or interp->basis == 1 the per-point record is up to
  * four (node, weight) pairs (52 bytes per point) instead of (segment, t).
@@ -327,7 +330,8 @@ hz_status hz_plan_hessenberg(const hz_plan* plan, int rhs, void* H, int* cols);
 /* ---- serving ----------------------------------------------------------
  * A server queues solve requests and admits them onto the GPU as slots and
  * device memory free up (admission by each request's device footprint
- * against hbm_budget, first fit in arrival order).  Each admitted request
+ * against hbm_budget, first fit in arrival order, with aging so that small
+ * requests cannot overtake a large one without bound).  Each admitted request
  * runs medium set-up, plan, (F)GMRES solve and read-back on its own
  * non-blocking stream and host worker, so the work of concurrent requests
  * overlaps on the device; allocations use the stream-ordered pool.  Every
@@ -339,6 +343,13 @@ typedef struct {
   int max_slots;       /* requests on the GPU at once (1..64)                            */
   int max_queue;       /* queued requests before hz_submit returns HZ_ERR_BUSY             */
   int device;          /* CUDA device the server uses                                      */
+  int autotune;        /* launch shapes of a served plan: 0 the autotuner's process cache
+                          entry for the request's grid, K, restart and precision (nearest
+                          right-hand-side count; no timing), defaults when there is none;
+                          1 the same, and hz_plan_autotune on a miss (once per key, on the
+                          request's stream); -1 the defaults                               */
+  int max_bypass;      /* aging: a queued request that later arrivals have been admitted
+                          ahead of this many times is not overtaken again; 0 = 2 max_slots */
 } hz_server_opts;
 
 typedef struct {

@@ -18,7 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhz.so")
-FFT_SIZES = (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 512, 1024, 2048)
+FFT_SIZES = (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 512, 1024, 2048,
+             20, 40, 60, 120, 180, 240, 360, 480, 720, 960, 1440, 1920, 2400, 2880, 3600, 4800)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

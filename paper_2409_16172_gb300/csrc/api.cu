@@ -84,6 +84,22 @@ const FftOps* fft_ops_256();
 const FftOps* fft_ops_512();
 const FftOps* fft_ops_1024();
 const FftOps* fft_ops_2048();
+const FftOps* fft_ops_20();
+const FftOps* fft_ops_40();
+const FftOps* fft_ops_60();
+const FftOps* fft_ops_120();
+const FftOps* fft_ops_180();
+const FftOps* fft_ops_240();
+const FftOps* fft_ops_360();
+const FftOps* fft_ops_480();
+const FftOps* fft_ops_720();
+const FftOps* fft_ops_960();
+const FftOps* fft_ops_1440();
+const FftOps* fft_ops_1920();
+const FftOps* fft_ops_2400();
+const FftOps* fft_ops_2880();
+const FftOps* fft_ops_3600();
+const FftOps* fft_ops_4800();
 
 const FftOps* fft_ops(int N) {
   switch (N) {
@@ -101,6 +117,22 @@ const FftOps* fft_ops(int N) {
     case 512: return fft_ops_512();
     case 1024: return fft_ops_1024();
     case 2048: return fft_ops_2048();
+    case 20: return fft_ops_20();
+    case 40: return fft_ops_40();
+    case 60: return fft_ops_60();
+    case 120: return fft_ops_120();
+    case 180: return fft_ops_180();
+    case 240: return fft_ops_240();
+    case 360: return fft_ops_360();
+    case 480: return fft_ops_480();
+    case 720: return fft_ops_720();
+    case 960: return fft_ops_960();
+    case 1440: return fft_ops_1440();
+    case 1920: return fft_ops_1920();
+    case 2400: return fft_ops_2400();
+    case 2880: return fft_ops_2880();
+    case 3600: return fft_ops_3600();
+    case 4800: return fft_ops_4800();
     default: return nullptr;
   }
 }

@@ -77,6 +77,29 @@ template <int S, typename V> __device__ __forceinline__ void dft3(V* x) {
   x[2] = csub(t, e);
 }
 
+// 5-point DFT from its definition, folded by the symmetry of the constants
+// c_m = cos(2 pi m / 5), s_m = sin(2 pi m / 5): with t1 = x1 + x4,
+// t2 = x2 + x3, t3 = x1 - x4, t4 = x2 - x3,
+//   X0     = x0 + t1 + t2
+//   X1, X4 = x0 + c1 t1 + c2 t2 +- S i (s1 t3 + s2 t4)
+//   X2, X3 = x0 + c2 t1 + c1 t2 +- S i (s2 t3 - s1 t4)
+template <int S, typename V> __device__ __forceinline__ void dft5(V* x) {
+  using R = decltype(V::x);
+  const R c1 = R(0.30901699437494742410), c2 = R(-0.80901699437494742410);
+  const R s1 = R(0.95105651629515357212), s2 = R(0.58778525229247312917);
+  const V t1 = cadd(x[1], x[4]), t2 = cadd(x[2], x[3]);
+  const V t3 = csub(x[1], x[4]), t4 = csub(x[2], x[3]);
+  const V a1 = cmk<V>(x[0].x + c1 * t1.x + c2 * t2.x, x[0].y + c1 * t1.y + c2 * t2.y);
+  const V a2 = cmk<V>(x[0].x + c2 * t1.x + c1 * t2.x, x[0].y + c2 * t1.y + c1 * t2.y);
+  const V b1 = cmul_si<S>(cmk<V>(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y));
+  const V b2 = cmul_si<S>(cmk<V>(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y));
+  x[0] = cadd(x[0], cadd(t1, t2));
+  x[1] = cadd(a1, b1);
+  x[4] = csub(a1, b1);
+  x[2] = cadd(a2, b2);
+  x[3] = csub(a2, b2);
+}
+
 template <int S, typename V> __device__ __forceinline__ void dft4(V* x) {
   V a = cadd(x[0], x[2]), b = csub(x[0], x[2]);
   V c = cadd(x[1], x[3]), d = cmul_si<S>(csub(x[1], x[3]));
@@ -363,11 +386,101 @@ template <int S> __device__ __forceinline__ PV w32mul(PV a, int k) {
   return cmul_const(a, -float(C[16 - k]), float(S) * float(C[k - 8]));
 }
 
+template <int S> __device__ __forceinline__ void dft5(PV* x) {
+  const f2 C1 = f2_splat(0.30901699437494742410f), C2 = f2_splat(-0.80901699437494742410f);
+  const f2 S1 = f2_splat(0.95105651629515357212f), S2 = f2_splat(0.58778525229247312917f);
+  const f2 NS1 = f2_splat(-0.95105651629515357212f);
+  const PV t1 = cadd(x[1], x[4]), t2 = cadd(x[2], x[3]);
+  const PV t3 = csub(x[1], x[4]), t4 = csub(x[2], x[3]);
+  PV a1, a2, u1, u2;
+  a1.x = fma2(t1.x, C1, fma2(t2.x, C2, x[0].x));
+  a1.y = fma2(t1.y, C1, fma2(t2.y, C2, x[0].y));
+  a2.x = fma2(t1.x, C2, fma2(t2.x, C1, x[0].x));
+  a2.y = fma2(t1.y, C2, fma2(t2.y, C1, x[0].y));
+  u1.x = fma2(t3.x, S1, t4.x * S2);
+  u1.y = fma2(t3.y, S1, t4.y * S2);
+  u2.x = fma2(t4.x, NS1, t3.x * S2);
+  u2.y = fma2(t4.y, NS1, t3.y * S2);
+  x[0] = cadd(x[0], cadd(t1, t2));
+  x[1] = cadd_si<S>(a1, u1);
+  x[4] = csub_si<S>(a1, u1);
+  x[2] = cadd_si<S>(a2, u2);
+  x[3] = csub_si<S>(a2, u2);
+}
+
+// cos and sin of 2 pi m / RR for the in-radix twiddles of the composite
+// radices below (RR = 6, 10, 12, 15, 20; 0 <= m < RR)
+__host__ __device__ constexpr double wr_cos(int RR, int m) {
+  return RR == 6    ? (m == 0 ? 1.0 : (m == 1 || m == 5) ? 0.5 : (m == 3 ? -1.0 : -0.5))
+         : RR == 10 ? (m == 0 ? 1.0 : m == 5 ? -1.0
+                       : (m == 1 || m == 9) ? 0.80901699437494742410
+                       : (m == 2 || m == 8) ? 0.30901699437494742410
+                       : (m == 3 || m == 7) ? -0.30901699437494742410 : -0.80901699437494742410)
+                    : 0.0;
+}
+__host__ __device__ constexpr double wr_sin(int RR, int m) {
+  return RR == 6    ? (m == 0 || m == 3 ? 0.0 : m < 3 ? 0.86602540378443864676 : -0.86602540378443864676)
+         : RR == 10 ? (m == 0 || m == 5 ? 0.0
+                       : (m == 1 || m == 4) ? 0.58778525229247312917
+                       : (m == 2 || m == 3) ? 0.95105651629515357212
+                       : (m == 6 || m == 9) ? -0.58778525229247312917 : -0.95105651629515357212)
+                    : 0.0;
+}
+// a * exp(S 2 pi i m / RR)
+template <int RR, int S, typename V> __device__ __forceinline__ V wrmul(V a, int m) {
+  using R = decltype(V::x);
+  m %= RR;
+  if (m == 0) return a;
+  if (4 * m == RR) return cmul_si<S>(a);
+  if (2 * m == RR) return cmk<V>(-a.x, -a.y);
+  if (4 * m == 3 * RR) return cmul_si<-S>(a);
+  return cmul(a, cmk<V>(R(wr_cos(RR, m)), R(S) * R(wr_sin(RR, m))));
+}
+template <int RR, int S> __device__ __forceinline__ PV wrmul(PV a, int m) {
+  m %= RR;
+  if (m == 0) return a;
+  if (4 * m == RR) return cmul_si<S>(a);
+  if (2 * m == RR) return cmk<PV>(neg2(a.x), neg2(a.y));
+  if (4 * m == 3 * RR) return cmul_si<-S>(a);
+  return cmul_const(a, float(wr_cos(RR, m)), float(S) * float(wr_sin(RR, m)));
+}
+
+template <int RAD, int S, typename V> __device__ __forceinline__ void dftR(V* x);
+
+// Composite radix R1 R2 by one Cooley-Tukey split: with n = n2 + R2 n1 and
+// k = k1 + R1 k2, X[k] = sum_n2 w_{R1R2}^{n2 k1} (sum_n1 x[n] w_{R1}^{n1 k1})
+// w_{R2}^{n2 k2}: R2 DFTs of length R1, the twiddles, then R1 of length R2.
+template <int R1, int R2, int S, typename V> __device__ __forceinline__ void dft_split(V* x) {
+  constexpr int RR = R1 * R2;
+  V y[RR];
+#pragma unroll
+  for (int n2 = 0; n2 < R2; ++n2) {
+    V t[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) t[n1] = x[n2 + R2 * n1];
+    dftR<R1, S>(t);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) y[n2 * R1 + k1] = wrmul<RR, S>(t[k1], n2 * k1);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    V t[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) t[n2] = y[n2 * R1 + k1];
+    dftR<R2, S>(t);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) x[k1 + R1 * k2] = t[k2];
+  }
+}
+
 template <int RAD, int S, typename V> __device__ __forceinline__ void dftR(V* x) {
   if constexpr (RAD == 2) dft2<S>(x);
   else if constexpr (RAD == 3) dft3<S>(x);
   else if constexpr (RAD == 4) dft4<S>(x);
+  else if constexpr (RAD == 5) dft5<S>(x);
+  else if constexpr (RAD == 6) dft_split<2, 3, S>(x);
   else if constexpr (RAD == 8) dft8<S>(x);
+  else if constexpr (RAD == 10) dft_split<2, 5, S>(x);
   else if constexpr (RAD == 16) dft16<S>(x);
   else if constexpr (RAD == 32) dft32<S>(x);
   else static_assert(RAD == 2, "unsupported radix");
@@ -399,6 +512,25 @@ HZ_PLAN(256, 16, 16, 16)
 HZ_PLAN(512, 8, 8, 8, 8)
 HZ_PLAN(1024, 16, 16, 16, 4)
 HZ_PLAN(2048, 16, 16, 16, 8)
+// Lengths with a factor 5 (the grids of the paper's Example 1 and Tables
+// 1-2): radices 10, 6 (and 2, 3) so that 30 elements per thread are a
+// multiple of every radix (10 for the lengths without a factor 3)
+HZ_PLAN(20, 10, 10, 2)
+HZ_PLAN(40, 10, 10, 2, 2)
+HZ_PLAN(60, 30, 10, 6)
+HZ_PLAN(120, 30, 10, 6, 2)
+HZ_PLAN(180, 30, 10, 6, 3)
+HZ_PLAN(240, 30, 10, 6, 2, 2)
+HZ_PLAN(360, 30, 10, 6, 6)
+HZ_PLAN(480, 30, 10, 6, 2, 2, 2)
+HZ_PLAN(720, 30, 10, 6, 6, 2)
+HZ_PLAN(960, 30, 10, 6, 2, 2, 2, 2)
+HZ_PLAN(1440, 30, 10, 6, 6, 2, 2)
+HZ_PLAN(1920, 30, 10, 6, 2, 2, 2, 2, 2)
+HZ_PLAN(2400, 30, 10, 10, 6, 2, 2)
+HZ_PLAN(2880, 30, 10, 6, 6, 2, 2, 2)
+HZ_PLAN(3600, 30, 10, 10, 6, 6)
+HZ_PLAN(4800, 30, 10, 10, 6, 2, 2, 2)
 
 // Row plans (contiguous lines, complex64): 32 threads per line for N = 512
 // and 1024 so that a line is one warp and its stage barriers are warp

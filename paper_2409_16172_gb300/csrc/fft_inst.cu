@@ -111,7 +111,11 @@ hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segta
   }
   // fewer blocks of ROW_LINES rows than SMs: few rows
   const bool small = (nrows + C::ROW_LINES - 1) / C::ROW_LINES < 152L;
-  if (mode == 1 || (mode == 0 && small)) {
+  // the fused pass holds three E-element arrays per thread; complex128 with
+  // 30 elements per thread (lengths with a factor 5) would spill, so those
+  // take the in-place pass and the gather
+  constexpr bool fused_ok = !(sizeof(R) == 8 && C::RP::E > 16);
+  if (mode == 1 || (mode == 0 && small) || !fused_ok) {
     // few rows: (row, node) lines in parallel, in place, then the gather
     auto ki = row_inv_inplace_kernel<R, N, C::ROW_LINES>;
     HZ_TRY(smem_attr(ki, C::row_smem()));
@@ -129,16 +133,18 @@ hz_status row_inv_acc_t(const void* planes, const void* rec, const uchar2* segta
     count_launches(1);  // the phase counts one
     return HZ_OK;
   }
-  constexpr int lines = C::ROW_LINES;
-  auto k = row_inv_acc_kernel<R, N, OutT, C::ROW_LINES>;
-  HZ_TRY(smem_attr(k, C::row_acc_smem(lines)));
-  const long blocks = (nrows + lines - 1) / lines;
-  HZ_CUDA(launch_pdl(k, dim3(unsigned(blocks)), dim3(lines * C::TPL_ROW), C::row_acc_smem(lines),
-                     st, static_cast<const V*>(planes),
-                     static_cast<const typename RecT<R>::T*>(rec), segtab, nseg, rowmask, K,
-                     rows_per_rhs, nrows, n, R(inv_n), static_cast<const V*>(tw),
-                     static_cast<OutT*>(out), active));
-  HZ_CUDA(cudaGetLastError());
+  if constexpr (fused_ok) {
+    constexpr int lines = C::ROW_LINES;
+    auto k = row_inv_acc_kernel<R, N, OutT, C::ROW_LINES>;
+    HZ_TRY(smem_attr(k, C::row_acc_smem(lines)));
+    const long blocks = (nrows + lines - 1) / lines;
+    HZ_CUDA(launch_pdl(k, dim3(unsigned(blocks)), dim3(lines * C::TPL_ROW), C::row_acc_smem(lines),
+                       st, static_cast<const V*>(planes),
+                       static_cast<const typename RecT<R>::T*>(rec), segtab, nseg, rowmask, K,
+                       rows_per_rhs, nrows, n, R(inv_n), static_cast<const V*>(tw),
+                       static_cast<OutT*>(out), active));
+    HZ_CUDA(cudaGetLastError());
+  }
   return HZ_OK;
 }
 

@@ -43,10 +43,12 @@ template <typename R, int N> struct LineCfg {
   static constexpr int TPL = N / CP::E;
   using RP = typename RowPlan<R, N>::P;           // row kernels
   static constexpr int TPL_ROW = N / RP::E;
-  static constexpr int ROW_THREADS = TPL_ROW > 128 ? TPL_ROW : 128;
-  static constexpr int ROW_LINES = ROW_THREADS / TPL_ROW;
-  // row kernels: a line's threads sit in one warp -> warp barriers
-  static constexpr bool WS = TPL_ROW <= 32;
+  // whole lines per block: about 128 threads, at least one line
+  static constexpr int ROW_LINES = TPL_ROW >= 128 ? 1 : 128 / TPL_ROW;
+  static constexpr int ROW_THREADS = ROW_LINES * TPL_ROW;
+  // row kernels: a line's threads sit in one warp (TPL_ROW divides 32, so
+  // no line straddles two warps) -> warp barriers
+  static constexpr bool WS = TPL_ROW <= 32 && 32 % TPL_ROW == 0;
   static constexpr int VB = int(2 * sizeof(R));
   static constexpr int tb_calc() {
     int tb = 32 / VB;                 // one 32-byte sector per row at least

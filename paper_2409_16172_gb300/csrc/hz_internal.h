@@ -256,6 +256,12 @@ struct Tune {
 };
 }
 
+namespace hz {
+// Sets plan->tune from the autotuner's process cache (no timing); false
+// when no entry of the same grid, K, restart and precision exists.
+bool tune_from_cache(hz_plan* plan);
+}
+
 struct hz_plan {
   hz_medium* med = nullptr;
   hz_solver_opts opts{};

@@ -333,6 +333,8 @@ bool fft_size_supported(int N) {
   switch (N) {
     case 8: case 12: case 16: case 24: case 32: case 48: case 64: case 96: case 128:
     case 192: case 256: case 512: case 1024: case 2048:
+    case 20: case 40: case 60: case 120: case 180: case 240: case 360: case 480: case 720:
+    case 960: case 1440: case 1920: case 2400: case 2880: case 3600: case 4800:
       return true;
     default:
       return false;

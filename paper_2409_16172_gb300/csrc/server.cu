@@ -42,6 +42,7 @@ struct Req {
   std::string error;
   size_t footprint = 0;
   Clock::time_point t_submit, t_start, t_done;
+  int bypassed = 0;  // later arrivals admitted ahead of this request
   bool done = false;
 };
 
@@ -104,6 +105,10 @@ void run_request(hz_server* s, Req& r, cudaStream_t st) {
   hz_status rc = hz_create_medium(&r.grid, r.c.data(), r.zeta.empty() ? nullptr : r.zeta.data(),
                                   r.a.empty() ? nullptr : r.a.data(), r.omega, &r.interp, &med);
   if (rc == HZ_OK) rc = hz_plan_create(med, &r.opts, r.nrhs, &plan);
+  // launch shapes: the autotuner's cached choice for this grid, K, restart
+  // and precision (timing once per key on a miss when opts.autotune == 1)
+  if (rc == HZ_OK && s->opts.autotune >= 0 && !hz::tune_from_cache(plan) && s->opts.autotune == 1)
+    rc = hz_plan_autotune(plan, st, nullptr);
   if (rc == HZ_OK) {
     const size_t vb = size_t(r.nrhs) * r.n * sizeof(double2);
     cudaError_t ce = cudaMemcpyAsync(plan->f, r.f.data(), vb, cudaMemcpyHostToDevice, st);
@@ -124,7 +129,6 @@ void run_request(hz_server* s, Req& r, cudaStream_t st) {
   if (med) hz_destroy_medium(med);
   cudaStreamSynchronize(st);
   r.status = rc;
-  (void)s;
 }
 
 void worker_main(hz_server* s) {
@@ -145,15 +149,24 @@ void worker_main(hz_server* s) {
           if (st) cudaStreamDestroy(st);
           return;
         }
-        // first fit in arrival order within the HBM budget
-        for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
-          if (s->in_use + (*it)->footprint <= s->opts.hbm_budget || s->active == 0) {
-            r = *it;
-            s->queue.erase(it);
+        // first fit in arrival order within the HBM budget, with aging: a
+        // request that later arrivals have overtaken max_bypass times is
+        // not overtaken again (admission waits until it fits)
+        size_t pick = s->queue.size();
+        for (size_t i = 0; i < s->queue.size(); ++i) {
+          const Req& q = *s->queue[i];
+          if (s->in_use + q.footprint <= s->opts.hbm_budget || s->active == 0) {
+            pick = i;
             break;
           }
+          if (q.bypassed >= s->opts.max_bypass) break;
         }
-        if (r) break;
+        if (pick < s->queue.size()) {
+          for (size_t i = 0; i < pick; ++i) ++s->queue[i]->bypassed;
+          r = s->queue[pick];
+          s->queue.erase(s->queue.begin() + long(pick));
+          break;
+        }
         s->cv_work.wait(lk);
       }
       s->in_use += r->footprint;
@@ -203,8 +216,11 @@ extern "C" hz_status hz_server_create(const hz_server_opts* opts, hz_server** ou
   *out = nullptr;
   if (opts->max_slots < 1 || opts->max_slots > 64 || opts->max_queue < 1)
     return set_error(HZ_ERR_INVALID_ARG, "need 1 <= max_slots <= 64 and max_queue >= 1");
+  if (opts->autotune < -1 || opts->autotune > 1 || opts->max_bypass < 0)
+    return set_error(HZ_ERR_INVALID_ARG, "need autotune in {-1, 0, 1} and max_bypass >= 0");
   hz_server* s = new hz_server();
   s->opts = *opts;
+  if (s->opts.max_bypass == 0) s->opts.max_bypass = 2 * s->opts.max_slots;
   s->device = opts->device;
   HZ_CUDA(cudaSetDevice(s->device));
   if (s->opts.hbm_budget == 0) {

@@ -12,6 +12,7 @@
 // Timing uses CUDA events on the caller's stream around 3 repetitions of
 // each candidate at the middle Arnoldi step of a cycle.
 #include <algorithm>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -66,6 +67,36 @@ struct Timer {
 };
 
 }  // namespace
+
+// Launch shapes from the process cache without timing: the entry of the
+// plan's own key, else the entry of the same grid, K, restart and precision
+// whose right-hand-side count is nearest.  The scattering x-inverse is not
+// taken for media with per-point (node, weight) records (with three or more
+// additions per point its result would depend on their order).
+bool hz::tune_from_cache(hz_plan* plan) {
+  const Key key = key_of(plan);
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_cache.find(key);
+  if (it == g_cache.end()) {
+    int best_d = 1 << 30;
+    for (auto jt = g_cache.begin(); jt != g_cache.end(); ++jt) {
+      const Key& k = jt->first;
+      if (std::get<0>(k) != std::get<0>(key) || std::get<1>(k) != std::get<1>(key) ||
+          std::get<2>(k) != std::get<2>(key) || std::get<3>(k) != std::get<3>(key) ||
+          std::get<5>(k) != std::get<5>(key) || std::get<6>(k) != std::get<6>(key))
+        continue;
+      const int d = std::abs(std::get<4>(k) - std::get<4>(key));
+      if (d < best_d) {
+        best_d = d;
+        it = jt;
+      }
+    }
+  }
+  if (it == g_cache.end()) return false;
+  plan->tune = it->second;
+  if (plan->med->generic && plan->tune.rowinv_mode == 3) plan->tune.rowinv_mode = 1;
+  return true;
+}
 
 extern "C" hz_status hz_plan_set_tune(hz_plan* plan, const hz_tune_report* r) {
   if (!plan || !r) return set_error(HZ_ERR_INVALID_ARG, "null argument");

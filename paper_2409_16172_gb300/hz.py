@@ -76,7 +76,7 @@ class hz_tune_report(C.Structure):
 
 class hz_server_opts(C.Structure):
     _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int), ("max_queue", C.c_int),
-                ("device", C.c_int)]
+                ("device", C.c_int), ("autotune", C.c_int), ("max_bypass", C.c_int)]
 
 
 class hz_request(C.Structure):
@@ -398,8 +398,8 @@ class Server:
     """Continuous-batching solve server (hz_server_* in the C ABI)."""
 
     def __init__(self, max_slots: int = 4, max_queue: int = 4096, hbm_budget: int = 0,
-                 device: int = 0):
-        o = hz_server_opts(hbm_budget, max_slots, max_queue, device)
+                 device: int = 0, autotune: int = 0, max_bypass: int = 0):
+        o = hz_server_opts(hbm_budget, max_slots, max_queue, device, autotune, max_bypass)
         h = _vp()
         check(lib.hz_server_create(C.byref(o), C.byref(h)))
         self._h = h

@@ -207,7 +207,7 @@ def test_edge_cases(hz):
         hz.Medium(bad, p.zeta, omega=p.omega, M=4, Mt=2)
     assert e.value.status == 8
     with pytest.raises(hz.HzError) as e:
-        hz.Medium(np.ones((20, 16)), omega=3.0, M=2)
+        hz.Medium(np.ones((22, 16)), omega=3.0, M=2)
     assert e.value.status == 1
     with pytest.raises(hz.HzError):
         plan.apply_operator(_dev(np.zeros((2, 16, 16), complex)))  # nrhs > max_nrhs

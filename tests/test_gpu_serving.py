@@ -110,7 +110,7 @@ def test_queue_limit_and_bad_request(hz):
     assert refused >= 2
     srv.result(t0)
     with pytest.raises(hz.HzError) as e:
-        srv.submit(np.ones((20, 16)), np.zeros((1, 20, 16), complex), omega=3.0, M=2)
+        srv.submit(np.ones((22, 16)), np.zeros((1, 22, 16), complex), omega=3.0, M=2)
     assert e.value.status == 1
     srv.close()
 

@@ -112,7 +112,15 @@ typedef struct {
  *              much as the kernels); 0: launch step by step.
  *   no_precond 1: plain GMRES(m) on P_N u = f without the preconditioner,
  *              all in FP64 (the unpreconditioned baseline the paper compares
- *              against in Section 5); 0: preconditioned by Q_M.         */
+ *              against in Section 5); 0: preconditioned by Q_M.
+ *   left       1: the paper's left preconditioning (Eqn. MainDiscretePrecond):
+ *              GMRES(m) on Q_M P_N u = Q_M f, each Arnoldi vector
+ *              Q_M (P_N v) (the stencil in FP64, Q_M in the precision
+ *              above), u += V y, and the stopping test (and the history) on
+ *              the preconditioned residual ||Q_M (f - P_N u)|| / ||Q_M f||,
+ *              as the paper's GMRES runs report it; hz_solve_stats still
+ *              reports the true residual.  0: right / flexible (default).
+ *              Ignored with no_precond.                                 */
 typedef struct {
   int precision;
   int restart;
@@ -120,6 +128,7 @@ typedef struct {
   int maxit;
   int graphs;
   int no_precond;
+  int left;
 } hz_solver_opts;
 
 typedef struct {

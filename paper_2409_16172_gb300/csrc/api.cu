@@ -266,6 +266,7 @@ extern "C" hz_status hz_plan_create(hz_medium* med, const hz_solver_opts* opts, 
     return set_error(HZ_ERR_INVALID_ARG, "precision must be 0 or 1");
   if (opts->no_precond != 0 && opts->no_precond != 1)
     return set_error(HZ_ERR_INVALID_ARG, "no_precond must be 0 or 1");
+  if (opts->left != 0 && opts->left != 1) return set_error(HZ_ERR_INVALID_ARG, "left must be 0 or 1");
   if (opts->restart < 1 || opts->restart > HZ_MAX_RESTART)
     return set_error(HZ_ERR_INVALID_ARG, "restart must be in [1, %d]", HZ_MAX_RESTART);
   if (!(opts->tol > 0) || opts->maxit < 1) return set_error(HZ_ERR_INVALID_ARG, "need tol > 0, maxit >= 1");

@@ -161,6 +161,20 @@ hz_status gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs, hz_
   HZ_CUDA(cudaMemcpyAsync(bnorm.data(), ks.bnorm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
   HZ_CUDA(cudaStreamSynchronize(st));
   for (auto& b : bnorm) b = std::sqrt(b);
+  const std::vector<double> fnorm = bnorm;  // ||f||
+  // The paper's left form (Eqn. MainDiscretePrecond): GMRES on Q_M P_N u =
+  // Q_M f; residuals are measured after Q_M, relative to ||Q_M f||.
+  const bool left = p->opts.left != 0 && p->opts.no_precond == 0;
+  if (left) {
+    HZ_TRY(precond_apply(p, prec, f, nullptr, nrhs, p->V, 1, st, nullptr));
+    {
+      PhaseScope ps(st, PH_NORM, 16.0 * Bn, 4.0 * Bn, 2);
+      HZ_TRY(launch_norm2(p->V, n, n, nrhs, p->partial, nblk_n, ks.bnorm, st));
+    }
+    HZ_CUDA(cudaMemcpyAsync(bnorm.data(), ks.bnorm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HZ_CUDA(cudaStreamSynchronize(st));
+    for (int b = 0; b < nrhs; ++b) bnorm[b] = fnorm[b] == 0.0 ? 0.0 : std::sqrt(bnorm[b]);
+  }
   HZ_CUDA(cudaMemcpyAsync(ks.bnorm, bnorm.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
 
   std::vector<int> done(nrhs, 0), conv(nrhs, 0), iters(nrhs, 0), restarts(nrhs, 0),
@@ -187,6 +201,12 @@ hz_status gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs, hz_
       PhaseScope ps(st, PH_RESID, 64.0 * Bn + (med->a ? 8.0 * Bn : 0.0), 30.0 * Bn, 2);
       HZ_TRY(launch_residual(med, u, f, p->V, n, nrhs, nullptr, p->partial, st));
       HZ_TRY(launch_reduce_r(p->partial, nblk_r, nrhs, w.rnorm2, st));
+    }
+    if (left) {
+      // r <- Q_M r in place, and its norm
+      HZ_TRY(precond_apply(p, prec, p->V, nullptr, nrhs, p->V, 1, st, nullptr));
+      PhaseScope ps(st, PH_NORM, 16.0 * Bn, 4.0 * Bn, 2);
+      HZ_TRY(launch_norm2(p->V, n, n, nrhs, p->partial, nblk_n, w.rnorm2, st));
     }
     HZ_CUDA(cudaMemcpyAsync(rn2.data(), w.rnorm2, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
     HZ_CUDA(cudaStreamSynchronize(st));
@@ -245,6 +265,14 @@ hz_status gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs, hz_
         }
         PhaseScope ps(st, PH_STENCIL, stb, stf);
         HZ_TRY(launch_stencil(med, 0, zt, n, Vn, n, nrhs, ks.active, st));
+      } else if (left) {
+        // left: v_{j+1} = Q_M (P_N (sigma_j V_j)); the FP64 stencil writes
+        // P_N V_j, the preconditioner scales it by sigma_j and works in place
+        {
+          PhaseScope ps(st, PH_STENCIL, Bn * (16.0 + 32.0 + (med->a ? 8.0 : 0.0)), stf);
+          HZ_TRY(launch_stencil(med, 0, Vj, n, Vn, n, nrhs, ks.active, st));
+        }
+        HZ_TRY(precond_apply(p, prec, Vn, sig_j, nrhs, Vn, 1, st, ks.active));
       } else if (prec == 1) {
         float2* Zj = static_cast<float2*>(p->Z) + long(j) * ldb * n;
         HZ_TRY(precond_apply(p, 1, Vj, sig_j, nrhs, Zj, 0, st, ks.active));
@@ -368,10 +396,10 @@ hz_status gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs, hz_
     HZ_CUDA(cudaMemcpyAsync(d_jn, jn.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
     HZ_CUDA(cudaMemcpyAsync(w.y, h_y.data(), size_t(nrhs) * m * sizeof(double2), cudaMemcpyHostToDevice, st));
     const int Jmax = *std::max_element(jn.begin(), jn.end());
-    if (prec == 1 && !noq) {
+    if (prec == 1 && !noq && !left) {
       PhaseScope ps(st, PH_SOLUPD, Bn * (8.0 * Jmax + 32.0), Bn * 8.0 * Jmax);
       HZ_TRY(launch_solution_update(1, p->Z, ldb, u, n, n, nrhs, w.y, m, d_jn, st));
-    } else if (noq) {
+    } else if (noq || left) {
       // u += V (sigma y)
       double2* t = p->V + long(m) * ldb * n;
       PhaseScope ps(st, PH_SOLUPD, Bn * (16.0 * Jmax + 64.0), Bn * (8.0 * Jmax + 2.0));
@@ -392,6 +420,18 @@ hz_status gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs, hz_
     HZ_CUDA(cudaStreamSynchronize(st));
   }
 
+  // the left form stopped on the preconditioned residual; report the true one
+  std::vector<double> rel_true = rel;
+  if (left) {
+    {
+      PhaseScope ps(st, PH_RESID, 64.0 * Bn + (med->a ? 8.0 * Bn : 0.0), 30.0 * Bn, 2);
+      HZ_TRY(launch_residual(med, u, f, p->V, n, nrhs, nullptr, p->partial, st));
+      HZ_TRY(launch_reduce_r(p->partial, nblk_r, nrhs, w.rnorm2, st));
+    }
+    HZ_CUDA(cudaMemcpyAsync(rn2.data(), w.rnorm2, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HZ_CUDA(cudaStreamSynchronize(st));
+    for (int b = 0; b < nrhs; ++b) rel_true[b] = fnorm[b] == 0.0 ? 0.0 : std::sqrt(rn2[b]) / fnorm[b];
+  }
   if (!u_dev) HZ_CUDA(cudaMemcpyAsync(u_io, p->u, vbytes, cudaMemcpyDeviceToHost, st));
   HZ_CUDA(cudaEventRecord(w.t1, st));
   HZ_CUDA(cudaEventSynchronize(w.t1));
@@ -412,7 +452,7 @@ hz_status gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs, hz_
       stats[b].restarts = restarts[b];
       stats[b].status = conv[b] ? HZ_OK : (status[b] == HZ_OK ? HZ_ERR_NOT_CONVERGED : status[b]);
       stats[b].converged = conv[b];
-      stats[b].rel_true_resid = rel[b];
+      stats[b].rel_true_resid = rel_true[b];
       stats[b].rel_est_resid = est[b];
       stats[b].ms_total = ms;
       stats[b].ms_precond = ms_pre;

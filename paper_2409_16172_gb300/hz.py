@@ -47,7 +47,8 @@ class hz_interp(C.Structure):
 
 class hz_solver_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("restart", C.c_int), ("tol", C.c_double),
-                ("maxit", C.c_int), ("graphs", C.c_int), ("no_precond", C.c_int)]
+                ("maxit", C.c_int), ("graphs", C.c_int), ("no_precond", C.c_int),
+                ("left", C.c_int)]
 
 
 class hz_solve_stats(C.Structure):
@@ -262,11 +263,11 @@ class Plan:
 
     def __init__(self, medium: Medium, *, precision: int = 1, restart: int = 40,
                  tol: float = 1e-6, maxit: int = 4000, max_nrhs: int = 1, graphs: bool = False,
-                 no_precond: bool = False):
+                 no_precond: bool = False, left: bool = False):
         self.medium = medium
         self.max_nrhs = max_nrhs
         self.opts = hz_solver_opts(precision, restart, tol, maxit, 1 if graphs else 0,
-                                   1 if no_precond else 0)
+                                   1 if no_precond else 0, 1 if left else 0)
         h = _vp()
         check(lib.hz_plan_create(medium.handle, C.byref(self.opts), max_nrhs, C.byref(h)))
         self._h = h
@@ -390,7 +391,7 @@ def request_footprint(shape, M, Mt, precision=1, restart=40, nrhs=1, has_a=False
                       basis=0) -> int:
     g = _grid_of(tuple(shape))
     it = hz_interp(M, Mt, 1.0, 0.0, 0.15, 0.0, 0, Ma, basis)
-    o = hz_solver_opts(precision, restart, 1e-6, 4000, 0, 0)
+    o = hz_solver_opts(precision, restart, 1e-6, 4000, 0, 0, 0)
     return int(lib.hz_request_footprint(C.byref(g), C.byref(it), C.byref(o), nrhs, 1 if has_a else 0))
 
 
@@ -423,7 +424,7 @@ class Server:
         r.a = _dptr(a)
         r.omega = omega
         r.interp = hz_interp(M, Mt, c_o, zeta_max, alpha, a_node, symbol_kind, Ma, basis)
-        r.opts = hz_solver_opts(precision, restart, tol, maxit, 1 if graphs else 0, 0)
+        r.opts = hz_solver_opts(precision, restart, tol, maxit, 1 if graphs else 0, 0, 0)
         r.nrhs = nrhs
         r.f = _vp(f.ctypes.data)
         t = C.c_uint64()

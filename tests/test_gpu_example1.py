@@ -58,6 +58,34 @@ def test_residual_history_matches_oracle(hz, no_precond):
         assert abs(np.log10(r_gpu / so["rel_true_resid"])) <= 0.2
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_left_preconditioned_history_matches_oracle(hz, prec):
+    """The paper's left form (Eqn. MainDiscretePrecond, opts.left): GMRES(10)
+    on Q_M P_N u = Q_M f, whose history is the preconditioned residual
+    ||Q_M (f - P_N u)|| / ||Q_M f||, against the oracle's left GMRES step by
+    step (FP64 preconditioner: the first three cycles to 1e-6; complex64:
+    the first cycle to the complex64 apply's accuracy); the reported true
+    residual is ||f - P_N u|| / ||f|| of the returned iterate."""
+    p = S.example1(128)
+    med_o, med_g = _media(hz, p)
+    plan = hz.Plan(med_g, precision=prec, restart=10, tol=1e-14, maxit=60, left=True)
+    u, st, H = plan.solve(np.ascontiguousarray(p.f[0]), history=60)
+    h = H[0]
+    assert st[0]["iters"] == 60
+    A = lambda x: O.apply_operator(med_o, x)
+    Q = lambda v: O.apply_preconditioner(med_o, v)
+    _, so = O.gmres(A, p.f[0], Q, restart=10, tol=1e-14, maxit=60, side="left",
+                    record_history=True)
+    ho = np.asarray(so["history"])
+    if prec == 0:
+        np.testing.assert_allclose(h[:30], ho[:30], rtol=1e-6)
+    else:
+        np.testing.assert_allclose(h[:10], ho[:10], rtol=1e-4)
+    assert np.all(np.abs(np.log10(h[:60] / ho)) <= 0.3)
+    r_true = np.linalg.norm(p.f[0] - A(u)) / np.linalg.norm(p.f[0])
+    assert abs(st[0]["rel_true_resid"] / r_true - 1) <= 1e-8
+
+
 def test_preconditioning_gap_and_mixed_precision(hz):
     """Preconditioned GMRES(10) ends 100 iterations orders of magnitude below
     the unpreconditioned run; the complex64 preconditioner inside FGMRES

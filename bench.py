@@ -801,63 +801,136 @@ def run_spectrum(args):
 
 
 def run_serving(args):
-    """Serving stream: requests drawn from the serving recipe arrive with
-    seeded exponential gaps; the server admits them by HBM footprint."""
+    """Serving stream: requests drawn from the serving recipe (each request
+    seeded by its index) arrive with seeded exponential gaps; the server
+    admits them by HBM footprint.  Requests are generated by producer
+    threads ahead of their arrival times (a stream of 2000 does not fit in
+    host memory at once) and only their stats are kept.  Before the stream,
+    one plan per (grid, K) of the stream is autotuned (untimed, reported);
+    served plans take those launch shapes from the process cache.  The plain
+    FP64 path serves the first --plain-requests requests one at a time with
+    the same arrival times, and the mixed-precision server serves the same
+    subset, for the comparison."""
+    import concurrent.futures as cf
+    import queue
     import torch
     from paper_2409_16172_gb300 import build, synth as S
     build.build()
     from paper_2409_16172_gb300 import hz
     torch.cuda.set_device(0)
-    rng = np.random.Generator(np.random.PCG64(16177))
-    reqs = [S.serving_request(rng) for _ in range(args.requests)]
-    gaps = rng.exponential(1.0 / args.rate, size=len(reqs))
-    srv = hz.Server(max_slots=args.slots)
-    # warm-up: one small request of each dimension
-    for q in reqs[:2]:
+
+    def request(i):
+        return S.serving_request(np.random.Generator(np.random.PCG64([16177, i])))
+
+    gaps = np.random.Generator(np.random.PCG64(16178)).exponential(1.0 / args.rate,
+                                                                    size=args.requests)
+    graphs_for = (lambda q: True) if args.serve_graphs == "all" else (lambda q: q.n <= 256 * 256)
+    # pre-tuning: one plan per (grid, K) seen in the first requests of the stream
+    t_tune = time.perf_counter()
+    keys = {}
+    for i in range(min(args.requests, 200)):
+        q = request(i) if len(keys) < 21 else None
+        if q is None:
+            break
+        keys.setdefault((q.shape, q.M, q.Mt), q)
+    if not args.no_pretune:
+        for (shape, M, Mt), q in sorted(keys.items(), key=lambda kv: str(kv[0])):
+            med = hz.Medium(q.c, q.zeta, omega=q.omega, M=M, Mt=Mt, alpha=0.15)
+            plan = hz.Plan(med, precision=1, restart=q.restart, tol=q.tol, max_nrhs=4)
+            plan.autotune()
+            del plan, med
+    t_tune = time.perf_counter() - t_tune
+
+    def run_stream(nreq, slots, precision):
+        srv = hz.Server(max_slots=slots, autotune=0 if not args.no_pretune else -1)
+        out_q = queue.Queue()
+        stats = []
+        pool = cf.ThreadPoolExecutor(max_workers=args.gen_threads)
+        futs = {}
+        ahead = 2 * args.gen_threads
+
+        def collect():
+            while True:
+                item = out_q.get()
+                if item is None:
+                    return
+                t, nr = item
+                done, u, st, status = srv.result(t, timeout=7200)
+                stats.append((done and status == 0 and all(x["converged"] for x in st), nr,
+                              max(x["iters"] for x in st)))
+                del u
+
+        col = threading.Thread(target=collect, daemon=True)
+        col.start()
+        for i in range(min(ahead, nreq)):
+            futs[i] = pool.submit(request, i)
+        t0 = time.perf_counter()
+        t_next = t0
+        late = 0.0
+        for i in range(nreq):
+            q = futs.pop(i).result()
+            if i + ahead < nreq:
+                futs[i + ahead] = pool.submit(request, i + ahead)
+            t_next += gaps[i]
+            dt = t_next - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            else:
+                late = max(late, -dt)
+            t = srv.submit(q.c, q.f, omega=q.omega, M=q.M, Mt=q.Mt, zeta=q.zeta, alpha=0.15,
+                           restart=q.restart, tol=q.tol, precision=precision, graphs=graphs_for(q))
+            out_q.put((t, q.f.shape[0]))
+            del q
+        out_q.put(None)
+        col.join()
+        span = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        pool.shutdown()
+        return span, st, stats, late
+
+    # warm-up: two requests through a server (module loading, pools)
+    srv = hz.Server(max_slots=2)
+    for i in range(2):
+        q = request(i)
         srv.result(srv.submit(q.c, q.f, omega=q.omega, M=q.M, Mt=q.Mt, zeta=q.zeta, alpha=0.15,
                               restart=q.restart, tol=q.tol), timeout=600)
     srv.close()
 
-    def run_stream(slots, precision):
-        srv = hz.Server(max_slots=slots)
-        t0 = time.perf_counter()
-        tickets = []
-        for q, g in zip(reqs, gaps):
-            time.sleep(g)
-            tickets.append(srv.submit(q.c, q.f, omega=q.omega, M=q.M, Mt=q.Mt, zeta=q.zeta,
-                                      alpha=0.15, restart=q.restart, tol=q.tol,
-                                      precision=precision, graphs=q.n <= 256 * 256))
-        res = [srv.result(t, timeout=3600) for t in tickets]
-        span = time.perf_counter() - t0
-        st = srv.stats()
-        srv.close()
-        return span, st, res
-
     sampler = ClockSampler(0)
     sampler.start()
-    span, st, res = run_stream(args.slots, 1)
+    span, st, stats, late = run_stream(args.requests, args.slots, 1)
     clocks = sampler.stop()
-    rhs = sum(q.f.shape[0] for q in reqs)
-    ok = all(r[0] and r[3] == 0 for r in res)
+    rhs = sum(x[1] for x in stats)
+    ok = all(x[0] for x in stats)
     plain = None
-    if not args.no_plain:
-        # the same arrival stream served by the plain FP64 path one request
-        # at a time
-        span0, st0, res0 = run_stream(1, 0)
-        plain = {"value": rhs / span0, "unit": "solves/s", "p50_ms": st0["p50_ms"],
-                 "p99_ms": st0["p99_ms"], "mean_ms": st0["mean_ms"], "span_s": span0,
-                 "all_converged": all(r[0] and r[3] == 0 for r in res0),
+    if args.plain_requests > 0:
+        nsub = min(args.plain_requests, args.requests)
+        span_m, st_m, stats_m, _ = run_stream(nsub, args.slots, 1)
+        span0, st0, stats0, late0 = run_stream(nsub, 1, 0)
+        rhs_sub = sum(x[1] for x in stats0)
+        plain = {"requests": nsub,
+                 "mixed": {"value": rhs_sub / span_m, "p50_ms": st_m["p50_ms"],
+                           "p99_ms": st_m["p99_ms"], "span_s": span_m},
+                 "plain_fp64": {"value": rhs_sub / span0, "unit": "solves/s",
+                                "p50_ms": st0["p50_ms"], "p99_ms": st0["p99_ms"],
+                                "mean_ms": st0["mean_ms"], "span_s": span0,
+                                "all_converged": all(x[0] for x in stats0),
+                                "generation_late_s": late0},
                  "path": "precision 0 (complex128 preconditioner, FP64 GMRES), one request "
-                         "on the GPU at a time, same requests and arrival times"}
+                         "on the GPU at a time, same requests and arrival times; 'mixed' is "
+                         "the mixed-precision server on the same subset"}
     out = {"metric": METRIC + " (serving stream)", "value": rhs / span, "unit": "solves/s",
-           "n_gpus": 1, "steps": len(reqs), "warmup": 2, "ms_per_step": 1e3 * span / len(reqs),
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32+f64", "data": "synthetic",
-           "config": {"workload": f"serving-{len(reqs)}req-poisson{args.rate}/s-slots{args.slots}",
-                      "grids": sorted({"x".join(map(str, q.shape)) for q in reqs}),
-                      "rhs_total": rhs},
+           "n_gpus": 1, "steps": args.requests, "warmup": 2,
+           "ms_per_step": 1e3 * span / args.requests, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": f"serving-{args.requests}req-poisson{args.rate}/s-slots{args.slots}",
+                      "grids": sorted({"x".join(map(str, k[0])) for k in keys}),
+                      "rhs_total": rhs, "graphs": args.serve_graphs,
+                      "pretune_s": t_tune, "pretuned_keys": 0 if args.no_pretune else len(keys)},
            "latency": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"]},
-           "server": st, "all_converged": ok, "clocks": clocks, "fp64_plain": plain}
+           "server": st, "all_converged": ok, "generation_late_s": late,
+           "iters_max": max(x[2] for x in stats), "clocks": clocks, "fp64_plain": plain}
     print(json.dumps(out), flush=True)
 
 
@@ -881,6 +954,14 @@ def main():
     ap.add_argument("--int-n", type=int, default=1024, help="interp: grid side N")
     ap.add_argument("--rate", type=float, default=4.0, help="serving: arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent requests")
+    ap.add_argument("--serve-graphs", choices=["all", "small"], default="all",
+                    help="serving: captured cycle graphs for every request or only <= 256^2")
+    ap.add_argument("--no-pretune", action="store_true",
+                    help="serving: no autotuning before the stream (served plans keep defaults)")
+    ap.add_argument("--plain-requests", type=int, default=30,
+                    help="serving: requests of the plain FP64 one-at-a-time comparison (0: none)")
+    ap.add_argument("--gen-threads", type=int, default=6,
+                    help="serving: producer threads generating requests ahead of arrival")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target oracle time of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -819,7 +819,11 @@ def run_serving(args):
     from paper_2409_16172_gb300 import hz
     torch.cuda.set_device(0)
 
+    pool = S.shared_media_pool(args.media_pool) if args.media_pool > 0 else None
+
     def request(i):
+        if pool is not None:  # requests on a few shared media
+            return S.shared_media_request(np.random.Generator(np.random.PCG64([16180, i])), pool)
         return S.serving_request(np.random.Generator(np.random.PCG64([16177, i])))
 
     gaps = np.random.Generator(np.random.PCG64(16178)).exponential(1.0 / args.rate,
@@ -841,8 +845,9 @@ def run_serving(args):
             del plan, med
     t_tune = time.perf_counter() - t_tune
 
-    def run_stream(nreq, slots, precision):
-        srv = hz.Server(max_slots=slots, autotune=0 if not args.no_pretune else -1)
+    def run_stream(nreq, slots, precision, batch_slots=0):
+        srv = hz.Server(max_slots=slots, autotune=0 if not args.no_pretune else -1,
+                        batch_slots=batch_slots)
         out_q = queue.Queue()
         stats = []
         pool = cf.ThreadPoolExecutor(max_workers=args.gen_threads)
@@ -899,8 +904,15 @@ def run_serving(args):
 
     sampler = ClockSampler(0)
     sampler.start()
-    span, st, stats, late = run_stream(args.requests, args.slots, 1)
+    span, st, stats, late = run_stream(args.requests, args.slots, 1, args.batch_slots)
     clocks = sampler.stop()
+    unbatched = None
+    if args.batch_slots > 0:
+        # the same stream with every request solved on its own
+        span_u, st_u, stats_u, _ = run_stream(args.requests, args.slots, 1, 0)
+        unbatched = {"value": sum(x[1] for x in stats_u) / span_u, "unit": "solves/s",
+                     "p50_ms": st_u["p50_ms"], "p99_ms": st_u["p99_ms"], "span_s": span_u,
+                     "all_converged": all(x[0] for x in stats_u)}
     rhs = sum(x[1] for x in stats)
     ok = all(x[0] for x in stats)
     plain = None
@@ -920,17 +932,21 @@ def run_serving(args):
                  "path": "precision 0 (complex128 preconditioner, FP64 GMRES), one request "
                          "on the GPU at a time, same requests and arrival times; 'mixed' is "
                          "the mixed-precision server on the same subset"}
+    wl = (f"serving-shared{args.media_pool}media-{args.requests}req" if pool is not None
+          else f"serving-{args.requests}req")
     out = {"metric": METRIC + " (serving stream)", "value": rhs / span, "unit": "solves/s",
            "n_gpus": 1, "steps": args.requests, "warmup": 2,
            "ms_per_step": 1e3 * span / args.requests, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-           "config": {"workload": f"serving-{args.requests}req-poisson{args.rate}/s-slots{args.slots}",
+           "config": {"workload": f"{wl}-poisson{args.rate}/s-slots{args.slots}"
+                                  f"-batch{args.batch_slots}",
                       "grids": sorted({"x".join(map(str, k[0])) for k in keys}),
                       "rhs_total": rhs, "graphs": args.serve_graphs,
                       "pretune_s": t_tune, "pretuned_keys": 0 if args.no_pretune else len(keys)},
            "latency": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"]},
            "server": st, "all_converged": ok, "generation_late_s": late,
-           "iters_max": max(x[2] for x in stats), "clocks": clocks, "fp64_plain": plain}
+           "iters_max": max(x[2] for x in stats), "clocks": clocks, "fp64_plain": plain,
+           "unbatched": unbatched}
     print(json.dumps(out), flush=True)
 
 
@@ -960,6 +976,14 @@ def main():
                     help="serving: no autotuning before the stream (served plans keep defaults)")
     ap.add_argument("--plain-requests", type=int, default=30,
                     help="serving: requests of the plain FP64 one-at-a-time comparison (0: none)")
+    ap.add_argument("--restart", type=int, default=0,
+                    help="override the workload's restart length m (0: the workload's own)")
+    ap.add_argument("--media-pool", type=int, default=0,
+                    help="serving: draw requests (1-4 sources each) on this many shared media "
+                         "instead of the serving recipe's one medium per request")
+    ap.add_argument("--batch-slots", type=int, default=0,
+                    help="serving: batched solves of this many slots for requests on the same "
+                         "medium (0: each request alone); with > 0 the unbatched stream is run too")
     ap.add_argument("--gen-threads", type=int, default=6,
                     help="serving: producer threads generating requests ahead of arrival")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -995,6 +1019,8 @@ def main():
         run_interp(args)
         return
     p = getattr(S, WORKLOADS[args.workload][0])()
+    if args.restart > 0:
+        p.restart = args.restart
     if args.impl == "reference":
         run_reference(args, p)
     else:

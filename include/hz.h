@@ -359,6 +359,15 @@ typedef struct {
                           request's stream); -1 the defaults                               */
   int max_bypass;      /* aging: a queued request that later arrivals have been admitted
                           ahead of this many times is not overtaken again; 0 = 2 max_slots */
+  int batch_slots;     /* 0: each request runs alone.  1..64: continuous batching of
+                          requests on the same problem (grid, medium arrays, omega, interp
+                          and solver options; only f differs): a request with at most
+                          batch_slots right-hand sides starts a batched solve of
+                          batch_slots slots or joins a running one at its next restart
+                          boundary, and leaves at the boundary after its last right-hand
+                          side finished; the others keep iterating.  A right-hand side's
+                          result does not depend on which requests share the batch.
+                          Right / flexible preconditioning only (opts.left = 0).         */
 } hz_server_opts;
 
 typedef struct {
@@ -379,6 +388,7 @@ typedef struct {
   size_t hbm_in_use, hbm_budget;
   double p50_ms, p99_ms, mean_ms;  /* submit-to-completion latency of finished requests */
   double rhs_per_s;                /* right-hand sides solved per second since creation  */
+  long long batch_joins;           /* requests that joined a running batched solve       */
 } hz_server_stats;
 
 typedef struct hz_server hz_server;

@@ -107,7 +107,8 @@ void solve_ws_destroy(hz_plan* p) {
 
 namespace {
 hz_status gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs, hz_solve_stats* stats,
-                      double* history, int hlen, void* stream) {
+                      double* history, int hlen, void* stream,
+                      const std::function<int(BatchCtl&)>* boundary = nullptr) {
   if (!plan || !f_in || !u_io) return set_error(HZ_ERR_INVALID_ARG, "null argument");
   if (nrhs < 1 || nrhs > plan->max_nrhs) return set_error(HZ_ERR_INVALID_ARG, "nrhs out of range");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -195,6 +196,48 @@ hz_status gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs, hz_
   std::vector<std::vector<double>> hist_b(history ? nrhs : 0);
   int total_iters = 0;
 
+  // continuous batching: slots join and leave at restart boundaries
+  std::vector<int> busy(nrhs, 0);
+  BatchCtl ctl;
+  if (boundary) {
+    ctl.plan = p;
+    ctl.st = st;
+    ctl.n = n;
+    ctl.B = nrhs;
+    ctl.f = const_cast<double2*>(f);
+    ctl.u = u;
+    ctl.busy = busy.data();
+    ctl.done = done.data();
+    ctl.conv = conv.data();
+    ctl.iters = iters.data();
+    ctl.restarts = restarts.data();
+    ctl.status = status.data();
+    ctl.rel = rel.data();
+    ctl.est = est.data();
+    const int nblk1 = krylov_blocks(n, 1, 1);
+    ctl.admit = [&, nblk1](int b) -> hz_status {
+      double nb = 0.0;
+      HZ_TRY(launch_norm2(f + long(b) * n, n, n, 1, p->partial, nblk1, ks.bnorm + b, st));
+      HZ_CUDA(cudaMemcpyAsync(&nb, ks.bnorm + b, sizeof(double), cudaMemcpyDeviceToHost, st));
+      HZ_CUDA(cudaStreamSynchronize(st));
+      nb = std::sqrt(nb);
+      HZ_CUDA(cudaMemcpyAsync(ks.bnorm + b, &nb, sizeof(double), cudaMemcpyHostToDevice, st));
+      HZ_CUDA(cudaStreamSynchronize(st));
+      bnorm[b] = nb;
+      busy[b] = 1;
+      done[b] = conv[b] = nb == 0.0 ? 1 : 0;  // a zero right-hand side: u = 0
+      iters[b] = restarts[b] = 0;
+      status[b] = HZ_OK;
+      rel[b] = est[b] = 0.0;
+      return HZ_OK;
+    };
+    ctl.release = [&](int b) {
+      busy[b] = 0;
+      done[b] = 1;
+      bnorm[b] = 0.0;
+    };
+  }
+
   for (;;) {
     // true FP64 residual r = f - P u into V_0
     {
@@ -225,6 +268,11 @@ hz_status gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs, hz_
         status[b] = HZ_ERR_NOT_CONVERGED;
       }
       live += !done[b];
+    }
+    if (boundary) {
+      const int a = (*boundary)(ctl);
+      if (a < 0) return hz_status(-a);
+      if (a > 0) continue;  // residuals of the admitted slots first
     }
     if (!live) break;
 
@@ -419,6 +467,7 @@ hz_status gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs, hz_
     }
     HZ_CUDA(cudaStreamSynchronize(st));
   }
+  if (boundary) return HZ_OK;  // each slot was reported at the boundary it finished
 
   // the left form stopped on the preconditioned residual; report the true one
   std::vector<double> rel_true = rel;
@@ -476,6 +525,17 @@ hz_status gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs, hz_
   return ret;
 }
 }  // namespace
+
+hz_status hz::gmres_batch(hz_plan* plan, cudaStream_t st,
+                          const std::function<int(BatchCtl&)>& boundary) {
+  if (!plan) return set_error(HZ_ERR_INVALID_ARG, "null plan");
+  if (plan->opts.left) return set_error(HZ_ERR_INVALID_ARG, "batched solves are right-preconditioned");
+  const size_t vb = size_t(plan->max_nrhs) * plan->med->n * sizeof(double2);
+  // every slot starts free, with a zero right-hand side and iterate
+  HZ_CUDA(cudaMemsetAsync(plan->f, 0, vb, st));
+  HZ_CUDA(cudaMemsetAsync(plan->u, 0, vb, st));
+  return gmres_solve(plan, plan->f, plan->u, plan->max_nrhs, nullptr, nullptr, 0, st, &boundary);
+}
 
 extern "C" hz_status hz_gmres_solve(hz_plan* plan, const void* f_in, void* u_io, int nrhs,
                                     hz_solve_stats* stats, void* stream) {

@@ -1,5 +1,7 @@
 // Launchers of the non-FFT kernels (stencil.cu, krylov.cu).
 #pragma once
+#include <functional>
+
 #include "hz_internal.h"
 
 namespace hz {
@@ -43,6 +45,40 @@ struct SolveWs {
 };
 hz_status solve_ws_create(hz_plan* p);
 void solve_ws_destroy(hz_plan* p);
+
+// Restart-boundary control of a batched solve (continuous batching): each of
+// the plan's max_nrhs slots holds one right-hand side that joins at a
+// restart boundary and leaves once it has converged or failed; the others
+// keep iterating.  Every kernel computes per slot, with launch shapes fixed
+// by the slot count, so a slot's iterates do not depend on the other slots.
+struct BatchCtl {
+  hz_plan* plan = nullptr;
+  cudaStream_t st = nullptr;
+  long n = 0;
+  int B = 0;
+  double2* f = nullptr;  // device right-hand sides, slot b at f + b n
+  double2* u = nullptr;  // device iterates (zero on admission), slot b at u + b n
+  // per-slot state at this boundary
+  const int* busy = nullptr;      // 1 while the slot holds a right-hand side
+  const int* done = nullptr;      // its iteration has ended (converged or failed)
+  const int* conv = nullptr;
+  const int* iters = nullptr;
+  const int* restarts = nullptr;
+  const int* status = nullptr;
+  const double* rel = nullptr;    // true relative residual at this boundary
+  const double* est = nullptr;    // last Givens estimate / ||f||
+  // admit(b): the caller has written f + b n (and zeroed u + b n) on st;
+  // computes ||f_b|| and starts the slot.  release(b): frees a done slot.
+  std::function<hz_status(int)> admit;
+  std::function<void(int)> release;
+};
+// Runs restarted (F)GMRES over the plan's slots until no slot is live and
+// boundary() admits none.  boundary(ctl) is called at every restart
+// boundary after the residual check; it returns 1 when it admitted slots
+// (their residuals are then computed before the next cycle), 0 when not, or
+// -status on an error.  Right / flexible preconditioning only.
+hz_status gmres_batch(hz_plan* plan, cudaStream_t st,
+                      const std::function<int(BatchCtl&)>& boundary);
 
 int stencil_blocks(long n);
 hz_status launch_stencil(const hz_medium* m, int in_prec, const void* x, long in_stride,

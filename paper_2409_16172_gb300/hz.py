@@ -77,7 +77,8 @@ class hz_tune_report(C.Structure):
 
 class hz_server_opts(C.Structure):
     _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int), ("max_queue", C.c_int),
-                ("device", C.c_int), ("autotune", C.c_int), ("max_bypass", C.c_int)]
+                ("device", C.c_int), ("autotune", C.c_int), ("max_bypass", C.c_int),
+                ("batch_slots", C.c_int)]
 
 
 class hz_request(C.Structure):
@@ -90,7 +91,7 @@ class hz_server_stats(C.Structure):
                 ("rejected", C.c_longlong), ("active", C.c_int), ("queued", C.c_int),
                 ("max_active", C.c_int), ("hbm_in_use", C.c_size_t), ("hbm_budget", C.c_size_t),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
-                ("rhs_per_s", C.c_double)]
+                ("rhs_per_s", C.c_double), ("batch_joins", C.c_longlong)]
 _SIGS = {
     "hz_last_error": (C.c_char_p, []),
     "hz_version": (C.c_char_p, []),
@@ -399,8 +400,10 @@ class Server:
     """Continuous-batching solve server (hz_server_* in the C ABI)."""
 
     def __init__(self, max_slots: int = 4, max_queue: int = 4096, hbm_budget: int = 0,
-                 device: int = 0, autotune: int = 0, max_bypass: int = 0):
-        o = hz_server_opts(hbm_budget, max_slots, max_queue, device, autotune, max_bypass)
+                 device: int = 0, autotune: int = 0, max_bypass: int = 0,
+                 batch_slots: int = 0):
+        o = hz_server_opts(hbm_budget, max_slots, max_queue, device, autotune, max_bypass,
+                           batch_slots)
         h = _vp()
         check(lib.hz_server_create(C.byref(o), C.byref(h)))
         self._h = h

@@ -266,7 +266,30 @@ def serving_request(rng, grids=SERVING_GRIDS, max_rhs: int = 8) -> Problem:
     omega = omega_for_ppw(float(c.min()), N, ppw)
     f = point_sources(rng, shape, width, nrhs)
     return Problem(f"serve-{d}d-{N}", shape, c, zeta, None, omega, 1.0, K - Mt, Mt, f, 40,
-                   1e-6, 1, width, meta=dict(ppw=ppw))
+                   1e-6, 1, width, meta=dict(ppw=ppw, width=width))
+
+
+SHARED_MEDIA_GRIDS = [(256, 256), (512, 512), (1024, 1024), (64, 64, 64), (128, 128, 128)]
+
+
+def shared_media_pool(n_media: int, seed: int = 16179, grids=SHARED_MEDIA_GRIDS) -> list:
+    """A pool of media for a stream of requests that share them (many source
+    positions on a few media): medium k is the serving recipe's medium drawn
+    with seed [seed, k] over the given grids, with its own frequency, layer
+    and K."""
+    return [serving_request(np.random.Generator(np.random.PCG64([seed, k])), grids, max_rhs=1)
+            for k in range(n_media)]
+
+
+def shared_media_request(rng, pool, max_rhs: int = 4) -> Problem:
+    """One request on a medium drawn uniformly from the pool: the medium's
+    grid, c, zeta, omega and K, with 1..max_rhs new point sources."""
+    base = pool[int(rng.integers(len(pool)))]
+    nrhs = int(rng.integers(1, max_rhs + 1))
+    f = point_sources(rng, base.shape, base.meta["width"], nrhs)
+    return Problem(base.name + "-shared", base.shape, base.c, base.zeta, None, base.omega, 1.0,
+                   base.M, base.Mt, f, base.restart, base.tol, base.precision, base.meta["width"],
+                   meta=dict(base.meta))
 
 
 def example1(N: int = 2048, *, ppw: float = 12.0, delta: float = 1.0, eta: float = 1.0 / 800,

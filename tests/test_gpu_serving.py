@@ -37,7 +37,8 @@ def _submit(srv, p, f, **kw):
 
 def test_mixed_requests_match_solo_solves_and_oracle(hz):
     reqs = _requests()
-    srv = hz.Server(max_slots=3)
+    # default launch shapes, as the standalone plans below use
+    srv = hz.Server(max_slots=3, autotune=-1)
     tickets = [_submit(srv, p, f) for p, f in reqs]
     results = [srv.result(t) for t in tickets]
     st = srv.stats()
@@ -136,3 +137,62 @@ def test_extension_requests_are_served(hz):
         u1, _ = plan.solve(np.ascontiguousarray(f))
         assert np.array_equal(u1, u), rel(u1, u)
     srv.close()
+
+
+def _batch_problem():
+    p = S.small_problem((96, 128), 9, M=6, Mt=2, width=3)
+    fs = [S.random_field(np.random.Generator(np.random.PCG64(90 + i)), p.shape, k)
+          for i, k in enumerate((2, 1, 3))]
+    return p, fs
+
+
+def _submit_b(srv, p, f):
+    return srv.submit(p.c, f, omega=p.omega, M=p.M, Mt=p.Mt, zeta=p.zeta, alpha=0.15,
+                      restart=10, tol=1e-10, maxit=3000)
+
+
+def test_batched_requests_join_at_restart_boundaries(hz):
+    """Continuous batching (batch_slots): requests on the same medium share
+    one batched solve; a request submitted while the batch is iterating
+    joins it at a restart boundary and leaves when its right-hand sides are
+    done.  Each request's solution is bit for bit the one it gets alone in a
+    batch, every right-hand side meets the tolerance by the oracle's
+    operator, and a request on another medium runs beside the batch."""
+    import time
+    p, (fa, fb, fc) = _batch_problem()
+    q = S.small_problem((64, 64), 8, M=5, Mt=2, width=3)
+    fq = S.random_field(np.random.Generator(np.random.PCG64(99)), q.shape, 1)
+    alone = {}
+    for name, f in (("a", fa), ("b", fb)):
+        srv = hz.Server(max_slots=1, batch_slots=4)
+        done, u, st, status = srv.result(_submit_b(srv, p, f))
+        assert done and status == 0
+        alone[name] = (u, st)
+        srv.close()
+    srv = hz.Server(max_slots=2, batch_slots=4)
+    ta = _submit_b(srv, p, fa)
+    t0 = time.time()
+    while srv.stats()["active"] < 1 and time.time() - t0 < 10:
+        time.sleep(0.001)
+    time.sleep(0.02)  # the batch is iterating
+    tb = _submit_b(srv, p, fb)
+    tc = _submit_b(srv, p, fc)  # 3 right-hand sides: no room beside a and b
+    tq = srv.submit(q.c, fq, omega=q.omega, M=q.M, Mt=q.Mt, zeta=q.zeta, alpha=0.15,
+                    restart=10, tol=1e-10, maxit=3000)
+    res = {k: srv.result(t, timeout=600) for k, t in (("a", ta), ("b", tb), ("c", tc), ("q", tq))}
+    stats = srv.stats()
+    srv.close()
+    assert stats["batch_joins"] >= 1, stats
+    assert stats["completed"] == 4 and stats["failed"] == 0
+    for k in ("a", "b"):
+        assert np.array_equal(res[k][1], alone[k][0]), k
+        assert [s["iters"] for s in res[k][2]] == [s["iters"] for s in alone[k][1]]
+    med_o = O.make_medium(p.c, p.zeta, None, p.omega, p.M, p.Mt, 1.0, None, 0.15)
+    for k, f in (("a", fa), ("b", fb), ("c", fc)):
+        done, u, st, status = res[k]
+        assert done and status == 0
+        for b in range(f.shape[0]):
+            assert st[b]["converged"]
+            assert rel(O.apply_operator(med_o, u[b]), f[b]) <= 1e-10
+    medq = O.make_medium(q.c, q.zeta, None, q.omega, q.M, q.Mt, 1.0, None, 0.15)
+    assert rel(O.apply_operator(medq, res["q"][1][0]), fq[0]) <= 1e-10

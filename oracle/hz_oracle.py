@@ -38,6 +38,10 @@ Readings of places where the paper is silent:
   * Quadratic Lagrange basis (basis = 1): M odd, elements of two consecutive
     intervals [c_2e, c_2e+2], each segment of the two-segment split holding
     an even number of intervals; layer points keep the hats in zeta.
+  * Cubic Hermite basis (basis = 2): on each interval the value planes take
+    h00, h01 and extra planes with the symbol's derivative dq/dc at the two
+    real nodes take h h10, h h11 (K = M + Mt + M planes); layer points keep
+    the hats in zeta.
   * Bivariate interpolation (Ma >= 2): Ma damping nodes equispaced on
     [min a, max a]; node (s, j) carries gamma_s and damping a_j + alpha w;
     weights are products of the speed weights and hats in a.
@@ -55,7 +59,10 @@ function here is "parity unpinned"):
   real_nodes, build_nodes equispaced nodes, c_o a node, the two-segment split (and its
                           even-interval form for the quadratic basis)
   hat_weights             partition of unity, <= 2 non-zeros, reproduction of gamma (hats);
-                          reproduction of 1, c, c^2 and <= 3 non-zeros (quadratic basis)
+                          reproduction of 1, c, c^2 and <= 3 non-zeros (quadratic basis);
+                          reproduction of cubics from values and derivatives, not of c^4,
+                          <= 4 non-zeros (cubic Hermite)
+  node_symbol_dc          central difference of node_symbol in c
   damping_nodes, damping_weights, interp_weights
                           reproduction of every bilinear f(c, a), <= 4 non-zeros, collapse to
                           the univariate form for constant a
@@ -64,7 +71,8 @@ function here is "parity unpinned"):
   apply_preconditioner    plane-wave closed form; equals the direct O(n^2) Op(q_M); equals the
                           un-interpolated Op(q) where the medium takes node values;
                           Q_{N,M} P_N = I (discrete symbol, constant c, a > 0, alpha = 0);
-                          convergence orders 2 (hats, in c and in a) and 3 (quadratic)
+                          convergence orders 2 (hats, in c and in a), 3 (quadratic) and 4
+                          (cubic Hermite)
   apply_pdo_direct, exact_symbol_at_point, interpolated_symbol_at_point
                           the constant-medium closed form and the pins above
   assemble_dense          column by column from apply_operator, then checked through the LU
@@ -198,7 +206,10 @@ class Nodes:
     m_o       index of c_o among the real nodes (-1 when there is no layer)
     a_nodes   damping nodes of the bivariate form (one entry otherwise);
               node k = s * Ma + j has speed node s and damping node j
-    basis     0: piecewise-linear hats in c; 1: piecewise quadratic Lagrange
+    basis     0: piecewise-linear hats in c; 1: piecewise quadratic Lagrange;
+              2: piecewise cubic Hermite (value and c-derivative planes)
+    deriv     per node: 0 for the symbol q(gamma_k, xi), 1 for its derivative
+              in the wave speed dq/dc at the real node c_k (basis 2)
     """
     gamma: np.ndarray
     a: np.ndarray
@@ -209,6 +220,7 @@ class Nodes:
     a_nodes: np.ndarray = field(default_factory=lambda: np.zeros(1))
     basis: int = 0
     alpha: float = 0.05
+    deriv: np.ndarray = field(default=None)
 
     @property
     def K(self) -> int:
@@ -303,7 +315,10 @@ def build_nodes(c, zeta, omega: float, M: int, Mt: int, c_o: float,
     c_lo, c_hi = float(c.min()), float(c.max())
     if has_layer:
         c_lo, c_hi = min(c_lo, c_o), max(c_hi, c_o)
-    cr = real_nodes(c_lo, c_hi, M, c_o if (has_layer or M == 1) else None, basis)
+    if basis == 2 and Ma >= 2:
+        raise ValueError("the cubic Hermite basis is univariate (Ma <= 1)")
+    cr = real_nodes(c_lo, c_hi, M, c_o if (has_layer or M == 1) else None,
+                    1 if basis == 1 else 0)
     m_o = -1
     if has_layer:
         hit = np.nonzero(cr == c_o)[0]
@@ -324,7 +339,14 @@ def build_nodes(c, zeta, omega: float, M: int, Mt: int, c_o: float,
         an = np.array([a_node], dtype=np.float64)
     gam = np.array([g for g in gam_s for _ in an], np.complex128)
     ak = np.array([aj + alpha * omega for _ in gam_s for aj in an], np.float64)
-    return Nodes(gam, ak, cr, zn, m_o, float(omega), an, int(basis), float(alpha))
+    deriv = np.zeros(len(gam), dtype=np.int64)
+    if basis == 2 and len(cr) >= 2:
+        # cubic Hermite: one derivative plane dq/dc per real node, after the
+        # value planes
+        gam = np.concatenate([gam, cr.astype(np.complex128)])
+        ak = np.concatenate([ak, np.full(len(cr), an[0] + alpha * omega)])
+        deriv = np.concatenate([deriv, np.ones(len(cr), dtype=np.int64)])
+    return Nodes(gam, ak, cr, zn, m_o, float(omega), an, int(basis), float(alpha), deriv)
 
 
 def hat_weights(c, zeta, nodes: Nodes) -> np.ndarray:
@@ -347,6 +369,21 @@ def hat_weights(c, zeta, nodes: Nodes) -> np.ndarray:
     M = len(cr)
     if M == 1:
         W[0, real] = 1.0
+    elif len(real) and nodes.basis == 2:
+        # cubic Hermite on [c_i, c_{i+1}], t = (c - c_i) / h: the values
+        # take h00 = 2t^3 - 3t^2 + 1 and h01 = 3t^2 - 2t^3, the derivative
+        # planes h h10 = h (t^3 - 2t^2 + t) and h h11 = h (t^3 - t^2)
+        cv = cf[real]
+        i = np.clip(np.searchsorted(cr, cv, side="right") - 1, 0, M - 2)
+        h = cr[i + 1] - cr[i]
+        t = (cv - cr[i]) / h
+        if np.any(t < -1e-12) or np.any(t > 1 + 1e-12):
+            raise ValueError("wave speed outside the node range")
+        nv = len(nodes.gamma) - M  # value planes come first
+        np.add.at(W, (i, real), 2 * t ** 3 - 3 * t ** 2 + 1)
+        np.add.at(W, (i + 1, real), 3 * t ** 2 - 2 * t ** 3)
+        np.add.at(W, (nv + i, real), h * (t ** 3 - 2 * t ** 2 + t))
+        np.add.at(W, (nv + i + 1, real), h * (t ** 3 - t ** 2))
     elif len(real) and nodes.basis == 1:
         # element e spans the nodes 2e, 2e+1, 2e+2; Lagrange polynomials of
         # degree 2 through them
@@ -421,6 +458,21 @@ def node_symbol(gamma_k: complex, a_k: float, omega: float, xi2: np.ndarray) -> 
     return 1.0 / (omega ** 2 + 1j * omega * a_k - gamma_k ** 2 * xi2)
 
 
+def node_symbol_dc(c_k: float, a_k: float, omega: float, xi2: np.ndarray) -> np.ndarray:
+    """dq/dc at the real node c_k: with q = 1/p, p = w^2 + i w a - c^2 |xi|^2
+    (Eqn. 021), dq/dc = -p_c / p^2 = 2 c |xi|^2 / p^2 (the first derivative
+    in c of the symbol whose second derivative Section 4.3 prints)."""
+    p = omega ** 2 + 1j * omega * a_k - c_k ** 2 * xi2
+    return 2.0 * c_k * xi2 / p ** 2
+
+
+def symbol_of(nodes: Nodes, k: int, omega: float, xi2: np.ndarray) -> np.ndarray:
+    """The symbol of plane k: q(gamma_k, xi), or dq/dc for a derivative plane."""
+    if nodes.deriv is not None and nodes.deriv[k]:
+        return node_symbol_dc(float(nodes.gamma[k].real), nodes.a[k], omega, xi2)
+    return node_symbol(nodes.gamma[k], nodes.a[k], omega, xi2)
+
+
 # ----------------------------------------------------------------------------
 # Preconditioner apply (Eqn. 103 / 403): one forward DFT, K symbol multiplies
 # each followed by an inverse DFT, then the pointwise weighted sum.
@@ -469,7 +521,7 @@ def apply_preconditioner(med: Medium, v: np.ndarray, exact: bool = False,
     vhat = dft(v, inverse=False, exact=exact, workers=workers)
     out = np.zeros(med.shape, dtype=np.complex128)
     for k in range(med.nodes.K):
-        qk = node_symbol(med.nodes.gamma[k], med.nodes.a[k], med.omega, med.xi2)
+        qk = symbol_of(med.nodes, k, med.omega, med.xi2)
         uk = dft(qk * vhat, inverse=True, exact=exact, workers=workers)
         out += med.W[k] * uk
     return out
@@ -523,7 +575,7 @@ def interpolated_symbol_at_point(med: Medium):
         s = np.zeros_like(xi2, dtype=np.complex128)
         for k in range(med.nodes.K):
             if Wf[k, p] != 0.0:
-                s = s + Wf[k, p] * node_symbol(med.nodes.gamma[k], med.nodes.a[k], med.omega, xi2)
+                s = s + Wf[k, p] * symbol_of(med.nodes, k, med.omega, xi2)
         return s
     return f
 

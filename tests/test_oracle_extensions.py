@@ -1,7 +1,7 @@
-"""Pins for the oracle's two extensions of the interpolation, both named by
-the paper as directions it did not take (Section 6): a piecewise quadratic
-Lagrange basis in the wave speed, and bivariate interpolation in (c, a) for
-damping that does not follow the wave speed.  Each pin is fixed by
+"""Pins for the oracle's extensions of the interpolation, named by the paper
+as directions it did not take (Section 6): piecewise quadratic Lagrange and
+cubic Hermite bases in the wave speed, and bivariate interpolation in (c, a)
+for damping that does not follow the wave speed.  Each pin is fixed by
 mathematics, not by re-running the oracle: polynomial reproduction, the
 order of convergence, linearity against the direct O(n^2) sum, and
 exactness at node values.  None of these tests needs a GPU."""
@@ -83,6 +83,79 @@ def test_lagrange_interpolation_converges_third_order():
         slopes[basis] = np.polyfit(np.log(hs), np.log(errs), 1)[0]
     assert 1.7 < slopes[0] < 2.5, slopes
     assert 2.6 < slopes[1] < 3.5, slopes
+
+
+# --------------------------------------------------------------------------
+# Piecewise cubic Hermite basis in c (values and c-derivatives at the nodes)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("M", [2, 4, 7])
+def test_hermite_basis_reproduces_cubics(M):
+    """With node values f(c_k) on the value planes and node derivatives
+    f'(c_k) on the derivative planes, the cubic Hermite weights reproduce
+    every cubic f exactly (and not c^4); at most four weights per point are
+    non-zero, and the value weights alone sum to one."""
+    nodes = _nodes_on_unit_range(M, 2)
+    assert nodes.K == 2 * M and list(nodes.deriv) == [0] * M + [1] * M
+    cs = np.linspace(1.0, 2.0, 301).reshape(-1, 1)
+    W = O.hat_weights(cs, np.zeros_like(cs), nodes)[:, :, 0]
+    ck = nodes.c_real
+    x = cs[:, 0]
+    Wv, Wd = W[:M], W[M:]
+    np.testing.assert_allclose(Wv.sum(0), 1.0, atol=1e-14)
+    for f, df in ((lambda c: 1 + 0 * c, lambda c: 0 * c), (lambda c: c, lambda c: 1 + 0 * c),
+                  (lambda c: c ** 2, lambda c: 2 * c), (lambda c: c ** 3 - 2 * c, lambda c: 3 * c ** 2 - 2)):
+        got = (Wv * f(ck)[:, None]).sum(0) + (Wd * df(ck)[:, None]).sum(0)
+        np.testing.assert_allclose(got, f(x), atol=1e-12)
+    got4 = (Wv * (ck ** 4)[:, None]).sum(0) + (Wd * (4 * ck ** 3)[:, None]).sum(0)
+    assert np.abs(got4 - x ** 4).max() > 1e-5
+    assert (np.count_nonzero(W, axis=0) <= 4).all()
+
+
+def test_symbol_derivative_in_c():
+    """node_symbol_dc is the derivative of node_symbol in the wave speed: a
+    central difference of Eqn. 021's symbol agrees to O(step^2)."""
+    xi2 = np.linspace(0.0, 4000.0, 41)
+    for c, a in ((1.3, 6.0), (2.1, 0.5)):
+        d = 1e-5
+        fd = (O.node_symbol(c + d, a, 30.0, xi2) - O.node_symbol(c - d, a, 30.0, xi2)) / (2 * d)
+        np.testing.assert_allclose(O.node_symbol_dc(c, a, 30.0, xi2), fd, rtol=1e-6, atol=1e-12)
+
+
+def test_hermite_interpolation_converges_fourth_order():
+    """Cubic Hermite interpolation of the symbol in c: ||(Q - Q_M) v|| falls
+    like h_M^4 (hats: h_M^2); the direct un-interpolated Q is the reference."""
+    shape = (12, 12)
+    c = _smooth_speed(shape)
+    v = S.random_field(rng(8), shape)
+    med0 = O.make_medium(c, None, None, 20.0, M=3, c_o=1.0, alpha=0.5, basis=2)
+    ref = O.apply_pdo_direct(O.exact_symbol_at_point(med0), v)
+    errs, hs = [], []
+    for M in (5, 9, 17, 33):
+        med = O.make_medium(c, None, None, 20.0, M=M, c_o=1.0, alpha=0.5, basis=2)
+        errs.append(np.linalg.norm(O.apply_preconditioner(med, v) - ref))
+        hs.append((c.max() - c.min()) / (M - 1))
+    slope = np.polyfit(np.log(hs), np.log(errs), 1)[0]
+    assert 3.5 < slope < 4.6, (slope, errs)
+
+
+def test_hermite_fft_apply_equals_direct_sum_with_layer():
+    """The K FFT form (value and derivative planes, hats in zeta in the
+    layer) equals the direct O(n^2) Op(q_M) with the interpolated symbol, and
+    is exact where c takes node values (the derivative weights vanish
+    there)."""
+    p = S.small_problem((12, 10), 5, M=4, Mt=2, width=2)
+    med = O.make_medium(p.c, p.zeta, None, p.omega, 4, 2, 1.0, None, 0.2, basis=2)
+    v = S.random_field(rng(3), p.shape)
+    fft = O.apply_preconditioner(med, v)
+    direct = O.apply_pdo_direct(O.interpolated_symbol_at_point(med), v)
+    assert np.linalg.norm(fft - direct) <= 1e-12 * np.linalg.norm(direct)
+    c = np.full((8, 8), 1.0)
+    c[2:6, 2:6] = 2.0
+    med = O.make_medium(c, None, None, 15.0, M=3, c_o=1.0, alpha=0.2, basis=2)
+    v = S.random_field(rng(4), c.shape)
+    exact = O.apply_pdo_direct(O.exact_symbol_at_point(med), v)
+    assert np.linalg.norm(O.apply_preconditioner(med, v) - exact) <= 1e-12 * np.linalg.norm(exact)
 
 
 # --------------------------------------------------------------------------

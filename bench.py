@@ -616,7 +616,8 @@ def run_interp(args):
     at the mean damping) and bivariately with Ma = 2, 3 (and 4) damping nodes,
     with the node damping regularised by alpha omega (alpha = 0.1) and not
     (alpha = 0; a > 0 everywhere); (b) the 1024^2 workload's medium with hats
-    vs quadratic Lagrange polynomials in c."""
+    vs quadratic Lagrange polynomials vs cubic Hermite (values and
+    c-derivatives) in c."""
     import torch
     from paper_2409_16172_gb300 import build, synth as S
     build.build()
@@ -672,6 +673,8 @@ def run_interp(args):
         basis[f"linear M={M}"] = one(pc, M=M)
     for M in (5, 7, 11, 13):
         basis[f"quadratic M={M}"] = one(pc, M=M, basis=1)
+    for M in (4, 6, 8):
+        basis[f"hermite M={M}"] = one(pc, M=M, basis=2)
     clocks = sampler.stop()
     tag = "a/w in [0.005, 0.05], alpha=0.0"
     u_it = biv[f"{tag}: univariate (a_k = mean a + alpha w)"]["iters"]

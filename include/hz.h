@@ -83,8 +83,13 @@ typedef struct {
  *              quadratic Lagrange polynomials on elements of two intervals
  *              (the higher-order basis of Section 6; M odd, and with c_o
  *              inside the range each of its two segments gets an even
- *              number of intervals).  Layer points keep the hats in zeta.
- *              basis 1 is univariate only (Ma <= 1).
+ *              number of intervals); 2: piecewise cubic Hermite in c (the
+ *              other basis Section 6 names): on [c_m, c_m+1] the planes of
+ *              q(c_m) and q(c_m+1) take h00(t), h01(t) and M extra planes
+ *              with the symbol's derivative dq/dc = 2 c |xi|^2 q^2 at the
+ *              real nodes take h h10(t), h h11(t) (K = M + Mt + M).  Layer
+ *              points keep the hats in zeta.  basis 1 and 2 are univariate
+ *              only (Ma <= 1).
  * Fields added later (Ma, basis) read as 0 when a caller zero-fills the
  * struct, which keeps the univariate piecewise-linear method.           */
 typedef struct {
@@ -176,10 +181,10 @@ hz_status hz_set_allocator(void* (*alloc)(size_t bytes, void* ctx),
  * 16, 24, 32, 48, 64, 96, 128, 192, 256, 512, 1024, 2048 and the lengths with
  * a factor 5 listed at the top of this file (z <= 1024); fewer
  * than 2^31 points.
- * With interp->Ma >= 2 or interp->basis == 1 the per-point record is up to
+ * With interp->Ma >= 2 or interp->basis >= 1 the per-point record is up to
  * four (node, weight) pairs (52 bytes per point) instead of (segment, t).
- * Errors: HZ_ERR_INVALID_ARG (grid, options: Ma < 0, basis not 0/1, basis 1
- * with Ma >= 2 or an even M, (M + Mt) Ma > 64), HZ_ERR_MEDIUM (c <= 0,
+ * Errors: HZ_ERR_INVALID_ARG (grid, options: Ma < 0, basis not 0/1/2, basis
+ * 1 or 2 with Ma >= 2, basis 1 with an even M, more than 64 planes), HZ_ERR_MEDIUM (c <= 0,
  * zeta < 0, NaN, c != c_o in the layer, too few nodes), HZ_ERR_OOM,
  * HZ_ERR_CUDA. */
 hz_status hz_create_medium(const hz_grid* grid, const double* c, const double* zeta,

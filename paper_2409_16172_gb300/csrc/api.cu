@@ -178,6 +178,7 @@ hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* s
   auto xi = [&](const AxisTables& t) -> const void* { return prec == 0 ? (const void*)t.xi2_64 : (const void*)t.xi2_32; };
   const void* A = prec == 0 ? (const void*)m->symA64 : (const void*)m->symA32;
   const void* G = prec == 0 ? (const void*)m->symG64 : (const void*)m->symG32;
+  const void* D = prec == 0 ? (const void*)m->symD64 : (const void*)m->symD32;
   const void* rec = prec == 0 ? (const void*)m->rec64 : (const void*)m->rec32;
   const long rows = n / nx;
   const double s = prec == 0 ? 16.0 : 8.0;          // working complex element
@@ -203,7 +204,7 @@ hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* s
     PhaseScope ps(st, PH_SYMINV, B * (dn * s + m->rowk_used * nx * s),
                   B * K * (5.0 * dn * l2(ny) + 14.0 * dn));
     HZ_TRY(oy->line_sym_inv(prec, p->tmp, p->planes, nx, 1, nx, 0, n, m->K, nrhs, xi(tx), nullptr,
-                            xi(ty), A, G, m->rowmask, 0, 1, tw(ty), tw2(ty), st, active,
+                            xi(ty), A, G, D, m->rowmask, 0, 1, tw(ty), tw2(ty), st, active,
                             p->tune.syminv_kpb, p->tune.col_pair));
   } else {
     const FftOps* oz = fft_ops(nz);
@@ -218,7 +219,7 @@ hz_status precond_apply(hz_plan* p, int prec, const double2* in, const double* s
       PhaseScope ps(st, PH_SYMINV, B * (dn * s + m->slabk_used * slab * s),
                     B * K * (5.0 * dn * l2(nz) + 14.0 * dn));
       HZ_TRY(oz->line_sym_inv(prec, p->tmp, p->planes, nx, ny, slab, nx, n, m->K, nrhs, xi(tx),
-                              xi(ty), xi(tz), A, G, m->slabmask, 0, 1, tw(tz), tw2(tz), st,
+                              xi(ty), xi(tz), A, G, D, m->slabmask, 0, 1, tw(tz), tw2(tz), st,
                               active, p->tune.syminv_kpb, p->tune.col_pair));
     }
     {

@@ -195,9 +195,9 @@ template <typename R>
 hz_status line_sym_inv_t(const void* vhat, void* planes, int nx, long outer, long S, long ostride,
                          long n, int K, int batch, const void* xi2_x, const void* xi2_o,
                          const void* xi2_l, const void* symA, const void* symG,
-                         const unsigned long long* smask, long smO, long smS, const void* tw,
-                         const void* tw2, cudaStream_t st, const int* active, int kpb,
-                         int pair) {
+                         const void* symD, const unsigned long long* smask, long smO, long smS,
+                         const void* tw, const void* tw2, cudaStream_t st, const int* active,
+                         int kpb, int pair) {
   using C = LineCfg<R, N>;
   using V = typename cvec<R>::T;
   // nodes per block: 1, 2 or 4
@@ -220,8 +220,9 @@ hz_status line_sym_inv_t(const void* vhat, void* planes, int nx, long outer, lon
                          static_cast<const float2*>(vhat), static_cast<float2*>(planes), nx, ntile,
                          S, ostride, n, K, static_cast<const float*>(xi2_x),
                          static_cast<const float*>(xi2_o), static_cast<const float*>(xi2_l),
-                         static_cast<const float2*>(symA), static_cast<const float2*>(symG), smask,
-                         smO, smS, static_cast<const float4*>(tw2), active));
+                         static_cast<const float2*>(symA), static_cast<const float2*>(symG),
+                         static_cast<const float*>(symD), smask, smO, smS,
+                         static_cast<const float4*>(tw2), active));
       HZ_CUDA(cudaGetLastError());
       return HZ_OK;
     }
@@ -235,8 +236,8 @@ hz_status line_sym_inv_t(const void* vhat, void* planes, int nx, long outer, lon
                      static_cast<const V*>(vhat), static_cast<V*>(planes), nx, ntile, S, ostride, n,
                      K, static_cast<const R*>(xi2_x), static_cast<const R*>(xi2_o),
                      static_cast<const R*>(xi2_l), static_cast<const V*>(symA),
-                     static_cast<const V*>(symG), smask, smO, smS, static_cast<const V*>(tw),
-                     active));
+                     static_cast<const V*>(symG), static_cast<const R*>(symD), smask, smO, smS,
+                     static_cast<const V*>(tw), active));
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
@@ -244,14 +245,15 @@ hz_status line_sym_inv_t(const void* vhat, void* planes, int nx, long outer, lon
 hz_status line_sym_inv(int prec, const void* vhat, void* planes, int nx, long outer, long S,
                        long ostride, long n, int K, int batch, const void* xi2_x,
                        const void* xi2_o, const void* xi2_l, const void* symA, const void* symG,
-                       const unsigned long long* smask, long smO, long smS, const void* tw,
-                       const void* tw2, cudaStream_t st, const int* active, int kpb, int pair) {
+                       const void* symD, const unsigned long long* smask, long smO, long smS,
+                       const void* tw, const void* tw2, cudaStream_t st, const int* active,
+                       int kpb, int pair) {
   return prec == 0
              ? line_sym_inv_t<double>(vhat, planes, nx, outer, S, ostride, n, K, batch, xi2_x,
-                                      xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, nullptr, st,
-                                      active, kpb, 0)
+                                      xi2_o, xi2_l, symA, symG, symD, smask, smO, smS, tw, nullptr,
+                                      st, active, kpb, 0)
              : line_sym_inv_t<float>(vhat, planes, nx, outer, S, ostride, n, K, batch, xi2_x,
-                                     xi2_o, xi2_l, symA, symG, smask, smO, smS, tw, tw2, st,
+                                     xi2_o, xi2_l, symA, symG, symD, smask, smO, smS, tw, tw2, st,
                                      active, kpb, pair);
 }
 

@@ -587,7 +587,7 @@ line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
                     long ostride, long n, int K, const R* __restrict__ xi2_x,
                     const R* __restrict__ xi2_o, const R* __restrict__ xi2_l,
                     const typename cvec<R>::T* __restrict__ symA,
-                    const typename cvec<R>::T* __restrict__ symG,
+                    const typename cvec<R>::T* __restrict__ symG, const R* __restrict__ symD,
                     const unsigned long long* __restrict__ smask, long smO, long smS,
                     const typename cvec<R>::T* __restrict__ tw, const int* __restrict__ active) {
   pdl_wait();
@@ -632,13 +632,21 @@ line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
 #pragma unroll 1
   for (int k = k0; k < k1; ++k) {
     const V A = symA[k], G = symG[k];
+    const R D = symD ? symD[k] : R(0);
     const int kk = k - k0;
     V v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       // vhat q_k = vhat conj(den) / |den|^2,  den = A - G |xi|^2
       const V den = cmk<V>(A.x - G.x * s2[e], A.y - G.y * s2[e]);
-      v[e] = cscale(cmulc(spec[e], den), recip(den.x * den.x + den.y * den.y));
+      const R inv = recip(den.x * den.x + den.y * den.y);
+      V r = cscale(cmulc(spec[e], den), inv);
+      if (D != R(0)) {
+        // derivative plane of the Hermite basis: vhat dq/dc = vhat q (D |xi|^2 q),
+        // D = 2 c_k
+        r = cscale(cmul(r, cmk<V>(den.x * inv, -den.y * inv)), D * s2[e]);
+      }
+      v[e] = r;
     }
     F::run_regs(sm + col, t, v, tw);
     if (valid) {
@@ -666,7 +674,7 @@ line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ p
                          int ntile, long S, long ostride, long n, int K,
                          const float* __restrict__ xi2_x, const float* __restrict__ xi2_o,
                          const float* __restrict__ xi2_l, const float2* __restrict__ symA,
-                         const float2* __restrict__ symG,
+                         const float2* __restrict__ symG, const float* __restrict__ symD,
                          const unsigned long long* __restrict__ smask, long smO, long smS,
                          const float4* __restrict__ tw2, const int* __restrict__ active) {
   pdl_wait();
@@ -699,7 +707,7 @@ line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ p
     mb[(e * KPB) / 32] |= bits << ((e * KPB) % 32);
   }
   // vhat q_k = vhat conj(den) / |den|^2,  den = A - G |xi|^2
-  auto symbol = [](const PV& sp, f2 s2, f2 AX, f2 AY, f2 NGX, f2 NGY) {
+  auto symbol = [](const PV& sp, f2 s2, f2 AX, f2 AY, f2 NGX, f2 NGY, float D) {
     PV den;
     den.x = fma2(NGX, s2, AX);
     den.y = fma2(NGY, s2, AY);
@@ -709,6 +717,16 @@ line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ p
     PV r;
     r.x = q.x * inv;
     r.y = q.y * inv;
+    if (D != 0.0f) {
+      // derivative plane of the Hermite basis: vhat dq/dc = vhat q (D |xi|^2 q)
+      PV qv;
+      qv.x = den.x * inv;
+      qv.y = neg2(den.y) * inv;
+      r = cmul(r, qv);
+      const f2 ds = f2_splat(D) * s2;
+      r.x = r.x * ds;
+      r.y = r.y * ds;
+    }
     return r;
   };
   auto store = [&](int k, int kk, PV (&v)[E]) {
@@ -734,6 +752,7 @@ line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ p
     // one node: the symbol product straight from the loads (no copy of the
     // spectrum kept across nodes)
     const float2 A = symA[k0], G = symG[k0];
+    const float D = symD ? symD[k0] : 0.0f;
     const f2 AX = f2_splat(A.x), AY = f2_splat(A.y), NGX = f2_splat(-G.x), NGY = f2_splat(-G.y);
     PV v[E];
 #pragma unroll
@@ -741,7 +760,7 @@ line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ p
       PV sp;
       f2 s2;
       load(e, sp, s2);
-      v[e] = symbol(sp, s2, AX, AY, NGX, NGY);
+      v[e] = symbol(sp, s2, AX, AY, NGX, NGY, D);
     }
     F::run_regs(sm + col, t, v, tw2);
     store(k0, 0, v);
@@ -753,10 +772,11 @@ line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ p
 #pragma unroll 1
     for (int k = k0; k < k1; ++k) {
       const float2 A = symA[k], G = symG[k];
+      const float D = symD ? symD[k] : 0.0f;
       const f2 AX = f2_splat(A.x), AY = f2_splat(A.y), NGX = f2_splat(-G.x), NGY = f2_splat(-G.y);
       PV v[E];
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = symbol(spec[e], s2[e], AX, AY, NGX, NGY);
+      for (int e = 0; e < E; ++e) v[e] = symbol(spec[e], s2[e], AX, AY, NGX, NGY, D);
       F::run_regs(sm + col, t, v, tw2);
       store(k, k - k0, v);
     }

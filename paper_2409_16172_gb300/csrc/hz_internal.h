@@ -157,6 +157,11 @@ struct hz_medium {
   double2* symG64 = nullptr;        // gamma_k^2
   float2* symA32 = nullptr;
   float2* symG32 = nullptr;
+  // cubic Hermite (basis 2): per plane 0 for the symbol q_k, 2 c_k for its
+  // derivative in c, dq/dc = 2 c |xi|^2 q^2 (NULL when no plane is one)
+  std::vector<double> dcoef;
+  double* symD64 = nullptr;
+  float* symD32 = nullptr;
   hz::AxisTables ax[3];
   double inv_h2[3] = {0, 0, 0};
   // sum over x-rows (3D: also z-slabs) of the number of nodes used there;
@@ -195,14 +200,15 @@ struct FftOps {
                          long ostride, long bstride, int batch,
                          const unsigned long long* omask, int K, const void* tw,
                          cudaStream_t st, const int* active, int per_rhs);
-  // last axis: symbol multiply of the spectrum and inverse FFT, one plane per k;
+  // last axis: symbol multiply of the spectrum and inverse FFT, one plane per k
+  // (symD, nullable: per plane 0, or 2 c_k for a Hermite derivative plane);
   // tw2 (complex64 only, nullable): the paired twiddle table, selects the
   // two-columns-per-thread kernel when nx is even; pair > 1 halves its blocks
   hz_status (*line_sym_inv)(int prec, const void* vhat, void* planes, int nx, long outer, long S,
                             long ostride, long n, int K, int batch, const void* xi2_x,
                             const void* xi2_o, const void* xi2_l, const void* symA,
-                            const void* symG, const unsigned long long* smask, long smO,
-                            long smS, const void* tw, const void* tw2, cudaStream_t st,
+                            const void* symG, const void* symD, const unsigned long long* smask,
+                            long smO, long smS, const void* tw, const void* tw2, cudaStream_t st,
                             const int* active, int kpb, int pair);
 };
 

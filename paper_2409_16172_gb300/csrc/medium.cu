@@ -152,8 +152,8 @@ __global__ void gen_record_kernel(const double* __restrict__ c, const double* __
     const double ci = c[i];
     const double zi = zeta ? zeta[i] : 0.0;
     const double ai = a ? a[i] : 0.0;
-    int sk[3] = {0, 0, 0};
-    double sw[3] = {0.0, 0.0, 0.0};
+    int sk[4] = {0, 0, 0, 0};
+    double sw[4] = {0.0, 0.0, 0.0, 0.0};
     int ns = 0;
     if (zi > 0.0) {
       int m = 0;
@@ -170,7 +170,20 @@ __global__ void gen_record_kernel(const double* __restrict__ c, const double* __
     } else {
       int m = 0;
       while (m + 2 < nd.M && ci >= nd.c_real[m + 1]) ++m;
-      if (nd.basis == 1) {
+      if (nd.basis == 2) {
+        // cubic Hermite on [c_m, c_m+1]: values h00, h01, derivative
+        // planes (after the M + Mt value planes) h h10, h h11
+        const double h = nd.c_real[m + 1] - nd.c_real[m];
+        double t = (ci - nd.c_real[m]) / h;
+        t = fmin(fmax(t, 0.0), 1.0);
+        const double t2 = t * t, t3 = t2 * t;
+        const int nv = nd.M + nd.Mt;
+        sk[0] = m;          sw[0] = 2.0 * t3 - 3.0 * t2 + 1.0;
+        sk[1] = m + 1;      sw[1] = 3.0 * t2 - 2.0 * t3;
+        sk[2] = nv + m;     sw[2] = h * (t3 - 2.0 * t2 + t);
+        sk[3] = nv + m + 1; sw[3] = h * (t3 - t2);
+        ns = 4;
+      } else if (nd.basis == 1) {
         const int e = min(m / 2, (nd.M - 1) / 2 - 1);
         const double c0 = nd.c_real[2 * e], c1 = nd.c_real[2 * e + 1], c2 = nd.c_real[2 * e + 2];
         sk[0] = 2 * e;     sw[0] = (ci - c1) * (ci - c2) / ((c0 - c1) * (c0 - c2));
@@ -369,11 +382,12 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
   if (!(interp->c_o > 0) || interp->alpha < 0 || interp->a_node < 0 ||
       (interp->symbol_kind != 0 && interp->symbol_kind != 1))
     return set_error(HZ_ERR_INVALID_ARG, "bad interpolation options");
-  if (interp->Ma < 0 || (interp->basis != 0 && interp->basis != 1) ||
-      (interp->basis == 1 && interp->Ma > 1) ||
-      (interp->M + interp->Mt) * std::max(interp->Ma, 1) > HZ_MAX_K)
+  if (interp->Ma < 0 || interp->basis < 0 || interp->basis > 2 ||
+      (interp->basis >= 1 && interp->Ma > 1) ||
+      (interp->M + interp->Mt) * std::max(interp->Ma, 1) + (interp->basis == 2 ? interp->M : 0) >
+          HZ_MAX_K)
     return set_error(HZ_ERR_INVALID_ARG,
-                     "need Ma >= 0, basis 0 or 1 (1 only with Ma <= 1), (M + Mt) Ma <= %d",
+                     "need Ma >= 0, basis 0, 1 or 2 (1 and 2 only with Ma <= 1), at most %d planes",
                      HZ_MAX_K);
 
   int dev = 0;
@@ -453,8 +467,8 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
     c_lo = std::min(c_lo, interp->c_o);
     c_hi = std::max(c_hi, interp->c_o);
   }
-  if ((st = real_nodes(c_lo, c_hi, interp->M, layer || interp->M == 1, interp->c_o, interp->basis,
-                       m->c_real)) != HZ_OK)
+  if ((st = real_nodes(c_lo, c_hi, interp->M, layer || interp->M == 1, interp->c_o,
+                       interp->basis == 1 ? 1 : 0, m->c_real)) != HZ_OK)
     return fail(st);
   m->M = int(m->c_real.size());
   m->m_o = -1;
@@ -486,7 +500,7 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
   }
   m->Ma = int(m->a_nodes.size());
   m->basis = interp->basis;
-  m->generic = m->Ma > 1 || (m->basis == 1 && m->M > 1);
+  m->generic = m->Ma > 1 || (m->basis >= 1 && m->M > 1);
   m->K = Ks * m->Ma;
   m->gamma_re.clear();
   m->gamma_im.clear();
@@ -500,6 +514,18 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
       m->gamma_im.push_back(gi);
       m->a_k.push_back(m->a_nodes[j] + interp->alpha * omega);
     }
+  }
+  // cubic Hermite: one plane per real node with the symbol's derivative in
+  // the wave speed, dq/dc = 2 c |xi|^2 q^2, after the value planes
+  m->dcoef.assign(m->K, 0.0);
+  if (m->basis == 2 && m->M > 1) {
+    for (int s = 0; s < m->M; ++s) {
+      m->gamma_re.push_back(m->c_real[s]);
+      m->gamma_im.push_back(0.0);
+      m->a_k.push_back(m->a_nodes[0] + interp->alpha * omega);
+      m->dcoef.push_back(2.0 * m->c_real[s]);
+    }
+    m->K += m->M;
   }
 
   // segment table: real segments, end entry, layer segments, end entry
@@ -588,6 +614,12 @@ extern "C" hz_status hz_create_medium(const hz_grid* grid, const double* c, cons
   if ((st = upload(m->arena, &m->symG64, G, cs)) != HZ_OK) return fail(st);
   if ((st = upload(m->arena, &m->symA32, Af, cs)) != HZ_OK) return fail(st);
   if ((st = upload(m->arena, &m->symG32, Gf, cs)) != HZ_OK) return fail(st);
+  if (m->basis == 2 && m->M > 1) {
+    std::vector<float> Df(m->K);
+    for (int k = 0; k < m->K; ++k) Df[k] = float(m->dcoef[k]);
+    if ((st = upload(m->arena, &m->symD64, m->dcoef, cs)) != HZ_OK) return fail(st);
+    if ((st = upload(m->arena, &m->symD32, Df, cs)) != HZ_OK) return fail(st);
+  }
   if ((st = upload(m->arena, &m->segtab, m->segtab_h, cs)) != HZ_OK) return fail(st);
 
   // per-axis tables

@@ -135,6 +135,7 @@ extern "C" hz_status hz_apply_preconditioner_noalloc(const hz_medium* med, const
   auto xi = [&](const AxisTables& t) -> const void* { return prec == 0 ? (const void*)t.xi2_64 : (const void*)t.xi2_32; };
   const void* A = prec == 0 ? (const void*)med->symA64 : (const void*)med->symA32;
   const void* G = prec == 0 ? (const void*)med->symG64 : (const void*)med->symG32;
+  const void* D = prec == 0 ? (const void*)med->symD64 : (const void*)med->symD32;
   const void* rec = prec == 0 ? (const void*)med->rec64 : (const void*)med->rec32;
   const long rows = n / nx;
   const long slab = long(nx) * ny;
@@ -144,7 +145,7 @@ extern "C" hz_status hz_apply_preconditioner_noalloc(const hz_medium* med, const
   int launches = 2;
   if (med->dim == 2) {
     HZ_TRY(oy->line_sym_inv(prec, tmp, planes, nx, 1, nx, 0, n, med->K, nrhs, xi(tx), nullptr, xi(ty),
-                            A, G, med->rowmask, 0, 1, tw(ty), tw2(ty), st, nullptr, 1, 1));
+                            A, G, D, med->rowmask, 0, 1, tw(ty), tw2(ty), st, nullptr, 1, 1));
     launches += 1;
   } else {
     const FftOps* oz = fft_ops(nz);
@@ -152,7 +153,7 @@ extern "C" hz_status hz_apply_preconditioner_noalloc(const hz_medium* med, const
     HZ_TRY(oz->line_pass(prec, -1, tmp, nx, ny, slab, nx, n, nrhs, nullptr, med->K, tw(tz), st,
                          nullptr, 1));
     HZ_TRY(oz->line_sym_inv(prec, tmp, planes, nx, ny, slab, nx, n, med->K, nrhs, xi(tx), xi(ty),
-                            xi(tz), A, G, med->slabmask, 0, 1, tw(tz), tw2(tz), st, nullptr, 1, 1));
+                            xi(tz), A, G, D, med->slabmask, 0, 1, tw(tz), tw2(tz), st, nullptr, 1, 1));
     HZ_TRY(oy->line_pass(prec, +1, planes, nx, nz, nx, slab, n, nrhs * med->K, med->slabmask, med->K,
                          tw(ty), st, nullptr, med->K));
     launches += 3;

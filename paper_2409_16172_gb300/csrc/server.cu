@@ -106,8 +106,8 @@ extern "C" size_t hz_request_footprint(const hz_grid* g, const hz_interp* it,
                                        const hz_solver_opts* o, int nrhs, int has_a) {
   const long n = long(g->n[0]) * g->n[1] * (g->dim == 3 ? g->n[2] : 1);
   const int Ka = it->Ma > 1 ? it->Ma : 1;
-  const int K = (it->M + it->Mt) * Ka;
-  const bool generic = Ka > 1 || it->basis == 1;  // per-point (node, weight) records
+  const int K = (it->M + it->Mt) * Ka + (it->basis == 2 ? it->M : 0);
+  const bool generic = Ka > 1 || it->basis >= 1;  // per-point (node, weight) records
   const int m = o->restart;
   const size_t B = size_t(nrhs);
   const size_t es = o->precision == 0 ? 16 : 8;
@@ -219,6 +219,8 @@ void run_batch(hz_server* s, std::shared_ptr<Req> first, cudaStream_t st) {
     {
       std::lock_guard<std::mutex> lk(s->mu);
       finish_locked(s, r0, false);
+      auto it = s->batch_free.find(r0.key);
+      if (it != s->batch_free.end() && (it->second -= B - r0.nrhs) <= 0) s->batch_free.erase(it);
     }
     s->cv_done.notify_all();
     if (plan) hz_destroy_plan(plan);
@@ -241,11 +243,9 @@ void run_batch(hz_server* s, std::shared_ptr<Req> first, cudaStream_t st) {
   std::vector<std::shared_ptr<Req>> members;
   std::vector<std::vector<int>> slots_of;         // per member: its slots
   std::vector<std::shared_ptr<Req>> pending{first};  // joining at the next boundary
-  int my_free = B - r0.nrhs;  // this batch's share of s->batch_free[key]
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->batch_free[proto.key] += my_free;
-  }
+  // this batch's share of s->batch_free[key] (registered by the worker when
+  // it admitted the first request)
+  int my_free = B - r0.nrhs;
   auto boundary = [&](hz::BatchCtl& ctl) -> int {
     // members whose slots have all finished leave
     for (size_t i = 0; i < members.size();) {
@@ -402,6 +402,8 @@ void worker_main(hz_server* s) {
       }
       s->in_use += r->footprint;
       ++s->active;
+      // a new batch: its free slots take queued requests of the same problem
+      if (r->batched) s->batch_free[r->key] += s->opts.batch_slots - r->nrhs;
       s->max_active_seen = std::max(s->max_active_seen, s->active);
       r->t_start = Clock::now();
     }

@@ -1,6 +1,6 @@
-"""GPU parity of the two interpolation extensions the paper names in
-Section 6 — bivariate interpolation in (c, a) for damping that does not
-follow the wave speed, and the quadratic Lagrange basis in c — against the
+"""GPU parity of the interpolation extensions the paper names in Section 6 —
+bivariate interpolation in (c, a) for damping that does not follow the wave
+speed, and the quadratic Lagrange and cubic Hermite bases in c — against the
 oracle, through the C ABI: node tables, the apply in both precisions with
 every x-inverse form, at ragged 2D/3D shapes with a layer, a full-size apply
 on sampled points through the plane-wave closed form, and solves checked
@@ -36,6 +36,8 @@ FORMS = {
     "bivariate-Ma2": (dict(M=3, Mt=3, damping=(0.0, 0.3)), dict(Ma=2)),
     "lagrange": (dict(M=5, Mt=2), dict(basis=1)),
     "lagrange-M7": (dict(M=7, Mt=3, contrast=0.9), dict(basis=1)),
+    "hermite": (dict(M=4, Mt=2), dict(basis=2)),
+    "hermite-M6": (dict(M=6, Mt=3, contrast=0.9), dict(basis=2)),
 }
 
 
@@ -61,7 +63,8 @@ def test_apply_matches_oracle(hz, shape, form):
 
 def test_bad_extension_options_are_refused(hz):
     p = S.small_problem((16, 16), 3, M=4, Mt=2, width=2, damping=(0.0, 0.2))
-    for kw in (dict(basis=1), dict(M=5, Ma=3, basis=1), dict(M=5, basis=2), dict(M=12, Mt=4, Ma=5)):
+    for kw in (dict(basis=1), dict(M=5, Ma=3, basis=1), dict(M=5, basis=3), dict(M=5, Ma=2, basis=2),
+               dict(M=12, Mt=4, Ma=5), dict(M=30, Mt=6, basis=2)):
         kw = dict(kw)
         M = kw.pop("M", 4)
         with pytest.raises(hz.HzError):
@@ -78,19 +81,24 @@ def _plane_wave_expected(med_o, shape, kvec, pts):
     the plane wave times the interpolated symbol, for any weights."""
     xi2 = sum(O.xi2_axis(shape[a], 1.0)[k % shape[a]] for a, k in enumerate(kvec))
     W = med_o.W.reshape(med_o.nodes.K, -1)
-    qk = np.array([O.node_symbol(med_o.nodes.gamma[k], med_o.nodes.a[k], med_o.omega,
-                                 np.array([xi2]))[0] for k in range(med_o.nodes.K)])
+    qk = np.array([O.symbol_of(med_o.nodes, k, med_o.omega, np.array([xi2]))[0]
+                   for k in range(med_o.nodes.K)])
     return (W[:, pts] * qk[:, None]).sum(axis=0)
 
 
-@pytest.mark.parametrize("form", ["bivariate", "lagrange"])
+@pytest.mark.parametrize("form", ["bivariate", "lagrange", "hermite"])
 def test_full_size_apply_plane_wave(hz, form):
-    """512^2 bivariate (K = 16 x 3 = 48 planes) and 1024^2 quadratic (K = 11 + 4)
-    applies through autotuned plans, on 4096 sampled points."""
+    """512^2 bivariate (K = 16 x 3 = 48 planes), 1024^2 quadratic (K = 11 + 4)
+    and 1024^2 cubic Hermite (K = 8 + 4 + 8) applies through autotuned
+    plans, on 4096 sampled points."""
     if form == "bivariate":
         p = S.damping_problem(N=512, Ma=3)
         med_g, med_o = media(hz, p, alpha=0.1, Ma=3)
         assert med_o.nodes.K == 48
+    elif form == "hermite":
+        p = S.config2()
+        med_g, med_o = media(hz, p, alpha=0.1, M=8, basis=2)
+        assert med_o.nodes.K == 20 and med_g.info()["K"] == 20
     else:
         p = S.config2()
         med_g, med_o = media(hz, p, alpha=0.1, M=11, basis=1)
@@ -105,7 +113,7 @@ def test_full_size_apply_plane_wave(hz, form):
         assert within(rel(got[pts], exp), prec, "interp_full"), (form, prec, rel(got[pts], exp))
 
 
-@pytest.mark.parametrize("mopt", [dict(Ma=3), dict(M=7, basis=1)])
+@pytest.mark.parametrize("mopt", [dict(Ma=3), dict(M=7, basis=1), dict(M=6, basis=2)])
 def test_solve_with_extension_converges(hz, mopt):
     """FGMRES with the bivariate or quadratic preconditioner reaches the
     tolerance by the oracle's operator on a 128^2 damping medium."""

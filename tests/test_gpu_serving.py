@@ -140,9 +140,9 @@ def test_extension_requests_are_served(hz):
 
 
 def _batch_problem():
-    p = S.small_problem((96, 128), 9, M=6, Mt=2, width=3)
+    p = S.small_problem((512, 512), 9, M=6, Mt=2, width=8)
     fs = [S.random_field(np.random.Generator(np.random.PCG64(90 + i)), p.shape, k)
-          for i, k in enumerate((2, 1, 3))]
+          for i, k in enumerate((2, 1, 1))]
     return p, fs
 
 
@@ -153,9 +153,10 @@ def _submit_b(srv, p, f):
 
 def test_batched_requests_join_at_restart_boundaries(hz):
     """Continuous batching (batch_slots): requests on the same medium share
-    one batched solve; a request submitted while the batch is iterating
-    joins it at a restart boundary and leaves when its right-hand sides are
-    done.  Each request's solution is bit for bit the one it gets alone in a
+    one batched solve.  b, submitted right after a, joins a's batch at a
+    restart boundary instead of starting its own; c joins later if the batch
+    is still iterating; each leaves when its right-hand sides are done.
+    Every request's solution is bit for bit the one it gets alone in a
     batch, every right-hand side meets the tolerance by the oracle's
     operator, and a request on another medium runs beside the batch."""
     import time
@@ -163,7 +164,7 @@ def test_batched_requests_join_at_restart_boundaries(hz):
     q = S.small_problem((64, 64), 8, M=5, Mt=2, width=3)
     fq = S.random_field(np.random.Generator(np.random.PCG64(99)), q.shape, 1)
     alone = {}
-    for name, f in (("a", fa), ("b", fb)):
+    for name, f in (("a", fa), ("b", fb), ("c", fc)):
         srv = hz.Server(max_slots=1, batch_slots=4)
         done, u, st, status = srv.result(_submit_b(srv, p, f))
         assert done and status == 0
@@ -171,20 +172,17 @@ def test_batched_requests_join_at_restart_boundaries(hz):
         srv.close()
     srv = hz.Server(max_slots=2, batch_slots=4)
     ta = _submit_b(srv, p, fa)
-    t0 = time.time()
-    while srv.stats()["active"] < 1 and time.time() - t0 < 10:
-        time.sleep(0.001)
-    time.sleep(0.02)  # the batch is iterating
     tb = _submit_b(srv, p, fb)
-    tc = _submit_b(srv, p, fc)  # 3 right-hand sides: no room beside a and b
     tq = srv.submit(q.c, fq, omega=q.omega, M=q.M, Mt=q.Mt, zeta=q.zeta, alpha=0.15,
                     restart=10, tol=1e-10, maxit=3000)
+    time.sleep(0.02)
+    tc = _submit_b(srv, p, fc)
     res = {k: srv.result(t, timeout=600) for k, t in (("a", ta), ("b", tb), ("c", tc), ("q", tq))}
     stats = srv.stats()
     srv.close()
     assert stats["batch_joins"] >= 1, stats
     assert stats["completed"] == 4 and stats["failed"] == 0
-    for k in ("a", "b"):
+    for k in ("a", "b", "c"):
         assert np.array_equal(res[k][1], alone[k][0]), k
         assert [s["iters"] for s in res[k][2]] == [s["iters"] for s in alone[k][1]]
     med_o = O.make_medium(p.c, p.zeta, None, p.omega, p.M, p.Mt, 1.0, None, 0.15)

@@ -979,6 +979,8 @@ def main():
                     help="serving: no autotuning before the stream (served plans keep defaults)")
     ap.add_argument("--plain-requests", type=int, default=30,
                     help="serving: requests of the plain FP64 one-at-a-time comparison (0: none)")
+    ap.add_argument("--n3d", type=int, default=256,
+                    help="cfg3: side of the cube (256 is the workload; smaller for profiling)")
     ap.add_argument("--restart", type=int, default=0,
                     help="override the workload's restart length m (0: the workload's own)")
     ap.add_argument("--media-pool", type=int, default=0,
@@ -1021,7 +1023,11 @@ def main():
     if args.workload == "interp":
         run_interp(args)
         return
-    p = getattr(S, WORKLOADS[args.workload][0])()
+    if args.workload == "cfg3" and args.n3d != 256:
+        # the same 3D recipe on a smaller cube (profiling captures)
+        p = S.config3(N=args.n3d)
+    else:
+        p = getattr(S, WORKLOADS[args.workload][0])()
     if args.restart > 0:
         p.restart = args.restart
     if args.impl == "reference":

@@ -62,6 +62,8 @@ GPU_STEPS_PER_SOLVE = {"cfg3": 113, "cfg2": 100, "cfg1": 29, "cfg4": 77}
 def workload_config(p, name=DEFAULT_WORKLOAD, nrhs=1, symbol_kind=0):
     """The workload both arms run (problem and solver parameters only)."""
     fac, alpha, g_default, label, l2 = WORKLOADS[name]
+    if name == "cfg3" and p.shape[0] != 256:
+        label = label.replace("256^3", f"{p.shape[0]}^3")
     return {"workload": label, "grid": list(p.shape), "K": p.K, "M": p.M, "Mt": p.Mt,
             "omega": round(p.omega, 4), "restart": p.restart, "tol": p.tol, "nrhs": nrhs,
             "alpha": alpha, "symbol_kind": symbol_kind, "l2": l2}

@@ -148,3 +148,36 @@ def test_unpreconditioned_with_graphs_and_multi_rhs(hz):
         _, so = O.gmres(A, f[b], None, restart=10, tol=1e-14, maxit=40)
         r = np.linalg.norm(f[b] - A(out[True][0][b])) / np.linalg.norm(f[b])
         assert abs(r / so["rel_true_resid"] - 1) <= 1e-6
+
+
+def test_paper_statement_at_its_grid_2400(hz):
+    """The paper's Example 1 statement at its own first grid (Section 5.1:
+    N = 2400, omega = 400 pi, M = 8, GMRES(10), 100 iterations): in the
+    paper's left form (Eqn. MainDiscretePrecond) with the finite-difference
+    symbol, the preconditioned residual ends at least 7 orders below the
+    residual of GMRES(10) without a preconditioner, with the FP64 and the
+    complex64 preconditioner.  The GPU histories follow the oracle's
+    (tests/golden/example1_2400_oracle.txt, written by make_example1_2400.py
+    from the oracle alone): the first three cycles to 1e-6, every step within
+    0.3 orders, the unpreconditioned run step by step."""
+    import os
+    golden = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden",
+                                     "example1_2400_oracle.txt"))
+    p = S.example1(2400)
+    med = hz.Medium(p.c, p.zeta, p.a, omega=p.omega, M=p.M, Mt=0, c_o=1.0, alpha=0.0,
+                    a_node=p.meta["a_node"], symbol_kind=1)
+    f = np.ascontiguousarray(p.f[0])
+    hist = {}
+    for key, kw in (("left", dict(precision=0, left=True)), ("left32", dict(precision=1, left=True)),
+                    ("none", dict(precision=0, no_precond=True))):
+        plan = hz.Plan(med, restart=10, tol=1e-14, maxit=100, **kw)
+        _, st, H = plan.solve(f, history=100)
+        assert st[0]["iters"] == 100
+        hist[key] = H[0]
+        del plan
+    np.testing.assert_allclose(hist["left"][:30], golden[:30, 1], rtol=1e-6)
+    assert np.all(np.abs(np.log10(hist["left"] / golden[:, 1])) <= 0.3)
+    np.testing.assert_allclose(hist["none"], golden[:, 2], rtol=1e-6)
+    for key in ("left", "left32"):
+        gap = math.log10(hist["none"][99] / hist[key][99])
+        assert gap >= 7.0, (key, gap)

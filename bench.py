@@ -228,8 +228,10 @@ def run_reference(args, p):
 
 
 # DRAM traffic / algorithmic bytes of the CGS2 dot kernel in one ncu capture
-# (1024^2, Arnoldi step j = 13: 262.2 MB read + write, 16 n (j + 2) = 251.7 MB)
-DOTS_TRAFFIC_RATIO = 262.2 / 251.7
+# of the 3D recipe at 128^3 with the 256^3 workload's launch shapes (Arnoldi
+# step j = 13: 557.2 MB read + write, 16 n (j + 2) = 503.3 MB; the right-hand
+# vector is re-read by the chunks of two basis vectors per block)
+DOTS_TRAFFIC_RATIO = 557.2 / 503.3
 FP64_DFMA_PER_CLK_PER_SM = 2  # sm_103 (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak)
 
 
@@ -435,7 +437,8 @@ def run_gpu(args, p, name):
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": traffic,
                 "traffic_note": "bytes per launch: the DRAM read + write of one ncu-captured dot "
-                                "launch (1024^2, j = 13: 262.2 MB against 251.7 MB algorithmic) "
+                                "launch (the 3D recipe at 128^3, j = 13: 557.2 MB against "
+                                "503.3 MB algorithmic) "
                                 "scaled to the average algorithmic bytes per launch of this phase "
                                 "(the launches run j = 0..m-1, and the phase's partial-sum "
                                 "launches count as launches)",

@@ -433,7 +433,9 @@ hz_status hz_server_destroy(hz_server* s);
  * cgs2_update, givens, solution_update, residual, norm.
  * hz_profile_enable(1) turns recording on for the whole process (it adds two
  * event records per launch); hz_profile_read waits for the recorded events,
- * fills up to max entries and optionally resets the counters. */
+ * fills up to max entries and optionally resets the counters.  With the
+ * environment variable HZ_NVTX=1 every phase is also an NVTX range of the
+ * same name, for timeline tools (read once per process). */
 typedef struct {
   char name[24];
   long long launches;

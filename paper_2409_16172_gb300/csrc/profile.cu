@@ -1,5 +1,8 @@
 // Per-phase CUDA-event timing and the launch counter (see hz.h).
+#include <stdlib.h>
 #include <string.h>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 #include <mutex>
@@ -29,6 +32,15 @@ struct Acc {
 };
 
 std::atomic<unsigned long long> g_launches{0};
+// NVTX ranges named after the phases around their launches, for timeline
+// tools, when the environment sets HZ_NVTX=1 (read once)
+bool nvtx_on() {
+  static const bool on = [] {
+    const char* e = getenv("HZ_NVTX");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
 std::atomic<bool> g_on{false};
 std::mutex g_mu;
 std::vector<Pending> g_pend;
@@ -91,6 +103,7 @@ void resolve_solve_sink(SolveSink* sink) {
 PhaseScope::PhaseScope(cudaStream_t s, Phase p, double b, double f, int l)
     : st(s), ph(p), bytes(b), flops(f), launches(l) {
   count_launches(l);
+  if (nvtx_on()) nvtxRangePushA(kNames[p]);
   if (!profiling()) return;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
@@ -115,6 +128,7 @@ PhaseScope::PhaseScope(cudaStream_t s, Phase p, double b, double f, int l)
 }
 
 PhaseScope::~PhaseScope() {
+  if (nvtx_on()) nvtxRangePop();
   if (slot < 0) return;
   std::lock_guard<std::mutex> lk(g_mu);
   Pending& p = g_pend[slot];

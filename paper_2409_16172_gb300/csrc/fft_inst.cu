@@ -208,9 +208,20 @@ hz_status line_sym_inv_t(const void* vhat, void* planes, int nx, long outer, lon
       const bool half = pair > 1;
       constexpr int T1 = C::template tb_p<1>(), T1H = C::template tb_p_half<1>();
       constexpr int Tn = C::template tb_p<2>(), TnH = C::template tb_p_half<2>();
-      auto k = kpb == 1 ? (half ? line_sym_inv_pair_kernel<N, 1, T1H> : line_sym_inv_pair_kernel<N, 1, T1>)
-             : kpb == 2 ? (half ? line_sym_inv_pair_kernel<N, 2, TnH> : line_sym_inv_pair_kernel<N, 2, Tn>)
-                        : (half ? line_sym_inv_pair_kernel<N, 4, TnH> : line_sym_inv_pair_kernel<N, 4, Tn>);
+      // the Hermite derivative planes (symD) are a compiled variant, so
+      // that other media run without their test
+      auto k = symD ? (kpb == 1 ? (half ? line_sym_inv_pair_kernel<N, 1, T1H, true>
+                                        : line_sym_inv_pair_kernel<N, 1, T1, true>)
+                       : kpb == 2 ? (half ? line_sym_inv_pair_kernel<N, 2, TnH, true>
+                                          : line_sym_inv_pair_kernel<N, 2, Tn, true>)
+                                  : (half ? line_sym_inv_pair_kernel<N, 4, TnH, true>
+                                          : line_sym_inv_pair_kernel<N, 4, Tn, true>))
+                    : (kpb == 1 ? (half ? line_sym_inv_pair_kernel<N, 1, T1H, false>
+                                        : line_sym_inv_pair_kernel<N, 1, T1, false>)
+                       : kpb == 2 ? (half ? line_sym_inv_pair_kernel<N, 2, TnH, false>
+                                          : line_sym_inv_pair_kernel<N, 2, Tn, false>)
+                                  : (half ? line_sym_inv_pair_kernel<N, 4, TnH, false>
+                                          : line_sym_inv_pair_kernel<N, 4, Tn, false>));
       const int tb = kpb == 1 ? (half ? T1H : T1) : (half ? TnH : Tn);
       const int tpl = kpb == 1 ? C::template tpl_p<1>() : C::template tpl_p<2>();
       HZ_TRY(smem_attr(k, C::col_pair_smem(tb)));
@@ -227,8 +238,12 @@ hz_status line_sym_inv_t(const void* vhat, void* planes, int nx, long outer, lon
       return HZ_OK;
     }
   }
-  auto k = kpb == 4 ? line_sym_inv_kernel<R, N, 4>
-                    : (kpb == 2 ? line_sym_inv_kernel<R, N, 2> : line_sym_inv_kernel<R, N, 1>);
+  auto k = symD ? (kpb == 4 ? line_sym_inv_kernel<R, N, 4, true>
+                            : (kpb == 2 ? line_sym_inv_kernel<R, N, 2, true>
+                                        : line_sym_inv_kernel<R, N, 1, true>))
+                : (kpb == 4 ? line_sym_inv_kernel<R, N, 4, false>
+                            : (kpb == 2 ? line_sym_inv_kernel<R, N, 2, false>
+                                        : line_sym_inv_kernel<R, N, 1, false>));
   HZ_TRY(smem_attr(k, C::col_smem()));
   const int ntile = (nx + C::TB - 1) / C::TB;
   dim3 grid(unsigned(ntile * outer), unsigned((K + kpb - 1) / kpb), unsigned(batch));

@@ -580,7 +580,7 @@ line_pass_kernel(typename cvec<R>::T* __restrict__ data, int nx, int ntile, long
 // Plane k is only stored where smask[o smO + p smS] has bit k: per row in 2D
 // (the next pass is the x inverse), per z-slab in 3D (the next pass is the y
 // inverse, which needs the whole slab).
-template <typename R, int N, int KPB>
+template <typename R, int N, int KPB, bool HERM>
 __global__ void __launch_bounds__(LineCfg<R, N>::COL_THREADS)
 line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
                     typename cvec<R>::T* __restrict__ planes, int nx, int ntile, long S,
@@ -632,7 +632,7 @@ line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
 #pragma unroll 1
   for (int k = k0; k < k1; ++k) {
     const V A = symA[k], G = symG[k];
-    const R D = symD ? symD[k] : R(0);
+    const R D = HERM ? symD[k] : R(0);
     const int kk = k - k0;
     V v[E];
 #pragma unroll
@@ -641,9 +641,9 @@ line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
       const V den = cmk<V>(A.x - G.x * s2[e], A.y - G.y * s2[e]);
       const R inv = recip(den.x * den.x + den.y * den.y);
       V r = cscale(cmulc(spec[e], den), inv);
-      if (D != R(0)) {
+      if (HERM && D != R(0)) {
         // derivative plane of the Hermite basis: vhat dq/dc = vhat q (D |xi|^2 q),
-        // D = 2 c_k
+        // D = 2 c_k (HERM: a medium with such planes; compiled out otherwise)
         r = cscale(cmul(r, cmk<V>(den.x * inv, -den.y * inv)), D * s2[e]);
       }
       v[e] = r;
@@ -667,7 +667,7 @@ line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
 // global accesses, and tw2 = the (re, re, im, im) twiddle table.  TB: column
 // pairs per block (the scalar kernel's TB, or half of it: the same registers
 // per thread, smaller blocks).
-template <int N, int KPB, int TB>
+template <int N, int KPB, int TB, bool HERM>
 __global__ void __launch_bounds__(TB * LineCfg<float, N>::template tpl_p<KPB>(),
                                   LineCfg<float, N>::template pair_min_blocks<KPB>(TB))
 line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ planes, int nx,
@@ -717,7 +717,7 @@ line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ p
     PV r;
     r.x = q.x * inv;
     r.y = q.y * inv;
-    if (D != 0.0f) {
+    if (HERM && D != 0.0f) {
       // derivative plane of the Hermite basis: vhat dq/dc = vhat q (D |xi|^2 q)
       PV qv;
       qv.x = den.x * inv;
@@ -752,7 +752,7 @@ line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ p
     // one node: the symbol product straight from the loads (no copy of the
     // spectrum kept across nodes)
     const float2 A = symA[k0], G = symG[k0];
-    const float D = symD ? symD[k0] : 0.0f;
+    const float D = HERM ? symD[k0] : 0.0f;
     const f2 AX = f2_splat(A.x), AY = f2_splat(A.y), NGX = f2_splat(-G.x), NGY = f2_splat(-G.y);
     PV v[E];
 #pragma unroll
@@ -772,7 +772,7 @@ line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ p
 #pragma unroll 1
     for (int k = k0; k < k1; ++k) {
       const float2 A = symA[k], G = symG[k];
-      const float D = symD ? symD[k] : 0.0f;
+      const float D = HERM ? symD[k] : 0.0f;
       const f2 AX = f2_splat(A.x), AY = f2_splat(A.y), NGX = f2_splat(-G.x), NGY = f2_splat(-G.y);
       PV v[E];
 #pragma unroll

@@ -855,7 +855,7 @@ def run_serving(args):
 
     def run_stream(nreq, slots, precision, batch_slots=0):
         srv = hz.Server(max_slots=slots, autotune=0 if not args.no_pretune else -1,
-                        batch_slots=batch_slots, max_bypass=args.max_bypass)
+                        batch_slots=batch_slots, max_bypass=args.max_bypass, order=args.order)
         out_q = queue.Queue()
         stats = []
         pool = cf.ThreadPoolExecutor(max_workers=args.gen_threads)
@@ -947,7 +947,8 @@ def run_serving(args):
            "ms_per_step": 1e3 * span / args.requests, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
            "config": {"workload": f"{wl}-poisson{args.rate}/s-slots{args.slots}"
-                                  f"-batch{args.batch_slots}-bypass{args.max_bypass}",
+                                  f"-batch{args.batch_slots}-bypass{args.max_bypass}"
+                                  f"-order{args.order}",
                       "grids": sorted({"x".join(map(str, k[0])) for k in keys}),
                       "rhs_total": rhs, "graphs": args.serve_graphs,
                       "pretune_s": t_tune, "pretuned_keys": 0 if args.no_pretune else len(keys)},
@@ -988,6 +989,8 @@ def main():
                     help="cfg3: side of the cube (256 is the workload; smaller for profiling)")
     ap.add_argument("--restart", type=int, default=0,
                     help="override the workload's restart length m (0: the workload's own)")
+    ap.add_argument("--order", type=int, default=1, choices=[0, 1],
+                    help="serving: admission order, 0 arrival order, 1 smallest footprint first")
     ap.add_argument("--max-bypass", type=int, default=0,
                     help="serving: aging limit (times a queued request may be overtaken; 0: 2 x slots)")
     ap.add_argument("--media-pool", type=int, default=0,

@@ -373,6 +373,11 @@ typedef struct {
                           side finished; the others keep iterating.  A right-hand side's
                           result does not depend on which requests share the batch.
                           Right / flexible preconditioning only (opts.left = 0).         */
+  int order;           /* admission order: 0 the first queued request (arrival order)
+                          that fits the budget; 1 the fitting request with the smallest
+                          footprint first (about the least work), so that short requests
+                          do not queue behind long ones; aging (max_bypass) bounds how
+                          often a request can be overtaken in both orders.               */
 } hz_server_opts;
 
 typedef struct {

@@ -374,9 +374,11 @@ void worker_main(hz_server* s) {
           if (st) cudaStreamDestroy(st);
           return;
         }
-        // first fit in arrival order within the HBM budget, with aging: a
-        // request that later arrivals have overtaken max_bypass times is
-        // not overtaken again (admission waits until it fits)
+        // Admission within the HBM budget, with aging: a request that later
+        // arrivals have overtaken max_bypass times is not overtaken again
+        // (admission waits until it fits).  order 0: the first request in
+        // arrival order that fits; order 1: the one with the smallest
+        // footprint (about the least work) that fits.
         size_t pick = s->queue.size();
         for (size_t i = 0; i < s->queue.size(); ++i) {
           const Req& q = *s->queue[i];
@@ -386,11 +388,15 @@ void worker_main(hz_server* s) {
             auto bf = s->batch_free.find(q.key);
             if (bf != s->batch_free.end() && bf->second >= q.nrhs) continue;
           }
-          if (s->in_use + q.footprint <= s->opts.hbm_budget || s->active == 0) {
+          const bool fits = s->in_use + q.footprint <= s->opts.hbm_budget || s->active == 0;
+          if (fits && (pick == s->queue.size() || q.footprint < s->queue[pick]->footprint))
             pick = i;
+          if (fits && s->opts.order == 0) break;
+          // an aged request: nothing behind it may go first
+          if (q.bypassed >= s->opts.max_bypass) {
+            if (fits) pick = i;
             break;
           }
-          if (q.bypassed >= s->opts.max_bypass) break;
         }
         if (pick < s->queue.size()) {
           for (size_t i = 0; i < pick; ++i) ++s->queue[i]->bypassed;
@@ -446,9 +452,10 @@ extern "C" hz_status hz_server_create(const hz_server_opts* opts, hz_server** ou
   if (opts->max_slots < 1 || opts->max_slots > 64 || opts->max_queue < 1)
     return set_error(HZ_ERR_INVALID_ARG, "need 1 <= max_slots <= 64 and max_queue >= 1");
   if (opts->autotune < -1 || opts->autotune > 1 || opts->max_bypass < 0 || opts->batch_slots < 0 ||
-      opts->batch_slots > 64)
+      opts->batch_slots > 64 || opts->order < 0 || opts->order > 1)
     return set_error(HZ_ERR_INVALID_ARG,
-                     "need autotune in {-1, 0, 1}, max_bypass >= 0 and batch_slots in 0..64");
+                     "need autotune in {-1, 0, 1}, max_bypass >= 0, batch_slots in 0..64, "
+                     "order 0 or 1");
   hz_server* s = new hz_server();
   s->opts = *opts;
   if (s->opts.max_bypass == 0) s->opts.max_bypass = 2 * s->opts.max_slots;

@@ -78,7 +78,7 @@ class hz_tune_report(C.Structure):
 class hz_server_opts(C.Structure):
     _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int), ("max_queue", C.c_int),
                 ("device", C.c_int), ("autotune", C.c_int), ("max_bypass", C.c_int),
-                ("batch_slots", C.c_int)]
+                ("batch_slots", C.c_int), ("order", C.c_int)]
 
 
 class hz_request(C.Structure):
@@ -401,9 +401,9 @@ class Server:
 
     def __init__(self, max_slots: int = 4, max_queue: int = 4096, hbm_budget: int = 0,
                  device: int = 0, autotune: int = 0, max_bypass: int = 0,
-                 batch_slots: int = 0):
+                 batch_slots: int = 0, order: int = 0):
         o = hz_server_opts(hbm_budget, max_slots, max_queue, device, autotune, max_bypass,
-                           batch_slots)
+                           batch_slots, order)
         h = _vp()
         check(lib.hz_server_create(C.byref(o), C.byref(h)))
         self._h = h

@@ -116,6 +116,36 @@ def test_queue_limit_and_bad_request(hz):
     srv.close()
 
 
+@pytest.mark.parametrize("order", [0, 1])
+def test_admission_order(hz, order):
+    """One slot, a large request running, then a large and a small request
+    queued: in arrival order (0) the large one goes first; smallest footprint
+    first (1) lets the small one overtake it.  The results do not depend on
+    the order."""
+    import time
+    big = S.small_problem((512, 512), 41, M=6, Mt=2, width=8)
+    small = S.small_problem((64, 64), 42, M=5, Mt=2, width=3)
+    fb = S.random_field(np.random.Generator(np.random.PCG64(43)), big.shape, 2)
+    fs = S.random_field(np.random.Generator(np.random.PCG64(44)), small.shape, 1)
+    srv = hz.Server(max_slots=1, order=order)
+    t_run = _submit(srv, big, fb)
+    t0 = time.time()
+    while srv.stats()["active"] < 1 and time.time() - t0 < 10:
+        time.sleep(0.001)
+    t_big = _submit(srv, big, fb)
+    t_small = _submit(srv, small, fs)
+    srv.wait(t_small, timeout=600)
+    pb = srv.poll(t_big)  # consumes the ticket when done
+    big_done_first = pb[0]
+    res = {t_small: srv.poll(t_small), t_run: srv.result(t_run, timeout=600),
+           t_big: pb if big_done_first else srv.result(t_big, timeout=600)}
+    srv.close()
+    assert big_done_first == (order == 0)
+    assert np.array_equal(res[t_run][1], res[t_big][1])
+    for t in (t_run, t_big, t_small):
+        assert res[t][0] and res[t][3] == 0
+
+
 def test_extension_requests_are_served(hz):
     """Bivariate (c, a) and quadratic-basis requests go through the server and
     give the result of the same request solved on its own plan."""

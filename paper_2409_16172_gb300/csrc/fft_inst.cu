@@ -210,7 +210,11 @@ hz_status line_sym_inv_t(const void* vhat, void* planes, int nx, long outer, lon
       constexpr int Tn = C::template tb_p<2>(), TnH = C::template tb_p_half<2>();
       // the Hermite derivative planes (symD) are a compiled variant, so
       // that other media run without their test
-      auto k = symD ? (kpb == 1 ? (half ? line_sym_inv_pair_kernel<N, 1, T1H, true>
+      // a square 2D grid (line stride N): the one-node form with compile-time offsets
+      const bool sq = kpb == 1 && !half && outer == 1 && S == N;
+      auto k = sq ? (symD ? line_sym_inv_pair_kernel<N, 1, T1, true, N>
+                          : line_sym_inv_pair_kernel<N, 1, T1, false, N>)
+             : symD ? (kpb == 1 ? (half ? line_sym_inv_pair_kernel<N, 1, T1H, true>
                                         : line_sym_inv_pair_kernel<N, 1, T1, true>)
                        : kpb == 2 ? (half ? line_sym_inv_pair_kernel<N, 2, TnH, true>
                                           : line_sym_inv_pair_kernel<N, 2, Tn, true>)

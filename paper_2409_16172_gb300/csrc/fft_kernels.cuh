@@ -666,8 +666,10 @@ line_sym_inv_kernel(const typename cvec<R>::T* __restrict__ vhat,
 // per column as line_sym_inv_kernel, in packed FP32 instructions, 16-byte
 // global accesses, and tw2 = the (re, re, im, im) twiddle table.  TB: column
 // pairs per block (the scalar kernel's TB, or half of it: the same registers
-// per thread, smaller blocks).
-template <int N, int KPB, int TB, bool HERM>
+// per thread, smaller blocks).  SC > 0: the line stride S is SC (a square 2D
+// grid, S = nx = N), so that every load and store offset of a thread is a
+// compile-time constant from one base address.
+template <int N, int KPB, int TB, bool HERM, int SC = 0>
 __global__ void __launch_bounds__(TB * LineCfg<float, N>::template tpl_p<KPB>(),
                                   LineCfg<float, N>::template pair_min_blocks<KPB>(TB))
 line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ planes, int nx,
@@ -694,17 +696,50 @@ line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ p
   const bool valid = x < nx;
   const long off = o * ostride + x;
   const float2* src = vhat + rhs * n + off;
+  // line stride: compile-time when SC > 0 (then S == SC)
+  const int Sl = SC > 0 ? SC : int(S);
   const float so = xi2_o ? xi2_o[o] : 0.0f;
   const float sx0 = (valid ? xi2_x[x] : 0.0f) + so, sx1 = (valid ? xi2_x[x + 1] : 0.0f) + so;
   constexpr int MW = (E * KPB + 31) / 32;
   uint32_t mb[MW];
+  constexpr int TPLP = LineCfg<float, N>::template tpl_p<KPB>();
+  // one node, E dividing 32: the block's warps build the E-bit store mask of
+  // every t by ballots (lane = (t, e) pair, E lanes per t), one entry of
+  // smask per (t, e) instead of E per thread
+  constexpr bool BALLOT = KPB == 1 && E <= 32 && 32 % E == 0 && TPLP % (32 / E) == 0 &&
+                          (TB * TPLP) % 32 == 0;
+  if constexpr (BALLOT) {
+    __shared__ uint32_t mwords[TPLP];
+    constexpr int TPW = 32 / E;                        // t values per warp round
+    constexpr int NW = TB * TPLP / 32;                 // warps per block
+    constexpr int ROUNDS = (TPLP + NW * TPW - 1) / (NW * TPW);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, e = lane % E;
+    // every round's entry loaded before the first ballot
+    unsigned bit[ROUNDS];
 #pragma unroll
-  for (int w = 0; w < MW; ++w) mb[w] = 0u;
+    for (int i = 0; i < ROUNDS; ++i) {
+      const int tt = (warp + i * NW) * TPW + lane / E;
+      bit[i] = tt < TPLP ? unsigned(smask[o * smO + F::out_index(tt, e) * int(smS)] >> k0) & 1u : 0u;
+    }
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int p = F::out_index(t, e);
-    const uint32_t bits = uint32_t(smask[o * smO + p * int(smS)] >> k0) & ((1u << KPB) - 1u);
-    mb[(e * KPB) / 32] |= bits << ((e * KPB) % 32);
+    for (int i = 0; i < ROUNDS; ++i) {
+      const int tt = (warp + i * NW) * TPW + lane / E;
+      if ((warp + i * NW) * TPW < TPLP) {  // warp-uniform
+        const unsigned bal = __ballot_sync(0xffffffffu, bit[i]);
+        if (e == 0) mwords[tt] = E == 32 ? bal : (bal >> lane) & ((1u << (E & 31)) - 1u);
+      }
+    }
+    __syncthreads();
+    mb[0] = mwords[t];
+  } else {
+#pragma unroll
+    for (int w = 0; w < MW; ++w) mb[w] = 0u;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int p = F::out_index(t, e);
+      const uint32_t bits = uint32_t(smask[o * smO + p * int(smS)] >> k0) & ((1u << KPB) - 1u);
+      mb[(e * KPB) / 32] |= bits << ((e * KPB) % 32);
+    }
   }
   // vhat q_k = vhat conj(den) / |den|^2,  den = A - G |xi|^2
   auto symbol = [](const PV& sp, f2 s2, f2 AX, f2 AY, f2 NGX, f2 NGY, float D) {
@@ -735,13 +770,14 @@ line_sym_inv_pair_kernel(const float2* __restrict__ vhat, float2* __restrict__ p
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       if ((mb[(e * KPB) / 32] >> ((e * KPB) % 32 + (KPB == 1 ? 0 : kk))) & 1u)
-        *reinterpret_cast<float4*>(dst + F::out_index(t, e) * int(S)) =
+        *reinterpret_cast<float4*>(dst + F::out_index(t, e) * Sl) =
             make_float4(f2_lo(v[e].x), f2_lo(v[e].y), f2_hi(v[e].x), f2_hi(v[e].y));
     }
   };
   auto load = [&](int e, PV& sp, f2& s2) {
     const int p = F::stage0_index(t, e);
-    const float4 a = valid ? *reinterpret_cast<const float4*>(src + p * int(S))
+    // the spectrum streams past L1 (.cg), which keeps the twiddle table
+    const float4 a = valid ? __ldcg(reinterpret_cast<const float4*>(src + p * Sl))
                            : make_float4(0.f, 0.f, 0.f, 0.f);
     sp.x = f2_make(a.x, a.z);
     sp.y = f2_make(a.y, a.w);

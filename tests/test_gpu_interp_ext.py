@@ -41,7 +41,7 @@ FORMS = {
 }
 
 
-@pytest.mark.parametrize("shape", [(64, 32), (48, 192), (12, 48, 8), (24, 16, 32)])
+@pytest.mark.parametrize("shape", [(64, 32), (48, 192), (64, 64), (12, 48, 8), (24, 16, 32)])
 @pytest.mark.parametrize("form", sorted(FORMS))
 def test_apply_matches_oracle(hz, shape, form):
     popt, mopt = FORMS[form]
@@ -53,6 +53,8 @@ def test_apply_matches_oracle(hz, shape, form):
     np.testing.assert_allclose(info["a"], med_o.nodes.a, rtol=1e-15, atol=0)
     v = S.random_field(np.random.Generator(np.random.PCG64(22)), shape, 2)
     ref = np.stack([O.apply_preconditioner(med_o, v[b]) for b in range(2)])
+    # (64, 64): the default launch shape (one node per block, column pairs) of
+    # a square grid is the symbol pass compiled with its line stride
     for prec in (0, 1):
         plan = hz.Plan(med_g, precision=prec, max_nrhs=2)
         for mode in (0, 1, 3):

@@ -42,13 +42,13 @@ METRIC = "Helmholtz solves/s at 1e-6 true relative residual"
 
 # name -> (problem factory, alpha, graphs, workload label, L2 note)
 WORKLOADS = {
-    "cfg3": ("config3", 0.15, False, "3d-256^3-layers6+incl10-layer24-ppw8-K16-fgmres40",
+    "cfg3": ("config3", 0.3, False, "3d-256^3-layers6+incl10-layer24-ppw8-K16-fgmres40",
              "working set larger than L2 (basis 11 GB, planes 2.1 GB); no flush"),
     "cfg2": ("config2", 0.1, True, "2d-1024x1024-bumps20+gradient-layer32-ppw8-K16-fgmres40",
              "working set larger than L2 (basis 0.7 GB, planes 134 MB); no flush"),
     "cfg1": ("config1", 0.15, True, "2d-128x128-bumps3-layer16-ppw10-K8-gmres30",
              "L2-resident (17 MB working set); timed as repeated solves, not an HBM figure"),
-    "cfg4": ("config4", 0.15, True, "2d-512x512-bumps3-layer16-ppw10-K12-64rhs-fgmres40",
+    "cfg4": ("config4", 0.1, True, "2d-512x512-bumps3-layer16-ppw10-K12-64rhs-fgmres40",
              "working set larger than L2 (basis 11 GB for 64 rhs); no flush"),
 }
 DEFAULT_WORKLOAD = "cfg3"
@@ -56,7 +56,7 @@ ALPHA = 0.1
 # Arnoldi steps the GPU solver takes per solve on each workload (measured on
 # the GB300 by this benchmark's GPU arm; the reference arm cannot run the GPU
 # and scales its per-step time by these counts)
-GPU_STEPS_PER_SOLVE = {"cfg3": 113, "cfg2": 100, "cfg1": 29, "cfg4": 82}
+GPU_STEPS_PER_SOLVE = {"cfg3": 95, "cfg2": 100, "cfg1": 29, "cfg4": 67}
 
 
 def workload_config(p, name=DEFAULT_WORKLOAD, nrhs=1, symbol_kind=0):

@@ -71,7 +71,7 @@ def test_config2_apply_and_solve_full_size(hz):
 
 def test_config4_batched_apply_sampled_rhs(hz):
     p = S.config4()
-    med_g, med_o = media(hz, p, alpha=0.15)
+    med_g, med_o = media(hz, p, alpha=0.1)
     nrhs = p.f.shape[0]
     plan = hz.Plan(med_g, precision=1, restart=p.restart, tol=p.tol, max_nrhs=nrhs, graphs=True)
     plan.autotune()
@@ -89,7 +89,7 @@ def test_config4_batched_solve_every_rhs(hz):
     operator from the returned solution, meets the tolerance and agrees with
     the residual the library reports."""
     p = S.config4()
-    med_g, med_o = media(hz, p, alpha=0.15)
+    med_g, med_o = media(hz, p, alpha=0.1)
     nrhs = p.f.shape[0]
     plan = hz.Plan(med_g, precision=1, restart=p.restart, tol=p.tol, max_nrhs=nrhs, graphs=True)
     plan.autotune()
@@ -105,7 +105,7 @@ def test_config4_batched_solve_every_rhs(hz):
 
 def test_config3_plane_wave_and_solve_full_size(hz):
     p = S.config3()
-    med_g, med_o = media(hz, p, alpha=0.15)
+    med_g, med_o = media(hz, p, alpha=0.3)
     plan = hz.Plan(med_g, precision=1, restart=p.restart, tol=p.tol)
     plan.autotune()
     kv = (5, -17, 64)

@@ -847,7 +847,7 @@ def run_serving(args):
         keys.setdefault((q.shape, q.M, q.Mt), q)
     if not args.no_pretune:
         for (shape, M, Mt), q in sorted(keys.items(), key=lambda kv: str(kv[0])):
-            med = hz.Medium(q.c, q.zeta, omega=q.omega, M=M, Mt=Mt, alpha=0.15)
+            med = hz.Medium(q.c, q.zeta, omega=q.omega, M=M, Mt=Mt, alpha=args.serve_alpha)
             plan = hz.Plan(med, precision=1, restart=q.restart, tol=q.tol, max_nrhs=4)
             plan.autotune()
             del plan, med
@@ -890,7 +890,7 @@ def run_serving(args):
                 time.sleep(dt)
             else:
                 late = max(late, -dt)
-            t = srv.submit(q.c, q.f, omega=q.omega, M=q.M, Mt=q.Mt, zeta=q.zeta, alpha=0.15,
+            t = srv.submit(q.c, q.f, omega=q.omega, M=q.M, Mt=q.Mt, zeta=q.zeta, alpha=args.serve_alpha,
                            restart=q.restart, tol=q.tol, precision=precision, graphs=graphs_for(q))
             out_q.put((t, q.f.shape[0]))
             del q
@@ -906,7 +906,7 @@ def run_serving(args):
     srv = hz.Server(max_slots=2)
     for i in range(2):
         q = request(i)
-        srv.result(srv.submit(q.c, q.f, omega=q.omega, M=q.M, Mt=q.Mt, zeta=q.zeta, alpha=0.15,
+        srv.result(srv.submit(q.c, q.f, omega=q.omega, M=q.M, Mt=q.Mt, zeta=q.zeta, alpha=args.serve_alpha,
                               restart=q.restart, tol=q.tol), timeout=600)
     srv.close()
 
@@ -948,7 +948,7 @@ def run_serving(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
            "config": {"workload": f"{wl}-poisson{args.rate}/s-slots{args.slots}"
                                   f"-batch{args.batch_slots}-bypass{args.max_bypass}"
-                                  f"-order{args.order}",
+                                  f"-order{args.order}-alpha{args.serve_alpha}",
                       "grids": sorted({"x".join(map(str, k[0])) for k in keys}),
                       "rhs_total": rhs, "graphs": args.serve_graphs,
                       "pretune_s": t_tune, "pretuned_keys": 0 if args.no_pretune else len(keys)},
@@ -989,6 +989,8 @@ def main():
                     help="cfg3: side of the cube (256 is the workload; smaller for profiling)")
     ap.add_argument("--restart", type=int, default=0,
                     help="override the workload's restart length m (0: the workload's own)")
+    ap.add_argument("--serve-alpha", type=float, default=0.1,
+                    help="serving: node damping alpha of every request")
     ap.add_argument("--order", type=int, default=1, choices=[0, 1],
                     help="serving: admission order, 0 arrival order, 1 smallest footprint first")
     ap.add_argument("--max-bypass", type=int, default=0,

@@ -406,7 +406,10 @@ def run_gpu(args, p, name):
     fh = torch.from_numpy(np.ascontiguousarray(p.f)).pin_memory().numpy()
     e2e_steps = max(1, min(args.steps, 5))
     uhs = [torch.zeros(p.f.shape, dtype=torch.complex128).pin_memory().numpy()
-           for _ in range(e2e_steps)]
+           for _ in range(e2e_steps + 1)]
+    # one untimed host-buffer solve first, as the device-timed leg has its
+    # warm-up solves
+    plan.solve(fh, uhs.pop(), stream=stream)
     torch.cuda.synchronize()
     barrier(dist)
     t0 = time.perf_counter()
